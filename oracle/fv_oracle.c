@@ -1,0 +1,862 @@
+/*
+ * fv_oracle.c -- plain, slow CPU oracle for batched implied volatility.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark; never by the product path.  It shares no
+ * code with the CUDA library.  Build: gcc -O2 -ffp-contract=off (see build.py
+ * beside this file).
+ *
+ * Notation (paper Section 2.2 "normalised Black", Section 2.4 Black-76):
+ *   theta = +1 call / -1 put, D = e^{-rT}, F = forward (Black-76) or
+ *   S e^{(r-q)T} (BSM; Black-Scholes is BSM with q = 0), p = P / D,
+ *   x = ln(F/K), s = sigma sqrt(T), beta = p / sqrt(F K),
+ *   b(x,s,theta) = theta [e^{x/2} Phi(theta(x/s+s/2)) - e^{-x/2} Phi(theta(x/s-s/2))],
+ *   so that P = D sqrt(F K) b(x, sigma sqrt(T), theta).
+ *
+ * Three kinds of function live here:
+ *   1. the definitions, evaluated in IEEE binary128 (_Float128, glibc's
+ *      expf128/erfcf128/...): price, normalised Black, implied volatility as a
+ *      bisected root, Greeks and the implicit-function gradient;
+ *   2. the per-quote status decision, in FP64, because an integer decided by
+ *      floating point must be decided in the kernel's precision;
+ *   3. the two solvers of Section 2.2 written step by step in FP64 (LBR:
+ *      boundaries, four-region guess, three-branch objective, Householder(3);
+ *      Halley x8 + bisection fallback), taking the normalised Black value from
+ *      binary128 so that only the algorithm's steps are under test.
+ */
+#define _GNU_SOURCE
+#include "fv_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+typedef _Float128 q128;
+
+/* ------------------------------------------------------------------------- */
+/* binary128 primitives                                                       */
+/* ------------------------------------------------------------------------- */
+static q128 q_rsqrt2(void) { return sqrtf128(0.5f128); }
+static q128 q_inv_sqrt_2pi(void) { return 1.0f128 / sqrtf128(2.0f128 * M_PIf128); }
+
+/* standard normal CDF, Phi(z) = erfc(-z/sqrt 2)/2 (Section 2.3: the CDF is
+ * evaluated through erfc for deep out-of-the-money precision) */
+static q128 Phi_q(q128 z) { return 0.5f128 * erfcf128(-z * q_rsqrt2()); }
+static q128 phi_q(q128 z) { return q_inv_sqrt_2pi() * expf128(-0.5f128 * z * z); }
+
+/* normalised Black with the two exponentials passed in (ep = e^{x/2},
+ * em = e^{-x/2}); s <= 0 gives the normalised intrinsic value. */
+static q128 nb_q_e(q128 x, q128 s, int th, q128 ep, q128 em) {
+  if (s <= 0) {
+    q128 v = (q128)th * (ep - em);
+    return v > 0 ? v : 0;
+  }
+  q128 h = x / s, t = 0.5f128 * s;
+  return (q128)th * (ep * Phi_q((q128)th * (h + t)) - em * Phi_q((q128)th * (h - t)));
+}
+static q128 nb_q(q128 x, q128 s, int th) {
+  return nb_q_e(x, s, th, expf128(0.5f128 * x), expf128(-0.5f128 * x));
+}
+/* b_max - b for a call: e^{x/2} Phi(-(h+t)) + e^{-x/2} Phi(h-t); both terms
+ * are positive, so the complement carries no cancellation. */
+static q128 nb_compl_q(q128 x, q128 s) {
+  q128 h = x / s, t = 0.5f128 * s;
+  return expf128(0.5f128 * x) * Phi_q(-(h + t)) + expf128(-0.5f128 * x) * Phi_q(h - t);
+}
+
+/* ------------------------------------------------------------------------- */
+/* threading                                                                  */
+/* ------------------------------------------------------------------------- */
+typedef void (*range_fn)(void* ctx, int64_t i0, int64_t i1);
+typedef struct {
+  range_fn fn;
+  void* ctx;
+  int64_t i0, i1;
+} job_t;
+static void* job_run(void* a) {
+  job_t* j = (job_t*)a;
+  j->fn(j->ctx, j->i0, j->i1);
+  return NULL;
+}
+int or_num_threads(void) {
+  long c = sysconf(_SC_NPROCESSORS_ONLN);
+  return c > 0 ? (int)c : 1;
+}
+static void parallel_for(int64_t n, int nthreads, range_fn fn, void* ctx) {
+  if (n <= 0) return;
+  if (nthreads <= 0) nthreads = or_num_threads();
+  if (nthreads > 256) nthreads = 256;
+  if ((int64_t)nthreads > n) nthreads = (int)n;
+  if (nthreads == 1) {
+    fn(ctx, 0, n);
+    return;
+  }
+  pthread_t th[256];
+  job_t jobs[256];
+  for (int k = 0; k < nthreads; k++) {
+    jobs[k].fn = fn;
+    jobs[k].ctx = ctx;
+    jobs[k].i0 = n * k / nthreads;
+    jobs[k].i1 = n * (k + 1) / nthreads;
+    pthread_create(&th[k], NULL, job_run, &jobs[k]);
+  }
+  for (int k = 0; k < nthreads; k++) pthread_join(th[k], NULL);
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP64 status decision (the same rule, the same operation order, is what the
+ * kernels implement).                                                        */
+/* ------------------------------------------------------------------------- */
+/* relative slack band of the bound tests: 4 * 2^-52 */
+#define EPS_S (4.0 * 2.220446049250313080847263336181640625e-16)
+
+typedef struct {
+  int status;      /* ORC_* */
+  int solve;       /* 1: OK and a positive root must be found; 0: sigma = 0 */
+  double x;        /* ln(F/K) */
+  double beta;     /* full normalised price */
+  double beta_otm; /* out-of-the-money normalised price (intrinsic removed) */
+  double x_otm;    /* -|x| */
+} quote_f64;
+
+static int finite_pos(double v) { return isfinite(v) && v > 0; }
+
+static void decide_f64(int model, double P, double SF, double K, double T, double r,
+                       double q, int8_t flag, quote_f64* o) {
+  memset(o, 0, sizeof(*o));
+  o->status = ORC_INVALID;
+  if (!(flag == 1 || flag == -1)) return;
+  if (!isfinite(P) || !finite_pos(SF) || !finite_pos(K) || !finite_pos(T) || !isfinite(r))
+    return;
+  double qq = 0.0;
+  if (model == ORC_BSM) {
+    if (!isfinite(q)) return;
+    qq = q;
+  }
+  /* ln(F/K) (or ln(S/K)): near the money F - K is exact (Sterbenz), so
+   * log1p((F-K)/K) keeps x accurate relative to itself; log(F/K) would carry
+   * an absolute error of one ulp of 1, which costs ~eps/s in sigma. */
+  double lm;
+  if (SF >= 0.5 * K && SF <= 2.0 * K)
+    lm = log1p((SF - K) / K);
+  else
+    lm = log(SF / K);
+  double x, beta;
+  if (model == ORC_BLACK76) {
+    x = lm;
+    beta = (P * exp(r * T)) / sqrt(SF * K);
+  } else {
+    x = lm + (r - qq) * T;
+    beta = (P * exp(0.5 * (r + qq) * T)) / sqrt(SF * K);
+  }
+  if (!isfinite(x) || !isfinite(beta)) return;
+  const double th = (double)flag;
+  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
+  double iota = th > 0 ? ep - em : em - ep;
+  if (iota < 0) iota = 0;
+  o->x = x;
+  o->beta = beta;
+  if (beta < iota * (1.0 - EPS_S)) {
+    o->status = ORC_BELOW_INTRINSIC;
+    return;
+  }
+  const double beta_otm = (th * x > 0) ? beta - iota : beta;
+  const double bmax_otm = 1.0 + (x > 0 ? em : ep); /* e^{-|x|/2} */
+  if (beta_otm >= bmax_otm * (1.0 - EPS_S)) {
+    o->status = ORC_ABOVE_MAX;
+    return;
+  }
+  o->status = ORC_OK;
+  o->beta_otm = beta_otm;
+  o->x_otm = -fabs(x);
+  o->solve = beta_otm > iota * EPS_S;
+}
+
+/* ------------------------------------------------------------------------- */
+/* binary128 normalisation (exact inputs -> x, beta) for the definitions      */
+/* ------------------------------------------------------------------------- */
+static void normalise_q(int model, double P, double SF, double K, double T, double r, double q,
+                        q128* x, q128* beta) {
+  q128 qq = (model == ORC_BSM) ? (q128)q : 0;
+  if (model == ORC_BLACK76) {
+    *x = logf128((q128)SF / (q128)K);
+    *beta = (q128)P * expf128((q128)r * (q128)T) / sqrtf128((q128)SF * (q128)K);
+  } else {
+    *x = logf128((q128)SF / (q128)K) + ((q128)r - qq) * (q128)T;
+    *beta = (q128)P * expf128(0.5f128 * ((q128)r + qq) * (q128)T) / sqrtf128((q128)SF * (q128)K);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Definition: sigma with b(x_otm, s) = beta_otm, by bisection in binary128.  */
+/* ------------------------------------------------------------------------- */
+static q128 solve_definition_q(q128 beta, q128 x) {
+  /* b(x, .) rises strictly from 0 to e^{x/2} (x <= 0); beta lies strictly in
+   * between.  Bracket by doubling / halving, then bisect to 2^-80 relative. */
+  const q128 ep = expf128(0.5f128 * x), em = expf128(-0.5f128 * x);
+  if (!(beta > 0)) return 0;
+  if (!(beta < ep)) return (q128)INFINITY;
+  q128 hi = x < 0 ? sqrtf128(-2.0f128 * x) : 1.0f128;
+  int guard = 0;
+  while (nb_q_e(x, hi, 1, ep, em) <= beta) {
+    hi *= 2;
+    if (++guard > 4000) return (q128)INFINITY;
+  }
+  q128 lo = 0.5f128 * hi;
+  guard = 0;
+  while (nb_q_e(x, lo, 1, ep, em) >= beta) {
+    hi = lo;
+    lo *= 0.5f128;
+    if (++guard > 4000) return 0;
+  }
+  const q128 tol = 0x1p-80f128;
+  for (int it = 0; it < 400 && (hi - lo) > tol * hi; it++) {
+    q128 mid = 0.5f128 * (lo + hi);
+    if (nb_q_e(x, mid, 1, ep, em) < beta)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5f128 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* exported: normalised Black, price, status                                  */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int model;
+  const double *P, *SF, *K, *T, *r, *q, *sigma, *x, *s, *grad;
+  const int8_t* flag;
+  const uint8_t* status_in;
+  double *out, *out2, *out3, *out4, *out5, *out6;
+  uint8_t* status;
+  int8_t* region;
+  int n_iter;
+} ctx_t;
+
+static void nb_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++)
+    c->out[i] = (double)nb_q((q128)c->x[i], (q128)c->s[i], c->flag[i] >= 0 ? 1 : -1);
+}
+void or_normalised_black(const double* x, const double* s, const int8_t* theta, int64_t n,
+                         double* out, int nthreads) {
+  ctx_t c = {0};
+  c.x = x;
+  c.s = s;
+  c.flag = theta;
+  c.out = out;
+  parallel_for(n, nthreads, nb_range, &c);
+}
+
+static int inputs_valid(int model, double SF, double K, double T, double r, double q,
+                        int8_t flag) {
+  if (!(flag == 1 || flag == -1)) return 0;
+  if (!finite_pos(SF) || !finite_pos(K) || !finite_pos(T) || !isfinite(r)) return 0;
+  if (model == ORC_BSM && !isfinite(q)) return 0;
+  return 1;
+}
+
+/* Model price at sigma: P = D sqrt(FK) b(x, sigma sqrt(T), theta), which is the
+ * textbook theta D [F Phi(theta d1) - K Phi(theta d2)]. */
+static q128 price_q(int model, double SF, double K, double T, double r, double q, double sigma,
+                    int th) {
+  q128 qq = (model == ORC_BSM) ? (q128)q : 0;
+  q128 D = expf128(-(q128)r * (q128)T);
+  q128 F = (model == ORC_BLACK76) ? (q128)SF : (q128)SF * expf128(((q128)r - qq) * (q128)T);
+  q128 s = (q128)sigma * sqrtf128((q128)T);
+  q128 x = logf128(F / (q128)K);
+  return D * sqrtf128(F * (q128)K) * nb_q(x, s, th);
+}
+static void price_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    double q = c->q ? c->q[i] : 0.0;
+    if (!inputs_valid(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->flag[i]) ||
+        !(c->sigma[i] >= 0) || !isfinite(c->sigma[i])) {
+      c->out[i] = NAN;
+      continue;
+    }
+    c->out[i] = (double)price_q(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->sigma[i],
+                                c->flag[i]);
+  }
+}
+void or_price(int model, const double* S_or_F, const double* K, const double* T, const double* r,
+              const double* q, const double* sigma, const int8_t* flag, int64_t n, double* out,
+              int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.sigma = sigma;
+  c.flag = flag;
+  c.out = out;
+  parallel_for(n, nthreads, price_range, &c);
+}
+
+static void status_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    quote_f64 d;
+    decide_f64(c->model, c->P[i], c->SF[i], c->K[i], c->T[i], c->r[i], c->q ? c->q[i] : 0.0,
+               c->flag[i], &d);
+    c->status[i] = (uint8_t)d.status;
+    if (c->out) c->out[i] = d.x;
+    if (c->out2) c->out2[i] = d.beta;
+  }
+}
+void or_status(int model, const double* P, const double* S_or_F, const double* K, const double* T,
+               const double* r, const double* q, const int8_t* flag, int64_t n, uint8_t* status,
+               double* x_out, double* beta_out, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.P = P;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.status = status;
+  c.out = x_out;
+  c.out2 = beta_out;
+  parallel_for(n, nthreads, status_range, &c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Definition of implied volatility                                           */
+/* ------------------------------------------------------------------------- */
+static void iv_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    double q = c->q ? c->q[i] : 0.0;
+    quote_f64 d;
+    decide_f64(c->model, c->P[i], c->SF[i], c->K[i], c->T[i], c->r[i], q, c->flag[i], &d);
+    c->status[i] = (uint8_t)d.status;
+    if (d.status != ORC_OK) {
+      c->out[i] = NAN;
+      continue;
+    }
+    if (!d.solve) {
+      c->out[i] = 0.0;
+      continue;
+    }
+    q128 x, beta;
+    normalise_q(c->model, c->P[i], c->SF[i], c->K[i], c->T[i], c->r[i], q, &x, &beta);
+    const int th = c->flag[i];
+    q128 iota = (q128)th * (expf128(0.5f128 * x) - expf128(-0.5f128 * x));
+    if (iota < 0) iota = 0;
+    q128 beta_otm = ((q128)th * x > 0) ? beta - iota : beta;
+    q128 x_otm = x > 0 ? -x : x;
+    q128 s = solve_definition_q(beta_otm, x_otm);
+    c->out[i] = (double)(s / sqrtf128((q128)c->T[i]));
+  }
+}
+void or_iv(int model, const double* P, const double* S_or_F, const double* K, const double* T,
+           const double* r, const double* q, const int8_t* flag, int64_t n, double* sigma,
+           uint8_t* status, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.P = P;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.out = sigma;
+  c.status = status;
+  parallel_for(n, nthreads, iv_range, &c);
+}
+
+static void cond_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    double q = c->q ? c->q[i] : 0.0;
+    c->out[i] = NAN;
+    c->out2[i] = NAN;
+    if (!inputs_valid(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->flag[i])) continue;
+    if (!(c->sigma[i] > 0) || !isfinite(c->sigma[i])) continue;
+    q128 x, beta;
+    normalise_q(c->model, c->P[i], c->SF[i], c->K[i], c->T[i], c->r[i], q, &x, &beta);
+    q128 s = (q128)c->sigma[i] * sqrtf128((q128)c->T[i]);
+    q128 h = x / s, t = 0.5f128 * s;
+    q128 v = q_inv_sqrt_2pi() * expf128(-0.5f128 * (h * h + t * t));
+    c->out[i] = (double)v;
+    c->out2[i] = (double)(beta / (s * v));
+  }
+}
+void or_conditioning(int model, const double* P, const double* S_or_F, const double* K,
+                     const double* T, const double* r, const double* q, const int8_t* flag,
+                     const double* sigma, int64_t n, double* vega_n, double* kappa,
+                     int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.P = P;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.sigma = sigma;
+  c.out = vega_n;
+  c.out2 = kappa;
+  parallel_for(n, nthreads, cond_range, &c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP64 helpers for the step-by-step solvers                                  */
+/* ------------------------------------------------------------------------- */
+static const double INV_SQRT_2PI = 0.398942280401432677939946059934381868;
+static const double SQRT_2PI = 2.50662827463100050241576528481104525;
+static const double SQRT3 = 1.73205080756887729352744634150587237;
+
+/* b(x,s) for the call, x <= 0, from binary128 rounded to FP64 */
+static double nb_d(double x, double s) { return (double)nb_q((q128)x, (q128)s, 1); }
+/* ln b(x,s) and b'/b for the call, from binary128 (no FP64 underflow in the
+ * lowest wing, where the objective works with ln b) */
+static void nb_log_d(double x, double s, double* L, double* qb) {
+  const q128 b = nb_q((q128)x, (q128)s, 1);
+  const q128 h = (q128)x / (q128)s, t = 0.5f128 * (q128)s;
+  const q128 bp = q_inv_sqrt_2pi() * expf128(-0.5f128 * (h * h + t * t));
+  *L = (double)logf128(b);
+  *qb = (double)(bp / b);
+}
+static double nbc_d(double x, double s) { return (double)nb_compl_q((q128)x, (q128)s); }
+/* normalised vega b'(s) = exp(-(h^2 + t^2)/2) / sqrt(2 pi) */
+static double vega_d(double x, double s) {
+  double h = x / s, t = 0.5 * s;
+  return exp(-0.5 * (h * h + t * t)) * INV_SQRT_2PI;
+}
+static double Phi_d(double z) { return 0.5 * erfc(-z * 0.70710678118654752440); }
+/* inverse normal CDF: Newton on ln Phi(z) = ln p from the tail asymptote */
+static double Phi_inv_d(double p) {
+  if (!(p > 0)) return -INFINITY;
+  if (!(p < 1)) return INFINITY;
+  if (p > 0.5) return -Phi_inv_d(1.0 - p);
+  double z = (p > 0.3) ? SQRT_2PI * (p - 0.5) : -sqrt(-2.0 * log(p));
+  const double lp = log(p);
+  for (int it = 0; it < 100; it++) {
+    double Pz = Phi_d(z);
+    double pdf = exp(-0.5 * z * z) * INV_SQRT_2PI;
+    double dz = (log(Pz) - lp) * Pz / pdf;
+    z -= dz;
+    if (fabs(dz) <= 1e-15 * (1.0 + fabs(z))) break;
+  }
+  return z;
+}
+
+/* cubic Hermite interpolation of s(beta) on [b0, b1] from end values and
+ * slopes ds/dbeta = 1/b' (the interior initial guess of Section 2.2) */
+static double hermite_guess(double beta, double b0, double b1, double s0, double s1, double d0,
+                            double d1) {
+  double dbeta = b1 - b0;
+  if (!(dbeta > 0)) return 0.5 * (s0 + s1);
+  double tau = (beta - b0) / dbeta, tau2 = tau * tau, tau3 = tau2 * tau;
+  double h00 = 2 * tau3 - 3 * tau2 + 1, h10 = tau3 - 2 * tau2 + tau;
+  double h01 = -2 * tau3 + 3 * tau2, h11 = tau3 - tau2;
+  return h00 * s0 + h10 * dbeta * d0 + h01 * s1 + h11 * dbeta * d1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* "Let's Be Rational" (Section 2.2, first item), FP64 step by step           */
+/* ------------------------------------------------------------------------- */
+/* beta in (0, e^{x/2}), x <= 0 (the reduced out-of-the-money call). */
+static double lbr_otm(double beta, double x, int n_iter, int* region) {
+  const double bmax = exp(0.5 * x);
+  double sc, bc, vc, sl = 0, bl = 0, vl = 0;
+  /* boundary points: inflection s_c = sqrt(2|x|), where the tangent of b meets
+   * 0 (s_l) and b_max (s_h); six normalised-Black evaluations (b and b' at
+   * s_l, s_c, s_h) */
+  if (x < 0) {
+    sc = sqrt(-2.0 * x);
+    bc = nb_d(x, sc);
+    vc = vega_d(x, sc);
+    sl = sc - bc / vc;
+    if (sl > 0) {
+      bl = nb_d(x, sl);
+      vl = vega_d(x, sl);
+    } else {
+      sl = 0;
+    }
+  } else {
+    sc = 0;
+    bc = 0;
+    vc = INV_SQRT_2PI;
+  }
+  const double sh = sc + (bmax - bc) / vc;
+  const double bh = nb_d(x, sh), vh = vega_d(x, sh);
+
+  /* four-region initial guess */
+  int reg;
+  double s;
+  if (beta < bl) {
+    /* lowest wing: b ~ c Phi(-|x|/(sqrt3 s))^3 as s -> 0; c matched at s_l */
+    reg = 0;
+    const double zl = -fabs(x) / (SQRT3 * sl);
+    const double Pl = Phi_d(zl);
+    const double cl = bl / (Pl * Pl * Pl);
+    const double z = Phi_inv_d(cbrt(beta / cl));
+    s = fabs(x) / (SQRT3 * fabs(z));
+  } else if (beta <= bc) {
+    reg = 1;
+    s = hermite_guess(beta, bl, bc, sl, sc, vl > 0 ? 1.0 / vl : 0.0, 1.0 / vc);
+  } else if (beta <= bh) {
+    reg = 2;
+    s = hermite_guess(beta, bc, bh, sc, sh, 1.0 / vc, 1.0 / vh);
+  } else {
+    /* highest wing: b_max - b ~ c' Phi(-s/2) as s -> inf; c' matched at s_h */
+    reg = 3;
+    const double ch = nbc_d(x, sh) / Phi_d(-0.5 * sh);
+    s = -2.0 * Phi_inv_d((bmax - beta) / ch);
+  }
+  if (region) *region = reg;
+
+  /* three-branch objective + Householder(3) */
+  const double ln_beta = log(beta);
+  const double c_beta = bmax - beta;
+  for (int k = 0; k < n_iter; k++) {
+    if (!(s > 0) || !isfinite(s)) break;
+    const double h = x / s, t = 0.5 * s;
+    const double bp = exp(-0.5 * (h * h + t * t)) * INV_SQRT_2PI;
+    const double u = h * h / s - 0.25 * s;           /* b''/b' */
+    const double du = -3.0 * h * h / (s * s) - 0.25; /* d(b''/b')/ds */
+    double nu, h2, h3;
+    if (reg == 0) {
+      /* g = 1/ln b - 1/ln beta */
+      double L, qb;
+      nb_log_d(x, s, &L, &qb);
+      if (!isfinite(L)) { /* b = 0 even in binary128: s far too small */
+        s *= 1.5;
+        continue;
+      }
+      const double k1 = 1.0 + 2.0 / L;
+      const double g = 1.0 / L - 1.0 / ln_beta;
+      const double gp = -qb / (L * L);
+      nu = -g / gp;
+      h2 = u - qb * k1;
+      h3 = h2 * h2 + du - (qb * u - qb * qb) * k1 + 2.0 * qb * qb / (L * L);
+    } else if (reg == 3) {
+      /* g = ln((b_max - beta)/(b_max - b)) */
+      const double cb = nbc_d(x, s);
+      const double w = bp / cb;
+      const double g = log(c_beta / cb);
+      nu = -g / w;
+      h2 = u + w;
+      h3 = h2 * h2 + du + w * h2;
+    } else {
+      /* g = b - beta */
+      const double b = nb_d(x, s);
+      nu = -(b - beta) / bp;
+      h2 = u;
+      h3 = u * u + du;
+    }
+    double ds = nu * (1.0 + 0.5 * h2 * nu) / (1.0 + nu * (h2 + h3 * nu / 6.0));
+    if (!isfinite(ds)) ds = nu;
+    /* keep s positive */
+    if (s + ds <= 0.25 * s) ds = -0.75 * s;
+    s += ds;
+  }
+  return s;
+}
+
+static void lbr_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    quote_f64 d;
+    decide_f64(c->model, c->P[i], c->SF[i], c->K[i], c->T[i], c->r[i], c->q ? c->q[i] : 0.0,
+               c->flag[i], &d);
+    c->status[i] = (uint8_t)d.status;
+    if (c->region) c->region[i] = -1;
+    if (d.status != ORC_OK) {
+      c->out[i] = NAN;
+      continue;
+    }
+    if (!d.solve) {
+      c->out[i] = 0.0;
+      continue;
+    }
+    int reg = -1;
+    double s = lbr_otm(d.beta_otm, d.x_otm, c->n_iter, &reg);
+    if (c->region) c->region[i] = (int8_t)reg;
+    c->out[i] = s / sqrt(c->T[i]);
+  }
+}
+void or_iv_lbr(int model, const double* P, const double* S_or_F, const double* K, const double* T,
+               const double* r, const double* q, const int8_t* flag, int64_t n, int n_iter,
+               double* sigma, uint8_t* status, int8_t* region, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.P = P;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.out = sigma;
+  c.status = status;
+  c.region = region;
+  c.n_iter = n_iter;
+  parallel_for(n, nthreads, lbr_range, &c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Halley x8 + bisection fallback (Section 2.2, second item), FP64            */
+/* ------------------------------------------------------------------------- */
+#define HALLEY_STEPS 8
+#define HALLEY_CONV_TOL 1e-10
+
+/* Fallback: bisection on the monotone residual ln b(s) - ln beta inside
+ * [lo, hi], each bisection replaced by a Newton step when that step stays in
+ * the bracket (Newton on the log residual does not crawl in the exponential
+ * lowest wing, where b - beta does). */
+static double bisect_fallback(double beta, double x, double lo, double hi) {
+  const double eps = 2.220446049250313e-16;
+  if (!isfinite(hi)) {
+    hi = lo > 0 ? 2.0 * lo : 1.0;
+    while (nb_d(x, hi) <= beta && hi < 1e6) {
+      lo = hi;
+      hi *= 2.0;
+    }
+  }
+  if (!(lo > 0)) {
+    lo = 0.5 * hi;
+    while (nb_d(x, lo) >= beta && lo > 1e-300) {
+      hi = lo;
+      lo *= 0.5;
+    }
+  }
+  const double ln_beta = log(beta);
+  double s = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; it++) {
+    double L, qb;
+    nb_log_d(x, s, &L, &qb);
+    const double f = L - ln_beta;
+    if (f < 0)
+      lo = s;
+    else if (f > 0)
+      hi = s;
+    else
+      return s;
+    const double sn = s - f / qb;
+    const double next = (sn > lo && sn < hi) ? sn : 0.5 * (lo + hi);
+    const double ds = next - s;
+    s = next;
+    if (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi) break;
+  }
+  return s;
+}
+
+static double halley_otm(double beta, double x, int* fell_back) {
+  /* Brenner-Subrahmanyam: at the money b ~ s / sqrt(2 pi) */
+  double s = SQRT_2PI * beta;
+  double lo = 0.0, hi = INFINITY, newton_err = INFINITY;
+  for (int k = 0; k < HALLEY_STEPS; k++) {
+    const double b = nb_d(x, s);
+    const double g = b - beta;
+    if (g < 0)
+      lo = s;
+    else if (g > 0)
+      hi = s;
+    else {
+      newton_err = 0;
+      break;
+    }
+    const double h = x / s, t = 0.5 * s;
+    const double bp = exp(-0.5 * (h * h + t * t)) * INV_SQRT_2PI;
+    const double u = h * h / s - 0.25 * s;
+    /* Newton estimate of the distance to the root, relative to s: the
+     * convergence test of the last sweep (a tiny Halley step alone can come
+     * from a flat residual far from the root) */
+    newton_err = fabs(g / bp) / s;
+    /* Halley on g = b - beta: ds = -2 g g' / (2 g'^2 - g g'') */
+    double step = -2.0 * g / (2.0 * bp - g * u);
+    double sn = s + step;
+    /* a step that leaves the bracket [lo, hi] becomes a bisection (or a
+     * doubling while no upper end is known) */
+    if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
+    s = sn;
+  }
+  int ok = isfinite(s) && s > 0 && newton_err <= HALLEY_CONV_TOL;
+  if (!ok) {
+    *fell_back = 1;
+    s = bisect_fallback(beta, x, lo, hi);
+  } else {
+    *fell_back = 0;
+  }
+  return s;
+}
+
+static void halley_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    quote_f64 d;
+    decide_f64(c->model, c->P[i], c->SF[i], c->K[i], c->T[i], c->r[i], c->q ? c->q[i] : 0.0,
+               c->flag[i], &d);
+    c->status[i] = (uint8_t)d.status;
+    if (c->region) ((uint8_t*)c->region)[i] = 0;
+    if (d.status != ORC_OK) {
+      c->out[i] = NAN;
+      continue;
+    }
+    if (!d.solve) {
+      c->out[i] = 0.0;
+      continue;
+    }
+    int fb = 0;
+    double s = halley_otm(d.beta_otm, d.x_otm, &fb);
+    if (c->region) ((uint8_t*)c->region)[i] = (uint8_t)fb;
+    c->out[i] = s / sqrt(c->T[i]);
+  }
+}
+void or_iv_halley(int model, const double* P, const double* S_or_F, const double* K,
+                  const double* T, const double* r, const double* q, const int8_t* flag, int64_t n,
+                  double* sigma, uint8_t* status, uint8_t* fallback, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.P = P;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.out = sigma;
+  c.status = status;
+  c.region = (int8_t*)fallback;
+  parallel_for(n, nthreads, halley_range, &c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Greeks and the implicit-function gradient (binary128 closed forms)         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  q128 V, dS, dK, dT, dr, dq, vega, gamma;
+} partials_q;
+
+/* raw partial derivatives of the model price at sigma */
+static void partials(int model, double SF, double K, double T, double r, double q, double sigma,
+                     int th, partials_q* o) {
+  const q128 qT = (q128)T, sq = sqrtf128(qT), sv = (q128)sigma * sq, qK = (q128)K;
+  const q128 qth = (q128)th, qr = (q128)r;
+  const q128 Dr = expf128(-qr * qT);
+  if (model == ORC_BLACK76) {
+    const q128 F = (q128)SF;
+    const q128 d1 = (logf128(F / qK) + 0.5f128 * sv * sv) / sv, d2 = d1 - sv;
+    const q128 N1 = Phi_q(qth * d1), N2 = Phi_q(qth * d2), n1 = phi_q(d1);
+    o->V = Dr * qth * (F * N1 - qK * N2);
+    o->dS = qth * Dr * N1;
+    o->dK = -qth * Dr * N2;
+    o->vega = F * Dr * n1 * sq;
+    o->dT = -qr * o->V + Dr * F * n1 * (q128)sigma / (2 * sq);
+    o->dr = -qT * o->V;
+    o->dq = 0;
+    o->gamma = Dr * n1 / (F * sv);
+  } else {
+    const q128 S = (q128)SF, qq = (model == ORC_BSM) ? (q128)q : 0;
+    const q128 Dq = expf128(-qq * qT);
+    const q128 d1 = (logf128(S / qK) + (qr - qq + 0.5f128 * (q128)sigma * (q128)sigma) * qT) / sv;
+    const q128 d2 = d1 - sv;
+    const q128 N1 = Phi_q(qth * d1), N2 = Phi_q(qth * d2), n1 = phi_q(d1);
+    o->V = qth * (S * Dq * N1 - qK * Dr * N2);
+    o->dS = qth * Dq * N1;
+    o->dK = -qth * Dr * N2;
+    o->vega = S * Dq * n1 * sq;
+    o->dT = S * Dq * n1 * (q128)sigma / (2 * sq) - qth * qq * S * Dq * N1 + qth * qr * qK * Dr * N2;
+    o->dr = qth * qK * qT * Dr * N2;
+    o->dq = -qth * S * qT * Dq * N1;
+    o->gamma = Dq * n1 / (S * sv);
+  }
+}
+
+static void greeks_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    double q = c->q ? c->q[i] : 0.0;
+    double* outs[5] = {c->out, c->out2, c->out3, c->out4, c->out5};
+    if (!inputs_valid(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->flag[i]) ||
+        !(c->sigma[i] > 0) || !isfinite(c->sigma[i])) {
+      for (int k = 0; k < 5; k++)
+        if (outs[k]) outs[k][i] = NAN;
+      continue;
+    }
+    partials_q p;
+    partials(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->sigma[i], c->flag[i], &p);
+    if (c->out) c->out[i] = (double)p.dS;
+    if (c->out2) c->out2[i] = (double)p.gamma;
+    if (c->out3) c->out3[i] = (double)(p.vega * 0.01f128);
+    if (c->out4) c->out4[i] = (double)(-p.dT / 365.0f128);
+    if (c->out5) c->out5[i] = (double)(p.dr * 0.01f128);
+  }
+}
+void or_greeks(int model, const double* S_or_F, const double* K, const double* T, const double* r,
+               const double* q, const double* sigma, const int8_t* flag, int64_t n, double* delta,
+               double* gamma, double* vega, double* theta, double* rho, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.sigma = sigma;
+  c.flag = flag;
+  c.out = delta;
+  c.out2 = gamma;
+  c.out3 = vega;
+  c.out4 = theta;
+  c.out5 = rho;
+  parallel_for(n, nthreads, greeks_range, &c);
+}
+
+static void grad_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    double q = c->q ? c->q[i] : 0.0;
+    double* outs[6] = {c->out, c->out2, c->out3, c->out4, c->out5, c->out6};
+    for (int k = 0; k < 6; k++)
+      if (outs[k]) outs[k][i] = 0.0;
+    if (c->status_in[i] != ORC_OK || !(c->sigma[i] > 0) || !isfinite(c->sigma[i])) continue;
+    if (!inputs_valid(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->flag[i])) continue;
+    partials_q p;
+    partials(c->model, c->SF[i], c->K[i], c->T[i], c->r[i], q, c->sigma[i], c->flag[i], &p);
+    if (!(p.vega > 0) || (double)p.vega == 0.0) continue;
+    const q128 g = (q128)c->grad[i];
+    if (c->out) c->out[i] = (double)(g / p.vega);
+    if (c->out2) c->out2[i] = (double)(-g * p.dS / p.vega);
+    if (c->out3) c->out3[i] = (double)(-g * p.dK / p.vega);
+    if (c->out4) c->out4[i] = (double)(-g * p.dT / p.vega);
+    if (c->out5) c->out5[i] = (double)(-g * p.dr / p.vega);
+    if (c->out6) c->out6[i] = (double)(-g * p.dq / p.vega);
+  }
+}
+void or_iv_grad(int model, const double* S_or_F, const double* K, const double* T, const double* r,
+                const double* q, const int8_t* flag, const double* sigma, const uint8_t* status,
+                const double* grad_sigma, int64_t n, double* gP, double* gS, double* gK,
+                double* gT, double* gr, double* gq, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.sigma = sigma;
+  c.status_in = status;
+  c.grad = grad_sigma;
+  c.out = gP;
+  c.out2 = gS;
+  c.out3 = gK;
+  c.out4 = gT;
+  c.out5 = gr;
+  c.out6 = gq;
+  parallel_for(n, nthreads, grad_range, &c);
+}

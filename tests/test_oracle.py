@@ -1,0 +1,377 @@
+"""Pins of the CPU oracle against what the mathematics and the paper fix.
+
+Every test here runs on the CPU.  None re-types the oracle's own formula: the
+price is checked against the risk-neutral expectation by quadrature, the
+normalised Black function against the closed form at the money and its series
+limits, the implied volatility against an independent mpmath root and against
+the closed-form inverse at the money, and the solvers of Section 2.2 against
+the binary128 definition.
+"""
+import json
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import oracle as orc
+from paper_2604_27210_gb300 import workloads as wl
+
+EPS = 2.0 ** -52
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# price and normalised Black
+# ---------------------------------------------------------------------------
+def _expectation_price(model, SF, K, T, r, q, sigma, theta):
+    """Discounted E[(theta (F_T - K))^+] by quadrature over the lognormal law."""
+    mp.mp.dps = 40
+    SF, K, T, r, q, sigma = (mp.mpf(v) for v in (SF, K, T, r, q, sigma))
+    F = SF if model == orc.BLACK76 else SF * mp.exp((r - q) * T)
+    s = sigma * mp.sqrt(T)
+    zk = (mp.log(K / F) + s * s / 2) / s  # F_T = K at z = zk
+
+    def payoff(z):
+        FT = F * mp.exp(-s * s / 2 + s * z)
+        return max(theta * (FT - K), 0) * mp.npdf(z)
+
+    lim = [-mp.inf, zk, mp.inf]
+    return mp.exp(-r * T) * mp.quad(payoff, lim)
+
+
+@pytest.mark.parametrize("model", [orc.BLACK76, orc.BLACK_SCHOLES, orc.BSM])
+def test_price_equals_risk_neutral_expectation(model):
+    cases = [(100.0, 95.0, 0.25, 0.05, 0.02, 0.2, 1), (100.0, 105.0, 0.25, 0.05, 0.02, 0.2, -1),
+             (100.0, 130.0, 1.5, 0.01, 0.03, 0.35, 1), (100.0, 70.0, 0.1, 0.04, 0.0, 0.6, -1),
+             (42.0, 40.0, 0.5, 0.1, 0.01, 0.2, 1), (100.0, 100.0, 2.0, 0.0, 0.0, 1.2, -1)]
+    for SF, K, T, r, q, sig, th in cases:
+        got = orc.price(model, SF, K, T, r, q, sig, th)[0]
+        want = float(_expectation_price(model, SF, K, T, r, q if model == orc.BSM else 0.0, sig, th))
+        assert got == pytest.approx(want, rel=1e-13, abs=1e-300)
+
+
+def test_put_call_parity():
+    w = wl.black76_quotes(512, seed=11)
+    for model in (orc.BLACK76, orc.BSM):
+        q = np.full(512, 0.02) if model == orc.BSM else None
+        c = orc.price(model, w["S_or_F"], w["K"], w["T"], w["r"], q, w["sigma_true"], 1)
+        p = orc.price(model, w["S_or_F"], w["K"], w["T"], w["r"], q, w["sigma_true"], -1)
+        D = np.exp(-w["r"] * w["T"])
+        F = w["S_or_F"] if model == orc.BLACK76 else w["S_or_F"] * np.exp((w["r"] - 0.02) * w["T"])
+        np.testing.assert_allclose(c - p, D * (F - w["K"]), rtol=0, atol=1e-12 * 100)
+
+
+def test_normalised_black_at_the_money_is_erf():
+    # x = 0: b(0, s) = Phi(s/2) - Phi(-s/2) = erf(s / (2 sqrt 2))
+    s = np.logspace(-6, 1.3, 200)
+    b = orc.normalised_black(np.zeros_like(s), s, 1)
+    np.testing.assert_allclose(b, special.erf(s / (2 * math.sqrt(2))), rtol=4 * EPS, atol=0)
+
+
+def test_normalised_black_brenner_subrahmanyam_limit():
+    # at the money, b = s/sqrt(2 pi) - s^3/(24 sqrt(2 pi)) + O(s^5)
+    s = np.array([1e-8, 1e-6, 1e-4, 1e-3])
+    b = orc.normalised_black(np.zeros_like(s), s, 1)
+    bs = s / math.sqrt(2 * math.pi) * (1 - s * s / 24)
+    np.testing.assert_allclose(b, bs, rtol=1e-12)
+
+
+def test_normalised_black_symmetries():
+    g = np.random.default_rng(5)
+    x = g.uniform(-4, 4, 300)
+    s = np.exp(g.uniform(np.log(1e-3), np.log(5), 300))
+    bc = orc.normalised_black(x, s, 1)
+    bp = orc.normalised_black(x, s, -1)
+    # call - put = e^{x/2} - e^{-x/2}
+    assert np.all(np.abs((bc - bp) - 2 * np.sinh(x / 2)) <= 8 * EPS * np.exp(np.abs(x) / 2))
+    # b(x, s, theta) = b(-x, s, -theta)
+    np.testing.assert_allclose(bc, orc.normalised_black(-x, s, -1), rtol=8 * EPS, atol=1e-300)
+
+
+def test_normalised_black_limits_and_monotonicity():
+    for x in (-3.0, -0.2, 0.0):
+        s = np.logspace(-3, 2, 400)
+        b = orc.normalised_black(np.full_like(s, x), s, 1)
+        assert np.all(np.diff(b) >= 0)
+        assert b[-1] == pytest.approx(math.exp(x / 2), rel=1e-15)
+    # s -> 0: the call tends to its intrinsic value max(e^{x/2}-e^{-x/2}, 0)
+    assert orc.normalised_black(np.array([0.7]), np.array([1e-4]), 1)[0] == pytest.approx(
+        2 * math.sinh(0.35), rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# implied volatility by definition
+# ---------------------------------------------------------------------------
+def _gate(model, P, w, sig):
+    v, kap = orc.conditioning(model, P, w["S_or_F"], w["K"], w["T"], w["r"], w.get("q"), w["flag"],
+                              sig)
+    return v, kap
+
+
+def test_iv_round_trip_black76():
+    w = wl.fill_prices(wl.black76_quotes(2048, seed=0), orc.price)
+    sig, st = orc.iv(w["model"], w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    assert np.all(st == orc.OK)
+    v, kap = _gate(w["model"], w["P"], w, sig)
+    ok = sig > 0
+    # the price was rounded to FP64: sigma moves by at most ~eps * kappa
+    rel = np.abs(sig[ok] - w["sigma_true"][ok]) / w["sigma_true"][ok]
+    assert np.all(rel <= 2 * EPS * (1 + kap[ok]))
+    # price(iv(P)) == P within rounding where the normalised vega is not tiny
+    back = orc.price(w["model"], w["S_or_F"], w["K"], w["T"], w["r"], None, sig, w["flag"])
+    m = ok & (v > 1e-8)
+    np.testing.assert_allclose(back[m], w["P"][m], rtol=1e-15)
+
+
+def test_iv_at_the_money_closed_form():
+    # x = 0: beta = erf(s / (2 sqrt 2))  =>  s = 2 sqrt(2) erfinv(beta)
+    beta = np.linspace(1e-6, 0.99, 64)
+    n = beta.size
+    sig, st = orc.iv(orc.BLACK76, beta, np.ones(n), np.ones(n), np.ones(n), np.zeros(n), None,
+                     np.ones(n, np.int8))
+    mp.mp.dps = 40
+    want = np.array([float(2 * mp.sqrt(2) * mp.erfinv(mp.mpf(b))) for b in beta])
+    np.testing.assert_allclose(sig, want, rtol=2 * EPS)
+
+
+def test_iv_matches_independent_high_precision_root():
+    # brute force on tiny inputs: mpmath root of the textbook price at 40 digits
+    w = wl.fill_prices(wl.bsm_grid(8, 4, seed=9, below_fraction=0.0), orc.price)
+    sig, st = orc.iv(w["model"], w["P"], w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["flag"])
+    mp.mp.dps = 40
+    checked = 0
+    for i in range(sig.size):
+        if st[i] != orc.OK or not sig[i] > 0:
+            continue
+        S, K, T, r, q, th = (mp.mpf(float(w[k][i])) for k in ("S_or_F", "K", "T", "r", "q", "flag"))
+        P = mp.mpf(float(w["P"][i]))
+
+        def f(sg):
+            s = sg * mp.sqrt(T)
+            d1 = (mp.log(S / K) + (r - q + sg * sg / 2) * T) / s
+            d2 = d1 - s
+            V = th * (S * mp.exp(-q * T) * mp.ncdf(th * d1) - K * mp.exp(-r * T) * mp.ncdf(th * d2))
+            return mp.log(V / P)  # relative residual: deep-wing prices reach 1e-200
+
+        root = mp.findroot(f, (mp.mpf(float(sig[i])) * (1 - mp.mpf(10) ** -6),
+                               mp.mpf(float(sig[i])) * (1 + mp.mpf(10) ** -6)), solver="anderson")
+        assert float(root) == pytest.approx(sig[i], rel=4 * EPS), i
+        checked += 1
+    assert checked >= 16
+
+
+def test_iv_put_call_parity_consistency():
+    w = wl.fill_prices(wl.black76_quotes(512, seed=3), orc.price)
+    th = w["flag"]
+    D = np.exp(-w["r"] * w["T"])
+    # the same option seen from the other side through put-call parity
+    P_other = w["P"] - th * D * (w["S_or_F"] - w["K"])
+    s1, st1 = orc.iv(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, th)
+    s2, st2 = orc.iv(0, P_other, w["S_or_F"], w["K"], w["T"], w["r"], None, -th)
+    ok = (st1 == 0) & (st2 == 0) & (s1 > 0) & (s2 > 0)
+    assert ok.sum() > 400
+    v, kap = _gate(0, np.maximum(w["P"], P_other), w, s1)
+    rel = np.abs(s1[ok] - s2[ok]) / s1[ok]
+    assert np.all(rel <= 8 * EPS * (1 + kap[ok]))
+
+
+def test_iv_power_of_two_scale_invariance():
+    w = wl.fill_prices(wl.black76_quotes(256, seed=4), orc.price)
+    s0, st0 = orc.iv(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    for k in (-3, 2, 5):
+        f = 4.0 ** k
+        s1, st1 = orc.iv(0, w["P"] * f, w["S_or_F"] * f, w["K"] * f, w["T"], w["r"], None, w["flag"])
+        assert np.array_equal(st0, st1)
+        assert np.array_equal(s0, s1, equal_nan=True)
+
+
+def test_iv_monotone_in_price():
+    P = np.linspace(0.5, 20.0, 200)
+    n = P.size
+    sig, st = orc.iv(0, P, np.full(n, 100.0), np.full(n, 110.0), np.full(n, 0.7), np.full(n, 0.02),
+                     None, np.ones(n, np.int8))
+    assert np.all(st == 0) and np.all(np.diff(sig) > 0)
+
+
+def test_status_decisions_at_exact_bounds():
+    # r = 0 so discounting is exact: intrinsic = max(theta (F - K), 0), max = F (call) / K (put)
+    F, K, T = 100.0, 90.0, 1.0
+    cases = [  # (P, flag, expected status, expected sigma)
+        (10.0, 1, orc.OK, 0.0),                      # exactly intrinsic -> sigma = 0
+        (10.0 * (1 - 1e-12), 1, orc.BELOW_INTRINSIC, None),
+        (-1e-3, -1, orc.BELOW_INTRINSIC, None),      # negative price of an OTM put
+        (0.0, -1, orc.OK, 0.0),                      # zero price of an OTM put
+        (100.0, 1, orc.ABOVE_MAX, None),             # call worth the forward
+        (90.0, -1, orc.ABOVE_MAX, None),             # put worth the strike
+        (150.0, 1, orc.ABOVE_MAX, None),
+        (float("nan"), 1, orc.INVALID, None),
+        (5.0, 0, orc.INVALID, None),                 # flag neither +1 nor -1
+        (12.0, 1, orc.OK, "positive"),
+    ]
+    for P, fl, want_st, want_sig in cases:
+        sig, st = orc.iv(0, P, F, K, T, 0.0, None, fl)
+        assert st[0] == want_st, (P, fl)
+        if want_sig is None:
+            assert math.isnan(sig[0])
+        elif want_sig == "positive":
+            assert sig[0] > 0
+        else:
+            assert sig[0] == want_sig
+    bad = [dict(K=-1.0), dict(K=0.0), dict(T=0.0), dict(F=float("inf")), dict(r=float("nan"))]
+    for b in bad:
+        args = dict(F=F, K=K, T=T, r=0.0)
+        args.update(b)
+        sig, st = orc.iv(0, 5.0, args["F"], args["K"], args["T"], args["r"], None, 1)
+        assert st[0] == orc.INVALID and math.isnan(sig[0])
+
+
+def test_paper_quick_use_example():
+    with open(os.path.join(GOLDEN, "paper_quick_use.json")) as f:
+        g = json.load(f)
+    K = np.array(g["K"])
+    n = K.size
+    flag = np.array([1 if c == "c" else -1 for c in g["flag"]], np.int8)
+    S, t, r = np.full(n, g["S"]), np.full(n, g["t"]), np.full(n, g["r"])
+    P = orc.price(orc.BLACK_SCHOLES, S, K, t, r, None, np.full(n, g["sigma"]), flag)
+    sig, st = orc.iv(orc.BLACK_SCHOLES, P, S, K, t, r, None, flag)
+    assert np.all(st == orc.OK)
+    np.testing.assert_allclose(sig, g["expected_iv"], rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# the step-by-step solvers of Section 2.2 against the definition
+# ---------------------------------------------------------------------------
+def _grid():
+    xs = -np.concatenate([[0.0], np.logspace(-8, np.log10(8.0), 40)])
+    ss = np.logspace(-3, np.log10(12.0), 60)
+    X, S = np.meshgrid(xs, ss, indexing="ij")
+    X, S = X.ravel(), S.ravel()
+    n = X.size
+    w = dict(model=0, S_or_F=np.ones(n), K=np.exp(-X), T=np.ones(n), r=np.zeros(n), q=None,
+             flag=np.ones(n, np.int8), sigma_true=S)
+    return wl.fill_prices(w, orc.price)
+
+
+@pytest.fixture(scope="module")
+def grid_truth():
+    w = _grid()
+    sig, st = orc.iv(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    v, kap = _gate(0, w["P"], w, sig)
+    solved = (st == orc.OK) & (sig > 0) & (w["P"] > 1e-300)
+    return w, sig, st, v, kap, solved
+
+
+@pytest.mark.parametrize("n_iter", [2, 3])
+def test_lbr_reaches_machine_precision_in_two_iterations(grid_truth, n_iter):
+    w, sig, st, v, kap, solved = grid_truth
+    sl, st2, reg = orc.iv_lbr(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"],
+                              n_iter=n_iter)
+    assert np.array_equal(st, st2)
+    # all four initial-guess regions are exercised
+    assert set(np.unique(reg[solved])) == {0, 1, 2, 3}
+    rel = np.abs(sl[solved] - sig[solved]) / sig[solved]
+    assert np.all(rel <= 4 * EPS * (1 + kap[solved]))
+    gate = (v[solved] > 1e-8) & (kap[solved] <= 1e3)
+    assert rel[gate].max() <= 1e-12
+
+
+def test_lbr_one_iteration_is_not_enough(grid_truth):
+    w, sig, st, v, kap, solved = grid_truth
+    sl, _, _ = orc.iv_lbr(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"], n_iter=1)
+    rel = np.abs(sl[solved] - sig[solved]) / sig[solved]
+    assert rel.max() > 1e-9
+
+
+def test_halley_with_bisection_fallback(grid_truth):
+    w, sig, st, v, kap, solved = grid_truth
+    sh, st2, fb = orc.iv_halley(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    assert np.array_equal(st, st2)
+    rel = np.abs(sh[solved] - sig[solved]) / sig[solved]
+    assert np.all(rel <= 8 * EPS * (1 + kap[solved]))
+    # near the money the eight Halley sweeps converge without the fallback
+    atm = solved & (np.abs(np.log(w["K"])) < 0.05) & (w["sigma_true"] > 0.05) & (w["sigma_true"] < 2)
+    assert fb[atm].mean() < 0.05
+
+
+def test_solvers_on_in_the_money_quotes():
+    w = wl.fill_prices(wl.black76_quotes(1024, seed=21), orc.price)
+    sig, st = orc.iv(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    v, kap = _gate(0, w["P"], w, sig)
+    ok = (st == 0) & (sig > 0)
+    for fn in (lambda: orc.iv_lbr(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"]),
+               lambda: orc.iv_halley(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])):
+        s2, st2, _ = fn()
+        assert np.array_equal(st, st2)
+        rel = np.abs(s2[ok] - sig[ok]) / sig[ok]
+        assert np.all(rel <= 8 * EPS * (1 + kap[ok]))
+
+
+# ---------------------------------------------------------------------------
+# Greeks and the implicit-function gradient
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [orc.BLACK76, orc.BLACK_SCHOLES, orc.BSM])
+def test_greeks_against_finite_differences(model):
+    w = wl.bsm_quotes(64, seed=7)
+    S, K, T, r, q, sg, fl = (w[k] for k in ("S_or_F", "K", "T", "r", "q", "sigma_true", "flag"))
+    qq = q if model == orc.BSM else None
+    d, g, vg, th, rho = orc.greeks(model, S, K, T, r, qq, sg, fl)
+    P = lambda S_=S, K_=K, T_=T, r_=r, s_=sg: orc.price(model, S_, K_, T_, r_, qq, s_, fl)
+
+    # fourth-order central stencils
+    def d1(f, h):
+        return (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+
+    def d2(f, h):
+        return (-f(2 * h) + 16 * f(h) - 30 * f(0 * h) + 16 * f(-h) - f(-2 * h)) / (12 * h * h)
+
+    hS = 1e-3 * S
+    fd_d = d1(lambda e: P(S_=S + e), hS)
+    fd_g = d2(lambda e: P(S_=S + e), hS)
+    fd_v = d1(lambda e: P(s_=sg + e), 1e-4 * sg) * 0.01
+    fd_t = -d1(lambda e: P(T_=T + e), 1e-4 * T) / 365
+    fd_r = d1(lambda e: P(r_=r + e), np.full_like(r, 1e-4)) * 0.01
+    np.testing.assert_allclose(d, fd_d, rtol=1e-8, atol=1e-11)
+    np.testing.assert_allclose(g, fd_g, rtol=1e-6, atol=1e-10)
+    np.testing.assert_allclose(vg, fd_v, rtol=1e-8, atol=1e-11)
+    np.testing.assert_allclose(th, fd_t, rtol=1e-8, atol=1e-11)
+    np.testing.assert_allclose(rho, fd_r, rtol=1e-8, atol=1e-11)
+
+
+def test_greeks_textbook_values():
+    # S = K = 100, T = 1, r = 5%, sigma = 20%: d1 = 0.35, delta = N(0.35)
+    d, g, vg, th, rho = orc.greeks(orc.BLACK_SCHOLES, 100.0, 100.0, 1.0, 0.05, None, 0.2, 1)
+    assert d[0] == pytest.approx(0.5 * math.erfc(-0.35 / math.sqrt(2)), rel=1e-15)
+    assert g[0] == pytest.approx(math.exp(-0.35 ** 2 / 2) / math.sqrt(2 * math.pi) / 20.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("model", [orc.BLACK76, orc.BSM])
+def test_iv_gradient_against_finite_differences(model):
+    w = wl.bsm_quotes(48, seed=8)
+    if model == orc.BLACK76:
+        w["q"] = None
+    w = wl.fill_prices(w, orc.price)
+    args = [w[k] for k in ("S_or_F", "K", "T", "r")]
+    q = w["q"]
+    sig, st = orc.iv(model, w["P"], *args, q, w["flag"])
+    ok = (st == 0) & (sig > 0)
+    gs = np.ones(sig.size)
+    grads = orc.iv_grad(model, *args, q, w["flag"], sig, st, gs)
+
+    def iv_at(**kw):
+        a = dict(P=w["P"], S=args[0], K=args[1], T=args[2], r=args[3], q=q)
+        a.update(kw)
+        return orc.iv(model, a["P"], a["S"], a["K"], a["T"], a["r"], a["q"], w["flag"])[0]
+
+    rel_h = 1e-6
+    names = ["P", "S", "K", "T", "r"] + (["q"] if model == orc.BSM else [])
+    base = dict(P=w["P"], S=args[0], K=args[1], T=args[2], r=args[3], q=q)
+    for k, name in enumerate(names):
+        x0 = base[name]
+        h = rel_h * np.abs(x0) if name in ("P", "S", "K", "T") else np.full(sig.size, 1e-6)
+        fd = (iv_at(**{name: x0 + h}) - iv_at(**{name: x0 - h})) / (2 * h)
+        np.testing.assert_allclose(grads[k][ok], fd[ok], rtol=2e-6, atol=1e-8, err_msg=name)
+    if model != orc.BSM:
+        assert np.all(grads[5] == 0)
