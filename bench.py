@@ -1,0 +1,403 @@
+"""Benchmark: implied volatilities per second on the 16,777,216-quote BSM grid.
+
+One step = one pass of the whole implied-volatility path (validation,
+normalisation, status, intrinsic reduction, LBR boundaries, four-region guess,
+Householder(3) steps, store) over the 4,096 strikes x 4,096 maturities grid,
+on inputs resident in HBM (822 MB, larger than the 129 MB L2, so no flush is
+needed between steps).  `value` is quotes per second over all ranks (each rank
+solves its own grid: weak scaling, no collective on the data path).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fv|reference]
+                       [--path lbr|mixed|fp32|halley] [--strikes S --maturities M]
+Under torchrun (N > 1) every rank runs its own grid; rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle on bounded samples of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2604_27210_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "IVs/sec on 16M-quote chain: FP64 LBR vs mixed FP32+FP64, % HBM roofline"
+UNIT = "IV/s"
+# algorithmic HBM bytes per quote: P, S, K, T, r, q (8 B each) + flag (1 B) in,
+# sigma (8 B) + status (1 B) out
+BYTES_PER_QUOTE = 58
+# FP64 flops per quote executed by the LBR kernel on this workload (thread-level
+# DADD + DMUL + 2 DFMA, from the ncu counters summarised in
+# profiles/iv_lbr_fp64_bsm_grid.md); the ALU roofline's algorithmic work
+FP64_FLOPS_PER_QUOTE = {"lbr": None, "mixed": None}
+# nominal FP64 (non-tensor) peak of a GB300 at its 2070 MHz maximum clock
+FP64_PEAK_GFLOPS_NOMINAL = 1250.0
+SM_MAX_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value, world_size):
+    """Max of a float over all ranks (identity for one rank)."""
+    if world_size <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world_size):
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        # "under load": samples within the top half of the observed clock range
+        load = [v for v in sm if v >= 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(fv, torch, dev, n_strikes, n_maturities, seed):
+    """The BSM grid on the device, priced by the library's own pricing kernel."""
+    w = wl.bsm_grid(n_strikes, n_maturities, seed=seed)
+    t = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in
+         ("S_or_F", "K", "T", "r", "q", "flag")}
+    mask = torch.from_numpy(w["below_mask"]).to(dev)
+    sig = torch.from_numpy(w["sigma_true"]).to(dev)
+    sig = torch.where(mask, torch.zeros_like(sig), sig)
+    P = fv.fv_price(fv.FV_BSM, t["flag"], t["S_or_F"], t["K"], t["T"], t["r"], t["q"], sig)
+    P = torch.where(mask, P * torch.from_numpy(w["below_factor"]).to(dev), P)
+    t["P"] = P.contiguous()
+    torch.cuda.synchronize()
+    return t, w
+
+
+def run_path(fv, t, path, out, st):
+    args = (t["P"], t["S_or_F"], t["K"], t["T"], t["r"], t["q"], t["flag"])
+    if path == "lbr":
+        fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *args, out, st)
+    elif path == "halley":
+        fv.fv_implied_vol(fv.FV_BSM, fv.FV_HALLEY, *args, out, st)
+    elif path == "mixed":
+        fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR, fv.FV_MIXED, *args, out, st)
+    elif path == "fp32":
+        fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR, fv.FV_FP32, *args, out, st)
+    else:
+        raise ValueError(path)
+
+
+LAUNCHES_PER_STEP = {"lbr": 1, "mixed": 1, "fp32": 1, "halley": 2}
+
+
+def time_steps(torch, fn, steps, warmup, world_size):
+    """W untimed steps, then K steps between barrier + synchronize; CUDA events
+    on the current stream (the stream the library launches on)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world_size)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    per = []
+    e0.record(stream)
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        per.append((a, b))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world_size)
+    total_ms = e0.elapsed_time(e1)
+    kernel_ms = [a.elapsed_time(b) for a, b in per]
+    return total_ms, kernel_ms
+
+
+def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
+    """The same metric through the public API from pinned host buffers: each step
+    copies the inputs host->device, solves, and reads sigma + status back."""
+    keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
+    host = {k: t_dev[k].cpu().pin_memory() for k in keys}
+    dev = {k: torch.empty_like(t_dev[k]) for k in keys}
+    n = t_dev["P"].numel()
+    out = torch.empty(n, dtype=torch.float64, device=t_dev["P"].device)
+    st = torch.empty(n, dtype=torch.uint8, device=t_dev["P"].device)
+    out_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    st_h = torch.empty(n, dtype=torch.uint8).pin_memory()
+
+    def step():
+        for k in keys:
+            dev[k].copy_(host[k], non_blocking=True)
+        run_path(fv, dev, path, out, st)
+        out_h.copy_(out, non_blocking=True)
+        st_h.copy_(st, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = max(e0.elapsed_time(e1), 1e3 * wall) / steps
+    h2d = sum(host[k].numel() * host[k].element_size() for k in keys)
+    d2h = n * 9
+    return ms, h2d, d2h
+
+
+def cpu_baseline(w_host, P_host, n_sample, seed=123):
+    """The oracle's FP64 LBR (as it stands) on a seeded sample of the workload,
+    all host cores."""
+    from oracle import oracle as orc
+    g = np.random.default_rng(seed)
+    idx = np.sort(g.choice(P_host.size, size=min(n_sample, P_host.size), replace=False))
+    sub = {k: np.ascontiguousarray(np.asarray(w_host[k])[idx]) for k in
+           ("S_or_F", "K", "T", "r", "q", "flag")}
+    P = np.ascontiguousarray(P_host[idx])
+    cores = orc.num_threads()
+    t0 = time.perf_counter()
+    orc.iv_lbr(orc.BSM, P, sub["S_or_F"], sub["K"], sub["T"], sub["r"], sub["q"], sub["flag"],
+               n_iter=3, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return idx.size / dt, cores, idx.size, dt
+
+
+def reference_arm(args):
+    """CPU oracle arm: each step inverts a bounded seeded sample of the grid."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    n_s, n_m = args.strikes, args.maturities
+    w = wl.bsm_grid(n_s, n_m, seed=1)
+    sample = args.ref_sample
+    g = np.random.default_rng(7)
+    cores = orc.num_threads()
+    times = []
+    for k in range(args.warmup + args.steps):
+        idx = np.sort(g.choice(w["K"].size, size=sample, replace=False))
+        sub = {key: np.ascontiguousarray(np.asarray(w[key])[idx]) for key in
+               ("S_or_F", "K", "T", "r", "q", "flag", "sigma_true", "below_mask", "below_factor")}
+        sub["model"] = wl.BSM
+        wl.fill_prices(sub, orc.price_f64)
+        t0 = time.perf_counter()
+        orc.iv_lbr(orc.BSM, sub["P"], sub["S_or_F"], sub["K"], sub["T"], sub["r"], sub["q"],
+                   sub["flag"], n_iter=3, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sample * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "BSM grid %d strikes x %d maturities (sampled %d quotes per step)"
+                                   % (n_s, n_m, sample), "solver": "LBR (CPU oracle, FP64 steps, "
+                                                                   "binary128 normalised Black)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d seeded quotes of the grid per step" % sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fv", choices=["fv", "reference"])
+    ap.add_argument("--path", default="lbr", choices=["lbr", "mixed", "fp32", "halley"])
+    ap.add_argument("--strikes", type=int, default=4096)
+    ap.add_argument("--maturities", type=int, default=4096)
+    ap.add_argument("--ref-sample", type=int, default=262144)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the selected path (for profiler runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2604_27210_gb300 import fv
+
+    t, w = make_inputs(fv, torch, dev, args.strikes, args.maturities, seed=1 + rank)
+    n = t["P"].numel()
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+
+    with ClockSampler(local if ws > 1 else 0) as clk:
+        total_ms, kernel_ms = time_steps(torch, lambda: run_path(fv, t, args.path, out, st),
+                                         args.steps, args.warmup, ws)
+    clocks = clk.summary()
+    ms_step = max_over_ranks(total_ms / args.steps, ws)
+    value = ws * n / (ms_step * 1e-3)
+
+    # kernel-level roofline of the dominant (only) kernel of the step
+    k_ms = statistics.mean(kernel_ms)
+    hbm_peak, hbm_kind = peaks()
+    gbs = BYTES_PER_QUOTE * n / (k_ms * 1e-3) / 1e9
+    flops_q = FP64_FLOPS_PER_QUOTE.get(args.path)
+    if flops_q is not None:
+        achieved = flops_q * n / (k_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS_NOMINAL,
+                    "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS_NOMINAL,
+                    "traffic": None, "peak_kind": "nominal FP64 pipe at 2070 MHz (recipe)"}
+    else:
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "traffic": None}
+    hbm = {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
+           "frac": gbs / hbm_peak, "bytes_per_quote": BYTES_PER_QUOTE}
+
+    extras = {}
+    if not args.no_extras:
+        for p, k in (("mixed", args.steps), ("fp32", args.steps), ("halley", 3)):
+            if p == args.path:
+                continue
+            tm, km = time_steps(torch, lambda: run_path(fv, t, p, out, st), k, 1, ws)
+            extras[p] = {"value": ws * n / (max_over_ranks(tm / k, ws) * 1e-3),
+                         "ms_per_step": tm / k,
+                         "hbm_frac": BYTES_PER_QUOTE * n / (statistics.mean(km) * 1e-3) / 1e9 / hbm_peak}
+        # pricing and Greeks on the same grid
+        sig = t["P"].new_tensor(w["sigma_true"])
+        for name, fn in (("price", lambda: fv.fv_price(fv.FV_BSM, t["flag"], t["S_or_F"], t["K"],
+                                                        t["T"], t["r"], t["q"], sig, out)),
+                         ("greeks", lambda: fv.fv_greeks(fv.FV_BSM, t["flag"], t["S_or_F"], t["K"],
+                                                          t["T"], t["r"], t["q"], sig))):
+            tm, _ = time_steps(torch, fn, 5, 1, ws)
+            extras[name] = {"value": ws * n / (max_over_ranks(tm / 5, ws) * 1e-3), "unit": "quotes/s",
+                            "ms_per_step": tm / 5}
+
+    e2e_ms, h2d, d2h = e2e_measure(fv, torch, w, t, max(3, args.steps // 4), 1, args.path)
+    e2e_ms = max_over_ranks(e2e_ms, ws)
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        P_host = t["P"].cpu().numpy()
+        rate, cores, m, dt = cpu_baseline(w, P_host, args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded quotes of the grid, oracle FP64 LBR (3 Householder steps, "
+                         "binary128 normalised Black), %.1f s" % (m, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.path in ("lbr", "halley") else
+                ("f32+f64" if args.path == "mixed" else "f32"),
+                "data": "synthetic",
+                "config": {"workload": "BSM grid %d strikes x %d maturities = %d quotes per GPU, "
+                                       "S=100, log-moneyness [-3,3], T log-spaced [1/365,5], "
+                                       "r~U[0,.06], q~U[0,.05], sigma~U[.01,3], 5%% below intrinsic"
+                                       % (args.strikes, args.maturities, n),
+                           "path": args.path, "solver": "LBR" if args.path != "halley" else "Halley",
+                           "inputs_vs_l2": "inputs %.0f MB > 129 MB L2: no flush between steps"
+                                           % (n * 49 / 1e6),
+                           "parallelism": "replicas x%d (one grid per GPU)" % ws},
+                "roofline": roofline, "hbm_roofline": hbm,
+                "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP[args.path] * args.steps,
+                "e2e": {"value": ws * n / (e2e_ms * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "cpu_baseline": cpu, "paths": extras}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * fv.h -- C ABI of the GB300 batched implied-volatility library (libfv.so).
+ *
+ * The library computes, for batches of European quotes held in device memory,
+ * the model price, the five Greeks, the implied volatility (Jaeckel's "Let's
+ * Be Rational" or the Halley x8 solver) and the gradient of the implied
+ * volatility with respect to every market input.  It follows the problem
+ * statement of the fast-vollib paper: Section 2.1 (public API), Section 2.2
+ * (the two solvers), Section 2.4 (Black-76 convention) and Section 3
+ * (pricing models, Greeks, differentiable IV, batching).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Data pointers are DEVICE pointers owned by the caller, structure-of-arrays,
+ *    one element per quote, length n.  Inputs are never written.  Any
+ *    alignment is accepted.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    asynchronous: they launch on `stream` and return; they never synchronise
+ *    and, except where stated, allocate nothing.
+ *  - Models: FV_BLACK76 takes the forward F and a DISCOUNTED price, and uses
+ *    the same r for discounting and inversion (Section 2.4).  FV_BLACK_SCHOLES
+ *    takes the spot S with q = 0.  FV_BSM takes S and a continuous dividend
+ *    yield q.  `q` may be NULL unless the model is FV_BSM.
+ *  - Flags: int8, +1 call, -1 put (the "c"/"p" of Section 3); any other value
+ *    makes that quote FV_Q_INVALID.
+ *  - Per-quote failures never become call errors: they go to the uint8
+ *    `status` array (fv_quote_status) and the quote's sigma is NaN.  A price
+ *    exactly at the intrinsic value (within a relative band of 4 * 2^-52) is
+ *    FV_Q_OK with sigma = 0.
+ *  - Call errors (fv_err < 0) are for arguments only (NULL required pointer,
+ *    n < 0, unknown enum): the call is then rejected before any launch.  A
+ *    CUDA error seen at launch, or left pending by earlier asynchronous work,
+ *    returns FV_ERR_CUDA.  fv_last_error() describes the last error of the
+ *    calling thread.
+ *  - n = 0 is valid and launches nothing.
+ */
+#ifndef FV_H
+#define FV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { FV_BLACK76 = 0, FV_BLACK_SCHOLES = 1, FV_BSM = 2 } fv_model;
+typedef enum { FV_LBR = 0, FV_HALLEY = 1 } fv_solver;
+typedef enum { FV_FP64 = 0, FV_MIXED = 1, FV_FP32 = 2 } fv_precision;
+typedef enum { FV_DTYPE_F64 = 0, FV_DTYPE_F32 = 1 } fv_dtype;
+typedef enum {
+  FV_Q_OK = 0,              /* converged (or exactly at intrinsic: sigma = 0) */
+  FV_Q_BELOW_INTRINSIC = 1, /* price below the discounted intrinsic value      */
+  FV_Q_ABOVE_MAX = 2,       /* price at or above the forward / strike bound    */
+  FV_Q_INVALID = 3          /* non-finite input, F|S, K, T <= 0, bad flag      */
+} fv_quote_status;
+typedef enum {
+  FV_SUCCESS = 0,
+  FV_ERR_ARG = -1,
+  FV_ERR_CUDA = -2,
+  FV_ERR_UNSUPPORTED = -3,
+  FV_ERR_NOMEM = -4
+} fv_err;
+
+/* Model price at sigma (Section 3 "Pricing models": fast_black,
+ * fast_black_scholes, fast_black_scholes_merton).
+ *   P = e^{-rT} sqrt(F K) b(ln(F/K), sigma sqrt(T), flag),
+ *   F = forward (Black-76) or S e^{(r-q)T}.
+ * sigma = 0 gives the discounted intrinsic value.  Invalid inputs or sigma < 0
+ * give NaN.  FP64 in and out. */
+fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const double* K,
+                const double* T, const double* r, const double* q, const double* sigma, int64_t n,
+                double* out_price, void* stream);
+
+/* Implied volatility (Section 3 "Implied volatility": fast_implied_volatility
+ * for BSM quotes, fast_implied_volatility_black for discounted Black-76 mids;
+ * Section 2.2 for the solvers).  FP64 inputs, FP64 arithmetic.
+ *   FV_LBR:    normalised coordinates, four-region initial guess,
+ *              three-branch objective, Householder(3) iteration (two steps,
+ *              plus a third wherever the second still moved sigma).
+ *   FV_HALLEY: Brenner-Subrahmanyam guess, eight Halley sweeps on the
+ *              residual, bisection fallback on the quotes that fail the
+ *              convergence test.  Uses a library-owned device workspace,
+ *              allocated on the first call for a given size (make that first
+ *              call before capturing the stream into a CUDA graph); use
+ *              fv_implied_vol_ws to supply the workspace instead.
+ * out_sigma: FP64, NaN where status != FV_Q_OK.  status: uint8 per quote. */
+fv_err fv_implied_vol(fv_model model, fv_solver solver, const double* price, const double* S_or_F,
+                      const double* K, const double* T, const double* r, const double* q,
+                      const int8_t* flag, int64_t n, double* out_sigma, uint8_t* status,
+                      void* stream);
+
+/* Bytes of device workspace fv_implied_vol_ws needs for n quotes (0 for
+ * FV_LBR). */
+size_t fv_workspace_size(fv_solver solver, int64_t n);
+
+/* fv_implied_vol with a caller-owned device workspace of at least
+ * fv_workspace_size(solver, n) bytes, 16-byte aligned; allocates nothing.
+ * The workspace holds the compacted list of quotes handed to the bisection
+ * fallback (Section 2.2, Halley item); its contents are undefined after the
+ * call, and two calls in flight must not share it. */
+fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
+                         const double* S_or_F, const double* K, const double* T, const double* r,
+                         const double* q, const int8_t* flag, int64_t n, double* out_sigma,
+                         uint8_t* status, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Implied volatility with a chosen precision and input type.
+ *   FV_FP64:  as fv_implied_vol.
+ *   FV_MIXED: the LBR bulk in FP32 followed by one FP64 Householder(3)
+ *             correction; the normalisation, status decision, intrinsic
+ *             subtraction and the final residual are FP64 (result within
+ *             1e-12 of the FP64 path where the quote is well conditioned).
+ *   FV_FP32:  the LBR in FP32 only (relative error about 1e-5); the status
+ *             decision is still the FP64 rule, evaluated in FP64 only where
+ *             an FP32 evaluation cannot decide it.
+ * in_dtype says whether price, S_or_F, K, T, r, q point to double or float.
+ * Only FV_LBR is supported with FV_MIXED / FV_FP32 (else FV_ERR_UNSUPPORTED).
+ * out_sigma is always FP64. */
+fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precision,
+                         fv_dtype in_dtype, const void* price, const void* S_or_F, const void* K,
+                         const void* T, const void* r, const void* q, const int8_t* flag,
+                         int64_t n, double* out_sigma, uint8_t* status, void* stream);
+
+/* The five Greeks (Section 3 "Greeks": vectorized_{delta,gamma,theta,rho,vega}
+ * and get_all_greeks, computed in one pass sharing d1/d2).  py_vollib scaling:
+ * delta, gamma, vega per 1% of volatility, theta per calendar day (dV/dt over
+ * 365), rho per 1% of rate.  Black-76 Greeks are with respect to F.  Any
+ * output pointer may be NULL.  NaN unless the inputs are valid and sigma > 0. */
+fv_err fv_greeks(fv_model model, const int8_t* flag, const double* S_or_F, const double* K,
+                 const double* T, const double* r, const double* q, const double* sigma,
+                 int64_t n, double* delta, double* gamma, double* vega, double* theta,
+                 double* rho, void* stream);
+
+/* Adjoint of the implied volatility (Section 3 "Differentiable IV"): by the
+ * implicit-function theorem, d sigma / d P = 1 / vega and
+ * d sigma / d x_i = -(dV/d x_i) / vega for x_i in {S|F, K, T, r, q}, with
+ * vega = dV/d sigma at the given sigma (no solver iterations are stored).
+ * Each output is grad_sigma times that derivative; gq is 0 unless the model is
+ * FV_BSM.  All outputs are 0 where status != FV_Q_OK, sigma <= 0 or vega = 0.
+ * Any output pointer may be NULL; price is read only for the Black-76 T and r
+ * partials (where V = price at the root). */
+fv_err fv_iv_adjoint(fv_model model, const double* price, const double* S_or_F, const double* K,
+                     const double* T, const double* r, const double* q, const int8_t* flag,
+                     const double* sigma, const uint8_t* status, const double* grad_sigma,
+                     int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
+                     double* gq, void* stream);
+
+/* Normalised Black function b(x, s, theta) =
+ *   theta [e^{x/2} Phi(theta(x/s + s/2)) - e^{-x/2} Phi(theta(x/s - s/2))]
+ * in FP64 (the evaluation of Section 2.2: erfcx form, small-t expansion); the
+ * device function the solvers use.  s <= 0 gives the intrinsic value. */
+fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta, int64_t n,
+                           double* out, void* stream);
+
+/* ---- batches of option chains (spec batching pattern) ------------ */
+/* One chain: device arrays of n quotes sharing one forward (Black-76) or spot
+ * (BSM / Black-Scholes), one maturity and one rate.  Each chain may live in
+ * its own allocation. */
+typedef struct {
+  const double* price;  /* n discounted prices (Black-76) or prices     */
+  const double* K;      /* n strikes                                    */
+  const int8_t* flag;   /* n flags                                      */
+  double* sigma;        /* n outputs                                    */
+  uint8_t* status;      /* n outputs                                    */
+  int64_t n;            /* quotes in the chain (0 allowed)              */
+  double S_or_F;        /* forward (Black-76) or spot                   */
+  double T;             /* maturity in years                            */
+  double r;             /* rate                                         */
+  double q;             /* dividend yield (FV_BSM only)                 */
+} fv_chain;
+
+typedef struct fv_chains_plan fv_chains_plan;
+
+/* Build a plan for one batch of chains: copy the descriptors and a tile
+ * table (tile -> chain, offset) to the device, pick the block size and quotes
+ * per thread by timing the candidates on `stream` (autotune = 1; 0 takes the
+ * default), and capture the persistent launch into a CUDA graph.  Allocates
+ * device memory and synchronises `stream`; owned by the plan.  Only FV_LBR in
+ * FP64 is supported.  The chains' arrays must stay valid while the plan is
+ * used. */
+fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* chains,
+                             int64_t n_chains, int autotune, void* stream, fv_chains_plan** plan);
+
+/* Launch the plan's graph on `stream` (one persistent launch over every
+ * chain).  Allocates nothing. */
+fv_err fv_implied_vol_chains(fv_chains_plan* plan, void* stream);
+
+/* Same work without the graph: one launch of the persistent kernel. */
+fv_err fv_implied_vol_chains_direct(fv_chains_plan* plan, void* stream);
+
+/* Block size, quotes per thread, grid size and tile count the plan uses. */
+fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_per_thread,
+                           int* grid, int64_t* tiles, int64_t* quotes);
+
+fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
+
+/* Error reporting. */
+const char* fv_status_string(fv_err err);
+const char* fv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H */

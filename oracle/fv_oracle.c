@@ -34,6 +34,7 @@
 #include <unistd.h>
 
 typedef _Float128 q128;
+static double Phi_d(double z);
 
 /* ------------------------------------------------------------------------- */
 /* binary128 primitives                                                       */
@@ -297,6 +298,51 @@ void or_price(int model, const double* S_or_F, const double* K, const double* T,
   c.flag = flag;
   c.out = out;
   parallel_for(n, nthreads, price_range, &c);
+}
+
+/* Textbook price in plain FP64 (glibc erfc): theta D [F Phi(theta d1) -
+ * K Phi(theta d2)].  Fast; loses relative accuracy deep out of the money to
+ * the subtraction.  Used to generate large input sets, whose implied
+ * volatility the definition then inverts exactly as given. */
+static void price_f64_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    const double q = c->q ? c->q[i] : 0.0;
+    const double SF = c->SF[i], K = c->K[i], T = c->T[i], r = c->r[i], sg = c->sigma[i];
+    const int th = c->flag[i];
+    if (!inputs_valid(c->model, SF, K, T, r, q, c->flag[i]) || !(sg >= 0) || !isfinite(sg)) {
+      c->out[i] = NAN;
+      continue;
+    }
+    const double D = exp(-r * T);
+    const double F = (c->model == ORC_BLACK76) ? SF : SF * exp((r - q) * T);
+    double v;
+    if (sg == 0) {
+      v = th * (F - K);
+      v = v > 0 ? v : 0;
+    } else {
+      const double s = sg * sqrt(T);
+      const double d1 = log(F / K) / s + 0.5 * s, d2 = d1 - s;
+      v = th * (F * Phi_d(th * d1) - K * Phi_d(th * d2));
+      if (v < 0) v = 0;
+    }
+    c->out[i] = D * v;
+  }
+}
+void or_price_f64(int model, const double* S_or_F, const double* K, const double* T,
+                  const double* r, const double* q, const double* sigma, const int8_t* flag,
+                  int64_t n, double* out, int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.sigma = sigma;
+  c.flag = flag;
+  c.out = out;
+  parallel_for(n, nthreads, price_f64_range, &c);
 }
 
 static void status_range(void* c_, int64_t i0, int64_t i1) {

@@ -57,6 +57,13 @@ void or_price(int model, const double* S_or_F, const double* K, const double* T,
               const double* r, const double* q, const double* sigma,
               const int8_t* flag, int64_t n, double* out, int nthreads);
 
+/* The same price by the textbook formula in plain FP64 (fast; deep out of
+ * the money it loses relative accuracy to the subtraction).  A generator of
+ * large input sets. */
+void or_price_f64(int model, const double* S_or_F, const double* K, const double* T,
+                  const double* r, const double* q, const double* sigma,
+                  const int8_t* flag, int64_t n, double* out, int nthreads);
+
 /* Status only, by the FP64 decision rule (also returns the FP64 normalised
  * log-moneyness x and normalised price beta; NULL to skip). */
 void or_status(int model, const double* P, const double* S_or_F, const double* K,

@@ -32,6 +32,7 @@ def _load():
         lib.or_num_threads.restype = _INT
         lib.or_normalised_black.argtypes = [_D, _D, _I8, _N, _D, _INT]
         lib.or_price.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _INT]
+        lib.or_price_f64.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _INT]
         lib.or_status.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _U8, _D, _D, _INT]
         lib.or_iv.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _U8, _INT]
         lib.or_conditioning.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _D, _N, _D, _D, _INT]
@@ -87,6 +88,16 @@ def price(model, S_or_F, K, T, r, q, sigma, flag, nthreads=0):
     out = np.empty(n, np.float64)
     _load().or_price(model, keep[0][1], keep[1][1], keep[2][1], keep[3][1], keep[4][1], keep[5][1],
                      keep[6][1], n, out.ctypes.data_as(_D), nthreads)
+    return out
+
+
+def price_f64(model, S_or_F, K, T, r, q, sigma, flag, nthreads=0):
+    """Textbook price in plain FP64 (fast input generator for large sets)."""
+    n = _len(S_or_F, K, T, r, q, sigma, flag)
+    keep = [_f64(S_or_F, n), _f64(K, n), _f64(T, n), _f64(r, n), _f64(0.0 if q is None else q, n),
+            _f64(sigma, n), _i8(flag, n)]
+    out = np.empty(n, np.float64)
+    _load().or_price_f64(model, *[k[1] for k in keep], n, out.ctypes.data_as(_D), nthreads)
     return out
 
 
@@ -173,7 +184,7 @@ def iv_grad(model, S_or_F, K, T, r, q, flag, sigma, status_, grad_sigma, nthread
 
 
 __all__ = ["BLACK76", "BLACK_SCHOLES", "BSM", "OK", "BELOW_INTRINSIC", "ABOVE_MAX", "INVALID",
-           "normalised_black", "price", "status", "iv", "iv_lbr", "iv_halley", "conditioning",
+           "normalised_black", "price", "price_f64", "status", "iv", "iv_lbr", "iv_halley", "conditioning",
            "greeks", "iv_grad", "num_threads"]
 
 if os.environ.get("FV_ORACLE_EAGER"):

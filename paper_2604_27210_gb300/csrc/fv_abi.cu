@@ -1,0 +1,498 @@
+// fv_abi.cu -- the extern "C" entry points declared in include/fv.h.
+//
+// Argument checks happen here, before any launch; the kernels live in
+// fv_kernels.cu.  Nothing here synchronises except plan creation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fv.h"
+#include "fv_internal.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "no error";
+
+fv_err fail(fv_err e, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return e;
+}
+
+fv_err cuda_result(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return FV_SUCCESS;
+  return fail(FV_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// A CUDA error left pending by earlier asynchronous work is reported, not lost.
+fv_err pending_error(const char* where) {
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess) return FV_SUCCESS;
+  cudaGetLastError();
+  return cuda_result(e, where);
+}
+
+bool model_ok(int m) { return m == FV_BLACK76 || m == FV_BLACK_SCHOLES || m == FV_BSM; }
+bool solver_ok(int s) { return s == FV_LBR || s == FV_HALLEY; }
+
+#define FV_REQUIRE(ptr, name, fn)                                         \
+  do {                                                                    \
+    if ((ptr) == nullptr) return fail(FV_ERR_ARG, "%s: %s is NULL", fn, name); \
+  } while (0)
+
+fv_err check_iv_args(const char* fn, int model, int solver, const void* P, const void* SF,
+                     const void* K, const void* T, const void* r, const void* q,
+                     const int8_t* flag, int64_t n, const double* sigma, const uint8_t* status) {
+  if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, model);
+  if (!solver_ok(solver)) return fail(FV_ERR_ARG, "%s: unknown solver %d", fn, solver);
+  if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
+  if (n == 0) return FV_SUCCESS;
+  FV_REQUIRE(P, "price", fn);
+  FV_REQUIRE(SF, "S_or_F", fn);
+  FV_REQUIRE(K, "K", fn);
+  FV_REQUIRE(T, "T", fn);
+  FV_REQUIRE(r, "r", fn);
+  if (model == FV_BSM) FV_REQUIRE(q, "q", fn);
+  FV_REQUIRE(flag, "flag", fn);
+  FV_REQUIRE(sigma, "out_sigma", fn);
+  FV_REQUIRE(status, "status", fn);
+  return FV_SUCCESS;
+}
+
+// library-owned Halley workspace, one per device, grown on demand
+struct WsCache {
+  std::mutex mu;
+  void* ptr[64] = {nullptr};
+  size_t bytes[64] = {0};
+};
+WsCache g_ws;
+
+fv_err cached_workspace(size_t need, void** out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return fail(FV_ERR_UNSUPPORTED, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_ws.mu);
+  if (g_ws.bytes[dev] < need) {
+    if (g_ws.ptr[dev]) {
+      // the previous buffer may still be in use by queued work on any stream
+      cudaDeviceSynchronize();
+      cudaFree(g_ws.ptr[dev]);
+      g_ws.ptr[dev] = nullptr;
+      g_ws.bytes[dev] = 0;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FV_ERR_NOMEM, "Halley workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+    }
+    g_ws.ptr[dev] = p;
+    g_ws.bytes[dev] = need;
+  }
+  *out = g_ws.ptr[dev];
+  return FV_SUCCESS;
+}
+
+fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const void* P,
+              const void* SF, const void* K, const void* T, const void* r, const void* q,
+              const int8_t* flag, int64_t n, double* sigma, uint8_t* status, void* ws,
+              size_t ws_bytes, bool use_cache, void* stream) {
+  fv_err e = check_iv_args(fn, model, solver, P, SF, K, T, r, q, flag, n, sigma, status);
+  if (e != FV_SUCCESS || n == 0) return e;
+  if (solver == FV_HALLEY && prec != fvk::P_FP64)
+    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 only", fn);
+  const size_t need = solver == FV_HALLEY ? fvk::halley_workspace_bytes(n) : 0;
+  if (solver == FV_HALLEY && !use_cache) {
+    if (ws == nullptr) return fail(FV_ERR_ARG, "%s: workspace is NULL", fn);
+    if (ws_bytes < need)
+      return fail(FV_ERR_ARG, "%s: workspace of %zu bytes, %zu needed", fn, ws_bytes, need);
+    if (reinterpret_cast<uintptr_t>(ws) % 16 != 0)
+      return fail(FV_ERR_ARG, "%s: workspace not 16-byte aligned", fn);
+  }
+  // every argument check precedes the first CUDA call
+  if ((e = pending_error(fn)) != FV_SUCCESS) return e;
+  fvk::IvArgs a;
+  a.model = model;
+  a.f32_inputs = f32;
+  a.P = P;
+  a.SF = SF;
+  a.K = K;
+  a.T = T;
+  a.r = r;
+  a.q = (model == FV_BSM) ? q : nullptr;
+  a.flag = flag;
+  a.n = n;
+  a.sigma = sigma;
+  a.status = status;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (solver == FV_LBR) return cuda_result(fvk::launch_iv_lbr(a, prec, st), fn);
+  if (use_cache && (e = cached_workspace(need, &ws)) != FV_SUCCESS) return e;
+  return cuda_result(fvk::launch_iv_halley(a, ws, st), fn);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// chains plan
+// ---------------------------------------------------------------------------
+struct fv_chains_plan {
+  int model;
+  int block, qpt, grid;
+  int64_t n_tiles, n_quotes;
+  fvk::ChainDesc* d_chains;
+  fvk::Tile* d_tiles;
+  std::vector<fvk::ChainDesc> h_chains;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int device;
+};
+
+namespace {
+
+fv_err build_tiles(fv_chains_plan* p, int block, int qpt, std::vector<fvk::Tile>& tiles) {
+  tiles.clear();
+  const int64_t tile = (int64_t)block * qpt;
+  for (size_t c = 0; c < p->h_chains.size(); c++) {
+    for (int64_t off = 0; off < p->h_chains[c].n; off += tile) {
+      fvk::Tile t;
+      t.chain = (int32_t)c;
+      t.pad = 0;
+      t.offset = off;
+      tiles.push_back(t);
+    }
+  }
+  return FV_SUCCESS;
+}
+
+fv_err upload_tiles(fv_chains_plan* p, const std::vector<fvk::Tile>& tiles, cudaStream_t st) {
+  if (p->d_tiles) {
+    cudaStreamSynchronize(st);
+    cudaFree(p->d_tiles);
+    p->d_tiles = nullptr;
+  }
+  p->n_tiles = (int64_t)tiles.size();
+  if (tiles.empty()) return FV_SUCCESS;
+  cudaError_t e = cudaMalloc(&p->d_tiles, tiles.size() * sizeof(fvk::Tile));
+  if (e != cudaSuccess) return cuda_result(e, "fv_chains_plan_create: tile table");
+  e = cudaMemcpyAsync(p->d_tiles, tiles.data(), tiles.size() * sizeof(fvk::Tile),
+                      cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_result(e, "fv_chains_plan_create: tile upload");
+}
+
+int plan_grid(int block, int64_t n_tiles) {
+  const int per_sm = fvk::chains_max_blocks_per_sm(block);
+  const int64_t g = std::min<int64_t>((int64_t)fvk::sm_count() * per_sm, std::max<int64_t>(1, n_tiles));
+  return (int)g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fv_status_string(fv_err err) {
+  switch (err) {
+    case FV_SUCCESS: return "FV_SUCCESS";
+    case FV_ERR_ARG: return "FV_ERR_ARG: invalid argument";
+    case FV_ERR_CUDA: return "FV_ERR_CUDA: CUDA error";
+    case FV_ERR_UNSUPPORTED: return "FV_ERR_UNSUPPORTED: unsupported combination";
+    case FV_ERR_NOMEM: return "FV_ERR_NOMEM: device allocation failed";
+  }
+  return "unknown fv_err";
+}
+
+const char* fv_last_error(void) { return g_last_error; }
+
+fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const double* K,
+                const double* T, const double* r, const double* q, const double* sigma, int64_t n,
+                double* out_price, void* stream) {
+  const char* fn = "fv_price";
+  if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
+  if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
+  if (n == 0) return FV_SUCCESS;
+  FV_REQUIRE(flag, "flag", fn);
+  FV_REQUIRE(S_or_F, "S_or_F", fn);
+  FV_REQUIRE(K, "K", fn);
+  FV_REQUIRE(T, "T", fn);
+  FV_REQUIRE(r, "r", fn);
+  if (model == FV_BSM) FV_REQUIRE(q, "q", fn);
+  FV_REQUIRE(sigma, "sigma", fn);
+  FV_REQUIRE(out_price, "out_price", fn);
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  return cuda_result(fvk::launch_price(model, flag, S_or_F, K, T, r, model == FV_BSM ? q : nullptr,
+                                       sigma, n, out_price, static_cast<cudaStream_t>(stream)),
+                     fn);
+}
+
+fv_err fv_implied_vol(fv_model model, fv_solver solver, const double* price, const double* S_or_F,
+                      const double* K, const double* T, const double* r, const double* q,
+                      const int8_t* flag, int64_t n, double* out_sigma, uint8_t* status,
+                      void* stream) {
+  return run_iv("fv_implied_vol", model, solver, fvk::P_FP64, false, price, S_or_F, K, T, r, q,
+                flag, n, out_sigma, status, nullptr, 0, true, stream);
+}
+
+size_t fv_workspace_size(fv_solver solver, int64_t n) {
+  if (solver != FV_HALLEY || n <= 0) return 0;
+  return fvk::halley_workspace_bytes(n);
+}
+
+fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
+                         const double* S_or_F, const double* K, const double* T, const double* r,
+                         const double* q, const int8_t* flag, int64_t n, double* out_sigma,
+                         uint8_t* status, void* workspace, size_t workspace_bytes, void* stream) {
+  return run_iv("fv_implied_vol_ws", model, solver, fvk::P_FP64, false, price, S_or_F, K, T, r, q,
+                flag, n, out_sigma, status, workspace, workspace_bytes, false, stream);
+}
+
+fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precision,
+                         fv_dtype in_dtype, const void* price, const void* S_or_F, const void* K,
+                         const void* T, const void* r, const void* q, const int8_t* flag,
+                         int64_t n, double* out_sigma, uint8_t* status, void* stream) {
+  const char* fn = "fv_implied_vol_ex";
+  if (precision != FV_FP64 && precision != FV_MIXED && precision != FV_FP32)
+    return fail(FV_ERR_ARG, "%s: unknown precision %d", fn, (int)precision);
+  if (in_dtype != FV_DTYPE_F64 && in_dtype != FV_DTYPE_F32)
+    return fail(FV_ERR_ARG, "%s: unknown input dtype %d", fn, (int)in_dtype);
+  if (solver == FV_HALLEY && precision != FV_FP64)
+    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 only", fn);
+  return run_iv(fn, model, solver, (int)precision, in_dtype == FV_DTYPE_F32, price, S_or_F, K, T, r,
+                q, flag, n, out_sigma, status, nullptr, 0, true, stream);
+}
+
+fv_err fv_greeks(fv_model model, const int8_t* flag, const double* S_or_F, const double* K,
+                 const double* T, const double* r, const double* q, const double* sigma,
+                 int64_t n, double* delta, double* gamma, double* vega, double* theta,
+                 double* rho, void* stream) {
+  const char* fn = "fv_greeks";
+  if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
+  if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
+  if (n == 0) return FV_SUCCESS;
+  FV_REQUIRE(flag, "flag", fn);
+  FV_REQUIRE(S_or_F, "S_or_F", fn);
+  FV_REQUIRE(K, "K", fn);
+  FV_REQUIRE(T, "T", fn);
+  FV_REQUIRE(r, "r", fn);
+  if (model == FV_BSM) FV_REQUIRE(q, "q", fn);
+  FV_REQUIRE(sigma, "sigma", fn);
+  if (!delta && !gamma && !vega && !theta && !rho) return FV_SUCCESS;
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  return cuda_result(fvk::launch_greeks(model, flag, S_or_F, K, T, r,
+                                        model == FV_BSM ? q : nullptr, sigma, n, delta, gamma,
+                                        vega, theta, rho, static_cast<cudaStream_t>(stream)),
+                     fn);
+}
+
+fv_err fv_iv_adjoint(fv_model model, const double* price, const double* S_or_F, const double* K,
+                     const double* T, const double* r, const double* q, const int8_t* flag,
+                     const double* sigma, const uint8_t* status, const double* grad_sigma,
+                     int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
+                     double* gq, void* stream) {
+  const char* fn = "fv_iv_adjoint";
+  if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
+  if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
+  if (n == 0) return FV_SUCCESS;
+  if (model == FV_BLACK76) FV_REQUIRE(price, "price", fn);
+  FV_REQUIRE(S_or_F, "S_or_F", fn);
+  FV_REQUIRE(K, "K", fn);
+  FV_REQUIRE(T, "T", fn);
+  FV_REQUIRE(r, "r", fn);
+  if (model == FV_BSM) FV_REQUIRE(q, "q", fn);
+  FV_REQUIRE(flag, "flag", fn);
+  FV_REQUIRE(sigma, "sigma", fn);
+  FV_REQUIRE(status, "status", fn);
+  FV_REQUIRE(grad_sigma, "grad_sigma", fn);
+  if (!gP && !gS && !gK && !gT && !gr && !gq) return FV_SUCCESS;
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  return cuda_result(
+      fvk::launch_adjoint(model, price, S_or_F, K, T, r, model == FV_BSM ? q : nullptr, flag, sigma,
+                          status, grad_sigma, n, gP, gS, gK, gT, gr, gq,
+                          static_cast<cudaStream_t>(stream)),
+      fn);
+}
+
+fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta, int64_t n,
+                           double* out, void* stream) {
+  const char* fn = "fv_normalised_black";
+  if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
+  if (n == 0) return FV_SUCCESS;
+  FV_REQUIRE(x, "x", fn);
+  FV_REQUIRE(s, "s", fn);
+  FV_REQUIRE(theta, "theta", fn);
+  FV_REQUIRE(out, "out", fn);
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  return cuda_result(
+      fvk::launch_normalised_black(x, s, theta, n, out, static_cast<cudaStream_t>(stream)), fn);
+}
+
+fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* chains,
+                             int64_t n_chains, int autotune, void* stream, fv_chains_plan** plan) {
+  const char* fn = "fv_chains_plan_create";
+  FV_REQUIRE(plan, "plan", fn);
+  *plan = nullptr;
+  if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
+  if (!solver_ok(solver)) return fail(FV_ERR_ARG, "%s: unknown solver %d", fn, (int)solver);
+  if (solver != FV_LBR) return fail(FV_ERR_UNSUPPORTED, "%s: chains run the LBR solver", fn);
+  if (n_chains < 0) return fail(FV_ERR_ARG, "%s: n_chains < 0", fn);
+  if (n_chains > 0) FV_REQUIRE(chains, "chains", fn);
+  if (n_chains >= (int64_t)1 << 31) return fail(FV_ERR_ARG, "%s: too many chains", fn);
+  for (int64_t c = 0; c < n_chains; c++) {
+    const fv_chain& ch = chains[c];
+    if (ch.n < 0) return fail(FV_ERR_ARG, "%s: chain %lld has n < 0", fn, (long long)c);
+    if (ch.n > 0 && (!ch.price || !ch.K || !ch.flag || !ch.sigma || !ch.status))
+      return fail(FV_ERR_ARG, "%s: chain %lld has a NULL array", fn, (long long)c);
+  }
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fv_chains_plan* p = new fv_chains_plan();
+  p->model = model;
+  p->d_chains = nullptr;
+  p->d_tiles = nullptr;
+  p->graph = nullptr;
+  p->exec = nullptr;
+  p->n_quotes = 0;
+  cudaGetDevice(&p->device);
+  p->h_chains.resize((size_t)n_chains);
+  for (int64_t c = 0; c < n_chains; c++) {
+    fvk::ChainDesc& d = p->h_chains[(size_t)c];
+    d.P = chains[c].price;
+    d.K = chains[c].K;
+    d.flag = chains[c].flag;
+    d.sigma = chains[c].sigma;
+    d.status = chains[c].status;
+    d.n = chains[c].n;
+    d.SF = chains[c].S_or_F;
+    d.T = chains[c].T;
+    d.r = chains[c].r;
+    d.q = (model == FV_BSM) ? chains[c].q : 0.0;
+    p->n_quotes += d.n;
+  }
+  auto cleanup = [&](fv_err err) {
+    fv_chains_plan_destroy(p);
+    return err;
+  };
+  if (n_chains > 0) {
+    cudaError_t ce = cudaMalloc(&p->d_chains, (size_t)n_chains * sizeof(fvk::ChainDesc));
+    if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: descriptors"));
+    ce = cudaMemcpyAsync(p->d_chains, p->h_chains.data(), (size_t)n_chains * sizeof(fvk::ChainDesc),
+                         cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: upload"));
+  }
+  // candidates: (block, quotes per thread); the default first
+  const int cand[][2] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {128, 4}};
+  const int n_cand = autotune ? (int)(sizeof(cand) / sizeof(cand[0])) : 1;
+  std::vector<fvk::Tile> tiles;
+  int best = 0;
+  if (n_cand > 1 && p->n_quotes > 0) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int k = 0; k < n_cand; k++) {
+      build_tiles(p, cand[k][0], cand[k][1], tiles);
+      if ((e = upload_tiles(p, tiles, st)) != FV_SUCCESS) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cleanup(e);
+      }
+      const int grid = plan_grid(cand[k][0], p->n_tiles);
+      // one warm-up launch, then the timed one
+      fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, cand[k][0], cand[k][1], grid, st);
+      cudaEventRecord(e0, st);
+      fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, cand[k][0], cand[k][1], grid, st);
+      cudaEventRecord(e1, st);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cleanup(cuda_result(ce, "fv_chains_plan_create: autotune"));
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = k;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  p->block = cand[best][0];
+  p->qpt = cand[best][1];
+  build_tiles(p, p->block, p->qpt, tiles);
+  if ((e = upload_tiles(p, tiles, st)) != FV_SUCCESS) return cleanup(e);
+  p->grid = plan_grid(p->block, p->n_tiles);
+  // capture the persistent launch into a graph on a private stream
+  if (p->n_tiles > 0) {
+    cudaStream_t cs;
+    cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: stream"));
+    ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, p->block, p->qpt, p->grid, cs);
+      ce = cudaStreamEndCapture(cs, &p->graph);
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: graph capture"));
+  }
+  *plan = p;
+  return FV_SUCCESS;
+}
+
+fv_err fv_implied_vol_chains(fv_chains_plan* plan, void* stream) {
+  const char* fn = "fv_implied_vol_chains";
+  FV_REQUIRE(plan, "plan", fn);
+  if (plan->n_tiles == 0) return FV_SUCCESS;
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  return cuda_result(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)), fn);
+}
+
+fv_err fv_implied_vol_chains_direct(fv_chains_plan* plan, void* stream) {
+  const char* fn = "fv_implied_vol_chains_direct";
+  FV_REQUIRE(plan, "plan", fn);
+  if (plan->n_tiles == 0) return FV_SUCCESS;
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  return cuda_result(fvk::launch_chains(plan->model, plan->d_chains, plan->d_tiles, plan->n_tiles,
+                                        plan->block, plan->qpt, plan->grid,
+                                        static_cast<cudaStream_t>(stream)),
+                     fn);
+}
+
+fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_per_thread,
+                           int* grid, int64_t* tiles, int64_t* quotes) {
+  const char* fn = "fv_chains_plan_info";
+  FV_REQUIRE(plan, "plan", fn);
+  if (block) *block = plan->block;
+  if (quotes_per_thread) *quotes_per_thread = plan->qpt;
+  if (grid) *grid = plan->grid;
+  if (tiles) *tiles = plan->n_tiles;
+  if (quotes) *quotes = plan->n_quotes;
+  return FV_SUCCESS;
+}
+
+fv_err fv_chains_plan_destroy(fv_chains_plan* plan) {
+  if (!plan) return FV_SUCCESS;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->d_tiles) cudaFree(plan->d_tiles);
+  if (plan->d_chains) cudaFree(plan->d_chains);
+  delete plan;
+  return FV_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,532 @@
+// fv_device.cuh -- device math of the GB300 implied-volatility library.
+//
+// Notation (fast-vollib paper, Section 2.2 and Section 2.4):
+//   theta = +1 call / -1 put, x = ln(F/K), s = sigma sqrt(T),
+//   beta = P e^{rT} / sqrt(F K)  (normalised, undiscounted price),
+//   b(x, s) = e^{x/2} Phi(x/s + s/2) - e^{-x/2} Phi(x/s - s/2)  for the call,
+//   h = x/s, t = s/2.
+// Every quote is reduced to an out-of-the-money call with x <= 0 (intrinsic
+// value subtracted, put/call symmetry b(x,s,theta) = b(-x,s,-theta)).
+//
+// The normalised Black value is computed as b = e * B with
+//   e = exp(-(h^2 + t^2)/2)   (sqrt(2 pi) times the normalised vega b'),
+// so that ln b = -(h^2+t^2)/2 + ln B never underflows.  B comes from one of
+// two evaluations (Section 2.2 lists erfcx, asymptotic, small-t and CDF-direct
+// branches; two suffice here, because the erfcx form below carries the
+// CDF-direct and asymptotic regimes without overflow for the arguments the
+// solvers reach):
+//   erfcx form:  B = [erfcx(-(h+t)/sqrt2) - erfcx((t-h)/sqrt2)] / 2
+//   complement:  (b_max - b)/e = [erfcx((h+t)/sqrt2) + erfcx((t-h)/sqrt2)] / 2
+//   small t:     B = sqrt(2/pi) sum_k R^{(2k+1)}(h) t^{2k+1} / (2k+1)!
+// where R(h) = Phi(h)/phi(h) = sqrt(pi/2) erfcx(-h/sqrt2) is the Mills ratio,
+// whose derivatives satisfy R' = 1 + h R, so R^{(n)} = P_n(h) + Q_n(h) R with
+// integer polynomials (P_{n+1} = P_n' + Q_n, Q_{n+1} = Q_n' + h Q_n).  The
+// series is the odd part of R(h+t) - R(h-t), i.e. the cancellation-free form
+// of the erfcx difference when t is small.
+//
+// Every lane of a warp calls the same special functions with lane-selected
+// arguments (region-selected coefficients instead of region branches), so the
+// four LBR regions do not serialise the FP64 pipe.
+#pragma once
+
+#include <cstdint>
+
+namespace fvd {
+
+// mathematical constants
+constexpr double kInvSqrt2Pi = 0.398942280401432677939946059934381868;  // 1/sqrt(2 pi)
+constexpr double kSqrt2Pi = 2.50662827463100050241576528481104525;      // sqrt(2 pi)
+constexpr double kInvSqrt2 = 0.707106781186547524400844362104849039;    // 1/sqrt(2)
+constexpr double kSqrtPiOver2 = 1.25331413731550025120788264240552263;  // sqrt(pi/2)
+constexpr double kSqrt2OverPi = 0.797884560802865355879892119868763737;  // sqrt(2/pi)
+constexpr double kInvSqrt3 = 0.577350269189625764509148780501957456;    // 1/sqrt(3)
+constexpr double kLn2Pi = 1.83787706640934548356065947281123527;        // ln(2 pi)
+// relative slack band of the three bound tests of the status rule: 4 * 2^-52
+constexpr double kEpsS = 8.8817841970012523233890533447265625e-16;
+
+enum { Q_OK = 0, Q_BELOW = 1, Q_ABOVE = 2, Q_INVALID = 3 };
+enum { M_BLACK76 = 0, M_BS = 1, M_BSM = 2 };
+
+// ---------------------------------------------------------------------------
+// precision traits and special-function wrappers (CUDA's math library)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  // the small-t series is used below t_small with `terms` odd terms; its
+  // truncation error is below 1e-17 t there
+  static constexpr double t_small = 0.1;
+  static constexpr int terms = 6;
+  // beyond |h| = h_asym the series' cancellation A + hRC costs eps h^2 and the
+  // two-term asymptote of the Mills-ratio difference is exact to 1/h^4
+  static constexpr double h_asym = 1e6;
+  // ln p below which the inverse normal CDF takes its tail asymptote
+  static constexpr double ln_p_floor = -700.0;
+};
+template <>
+struct Prec<float> {
+  static constexpr float t_small = 0.3f;
+  static constexpr int terms = 4;
+  static constexpr float h_asym = 300.0f;
+  static constexpr float ln_p_floor = -80.0f;
+};
+
+__device__ __forceinline__ double f_exp(double v) { return exp(v); }
+__device__ __forceinline__ float f_exp(float v) { return expf(v); }
+__device__ __forceinline__ double f_log(double v) { return log(v); }
+__device__ __forceinline__ float f_log(float v) { return logf(v); }
+__device__ __forceinline__ double f_erfcx(double v) { return erfcx(v); }
+__device__ __forceinline__ float f_erfcx(float v) { return erfcxf(v); }
+__device__ __forceinline__ double f_ncdf(double v) { return normcdf(v); }
+__device__ __forceinline__ float f_ncdf(float v) { return normcdff(v); }
+__device__ __forceinline__ double f_ncdfinv(double v) { return normcdfinv(v); }
+__device__ __forceinline__ float f_ncdfinv(float v) { return normcdfinvf(v); }
+__device__ __forceinline__ double f_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float f_sqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double f_abs(double v) { return fabs(v); }
+__device__ __forceinline__ float f_abs(float v) { return fabsf(v); }
+__device__ __forceinline__ bool f_finite(double v) { return isfinite(v); }
+__device__ __forceinline__ bool f_finite(float v) { return isfinite(v); }
+
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// ---------------------------------------------------------------------------
+// normalisation and the per-quote status decision (always FP64)
+// ---------------------------------------------------------------------------
+struct Norm {
+  int status;       // Q_*
+  bool solve;       // OK and strictly above intrinsic: a positive root exists
+  double x;         // ln(F/K)
+  double beta;      // full normalised price
+  double iota;      // normalised intrinsic value
+  double beta_otm;  // beta - iota for in-the-money quotes, else beta
+  double x_otm;     // -|x|
+  double bmax;      // e^{x_otm/2}: upper bound of the reduced call
+  double ln_beta;   // ln beta when beta < 1e-280 (else 0: take log(beta_otm))
+};
+
+// ln(F/K): near the money F - K is exact (Sterbenz) and log1p keeps x accurate
+// relative to itself; log(F/K) would carry one ulp of 1 in absolute error.
+__device__ __forceinline__ double log_moneyness(double SF, double K) {
+  return (SF >= 0.5 * K && SF <= 2.0 * K) ? log1p(__ddiv_rn(__dsub_rn(SF, K), K))
+                                          : log(__ddiv_rn(SF, K));
+}
+
+__device__ __forceinline__ bool pos_finite(double v) { return isfinite(v) && v > 0.0; }
+
+__device__ __forceinline__ bool inputs_valid(int model, double SF, double K, double T, double r,
+                                             double q, int flag) {
+  if (!(flag == 1 || flag == -1)) return false;
+  if (!pos_finite(SF) || !pos_finite(K) || !pos_finite(T) || !isfinite(r)) return false;
+  if (model == M_BSM && !isfinite(q)) return false;
+  return true;
+}
+
+// x = ln(F/K) for the model (Black-Scholes / BSM: F = S e^{(r-q)T})
+__device__ __forceinline__ double model_x(int model, double SF, double K, double T, double r,
+                                          double q) {
+  const double lm = log_moneyness(SF, K);
+  if (model == M_BLACK76) return lm;
+  const double qq = model == M_BSM ? q : 0.0;
+  return __dadd_rn(lm, __dmul_rn(__dsub_rn(r, qq), T));
+}
+
+// The status rule: every product and sum rounded as written (no contraction),
+// so the decision matches an FP64 evaluation of the same expressions.
+__device__ __forceinline__ Norm decide(int model, double P, double SF, double K, double T,
+                                       double r, double q, int flag) {
+  Norm o;
+  o.status = Q_INVALID;
+  o.solve = false;
+  o.x = o.beta = o.iota = o.beta_otm = o.x_otm = o.ln_beta = 0.0;
+  o.bmax = 1.0;
+  if (!isfinite(P) || !inputs_valid(model, SF, K, T, r, q, flag)) return o;
+  const double qq = model == M_BSM ? q : 0.0;
+  const double x = model_x(model, SF, K, T, r, qq);
+  double beta;
+  const double rate = model == M_BLACK76 ? __dmul_rn(r, T)
+                                         : __dmul_rn(__dmul_rn(0.5, __dadd_rn(r, qq)), T);
+  beta = __ddiv_rn(__dmul_rn(P, exp(rate)), sqrt(__dmul_rn(SF, K)));
+  // beta of a price near the bottom of the FP64 range has lost digits to
+  // subnormal rounding; its logarithm is taken from P directly
+  o.ln_beta = (beta < 1e-280 && P > 0.0) ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K)) : 0.0;
+  if (!isfinite(x) || !isfinite(beta)) return o;
+  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
+  double iota = flag > 0 ? __dsub_rn(ep, em) : __dsub_rn(em, ep);
+  if (iota < 0.0) iota = 0.0;
+  o.x = x;
+  o.beta = beta;
+  o.iota = iota;
+  if (beta < __dmul_rn(iota, 1.0 - kEpsS)) {
+    o.status = Q_BELOW;
+    return o;
+  }
+  const double beta_otm = (flag * x > 0.0) ? __dsub_rn(beta, iota) : beta;
+  const double bmax = __dadd_rn(1.0, x > 0.0 ? em : ep);
+  if (beta_otm >= __dmul_rn(bmax, 1.0 - kEpsS)) {
+    o.status = Q_ABOVE;
+    return o;
+  }
+  o.status = Q_OK;
+  o.beta_otm = beta_otm;
+  o.x_otm = -fabs(x);
+  o.bmax = bmax;
+  o.solve = beta_otm > __dmul_rn(iota, kEpsS);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// normalised Black function
+// ---------------------------------------------------------------------------
+template <typename T>
+struct NB {
+  T e;      // exp(-(h^2+t^2)/2)
+  T B;      // b/e (or (b_max - b)/e for the complement)
+  T h, t, inv_s;
+};
+
+// Odd part of R(h+t) - R(h-t) divided by 2: sum_k R^{(2k+1)}(h) t^{2k+1}/(2k+1)!
+// with R^{(n)} = P_n(h) + Q_n(h) R.  P_{2k+1} is even in h, Q_{2k+1} odd; the
+// coefficients below are P_{2k+1}(h) and Q_{2k+1}(h)/h as polynomials in h^2,
+// each divided by (2k+1)!.
+template <typename T>
+__device__ __forceinline__ T small_t_series(T h, T t, T R) {
+  const T u = h * h, w = t * t;
+  // k = 0: P1 = 1, Q1/h = 1
+  // k = 1: P3 = 2 + u, Q3/h = 3 + u                       (/3!)
+  // k = 2: P5 = 8 + 9u + u^2, Q5/h = 15 + 10u + u^2       (/5!)
+  // k = 3: P7 = 48 + 87u + 20u^2 + u^3,
+  //        Q7/h = 105 + 105u + 21u^2 + u^3                (/7!)
+  // k = 4: P9 = 384 + 975u + 345u^2 + 35u^3 + u^4,
+  //        Q9/h = 945 + 1260u + 378u^2 + 36u^3 + u^4      (/9!)
+  // k = 5: P11 = 3840 + 12645u + 6090u^2 + 938u^3 + 54u^4 + u^5,
+  //        Q11/h = 10395 + 17325u + 6930u^2 + 990u^3 + 55u^4 + u^5   (/11!)
+  const T p1 = T(1), q1 = T(1);
+  const T p3 = (T(2) + u) * T(1.0 / 6.0), q3 = (T(3) + u) * T(1.0 / 6.0);
+  const T p5 = (T(8) + u * (T(9) + u)) * T(1.0 / 120.0);
+  const T q5 = (T(15) + u * (T(10) + u)) * T(1.0 / 120.0);
+  const T p7 = (T(48) + u * (T(87) + u * (T(20) + u))) * T(1.0 / 5040.0);
+  const T q7 = (T(105) + u * (T(105) + u * (T(21) + u))) * T(1.0 / 5040.0);
+  T A, C;
+  if (Prec<T>::terms >= 6) {
+    const T p9 = (T(384) + u * (T(975) + u * (T(345) + u * (T(35) + u)))) * T(1.0 / 362880.0);
+    const T q9 = (T(945) + u * (T(1260) + u * (T(378) + u * (T(36) + u)))) * T(1.0 / 362880.0);
+    const T p11 = (T(3840) + u * (T(12645) + u * (T(6090) + u * (T(938) + u * (T(54) + u))))) *
+                  T(1.0 / 39916800.0);
+    const T q11 = (T(10395) + u * (T(17325) + u * (T(6930) + u * (T(990) + u * (T(55) + u))))) *
+                  T(1.0 / 39916800.0);
+    A = p1 + w * (p3 + w * (p5 + w * (p7 + w * (p9 + w * p11))));
+    C = q1 + w * (q3 + w * (q5 + w * (q7 + w * (q9 + w * q11))));
+  } else {
+    A = p1 + w * (p3 + w * (p5 + w * p7));
+    C = q1 + w * (q3 + w * (q5 + w * q7));
+  }
+  return t * (A + h * R * C);
+}
+
+// b(x, s) for x <= 0 (or its complement b_max - b when comp), scaled by e.
+template <typename T>
+__device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o) {
+  o.inv_s = T(1) / s;
+  o.h = x * o.inv_s;
+  o.t = T(0.5) * s;
+  const T h = o.h, t = o.t;
+  o.e = f_exp(T(-0.5) * (h * h + t * t));
+  const bool small = (t < Prec<T>::t_small) && !comp;
+  const T a1 = small ? -h * T(kInvSqrt2) : (comp ? (h + t) : -(h + t)) * T(kInvSqrt2);
+  const T Y1 = f_erfcx(a1);
+  if (small) {
+    if (f_abs(h) < Prec<T>::h_asym) {
+      o.B = T(kSqrt2OverPi) * small_t_series<T>(h, t, T(kSqrtPiOver2) * Y1);
+    } else {
+      // R(z) ~ 1/|z| - 1/|z|^3 for z -> -inf: with a = |h|, D = a^2 - t^2,
+      // [R(h+t) - R(h-t)]/2 = (t/D) (1 - (3a^2 + t^2)/D^2) + O(t/a^6)
+      const T D = h * h - t * t;
+      o.B = T(kSqrt2OverPi) * (t / D) * (T(1) - (T(3) * h * h + t * t) / (D * D));
+    }
+  } else {
+    const T Y2 = f_erfcx((t - h) * T(kInvSqrt2));
+    o.B = comp ? T(0.5) * (Y1 + Y2) : T(0.5) * (Y1 - Y2);
+  }
+}
+
+// ln of the value nb_eval describes
+template <typename T>
+__device__ __forceinline__ T nb_log(const NB<T>& v) {
+  return T(-0.5) * (v.h * v.h + v.t * v.t) + f_log(v.B);
+}
+
+// full normalised Black b(x, s, theta) for any x, s >= 0 (FP64)
+__device__ __forceinline__ double normalised_black(double x, double s, int theta) {
+  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
+  const double iota = (theta * x > 0.0) ? fabs(ep - em) : 0.0;
+  if (!(s > 0.0)) return iota;
+  NB<double> v;
+  nb_eval<double>(-fabs(x), s, false, v);
+  return iota + v.e * v.B;
+}
+
+// ---------------------------------------------------------------------------
+// "Let's Be Rational" (Section 2.2): boundaries, guess, objective, HH(3)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T hermite_guess(T beta, T b0, T b1, T s0, T s1, T d0, T d1) {
+  const T db = b1 - b0;
+  if (!(db > T(0))) return T(0.5) * (s0 + s1);
+  const T tau = (beta - b0) / db, tau2 = tau * tau, tau3 = tau2 * tau;
+  const T h00 = T(2) * tau3 - T(3) * tau2 + T(1), h10 = tau3 - T(2) * tau2 + tau;
+  const T h01 = T(-2) * tau3 + T(3) * tau2, h11 = tau3 - tau2;
+  return h00 * s0 + h10 * db * d0 + h01 * s1 + h11 * db * d1;
+}
+
+// inverse normal CDF of p = e^{ln_p} (p < 1/2), with the tail asymptote
+// z^2 = L - ln(L) - ln(2 pi), L = -2 ln p, where p underflows the type.
+template <typename T>
+__device__ __forceinline__ T ncdfinv_log(T ln_p) {
+  if (ln_p > Prec<T>::ln_p_floor) return f_ncdfinv(f_exp(ln_p));
+  const T L = T(-2) * ln_p;
+  return -f_sqrt(L - f_log(L) - T(kLn2Pi));
+}
+
+// Quantities the solver needs besides (beta, x): ln beta and b_max - beta
+// (both from FP64 when T is float), and b_max = e^{x/2}.
+template <typename T>
+struct Reduced {
+  T beta, ln_beta, c_beta, x, bmax;
+};
+
+template <typename T>
+struct Objective {
+  T nu, h2, h3;  // -g/g', g''/g', g'''/g'
+};
+
+// Householder(3) ingredients for the three-branch objective of Section 2.2:
+//   region 0 (lowest):        g = 1/ln b - 1/ln beta
+//   regions 1, 2 (middle):    g = b - beta
+//   region 3 (highest):       g = ln((b_max - beta)/(b_max - b))
+template <typename T>
+__device__ __forceinline__ Objective<T> objective(const Reduced<T>& q, T s, int reg) {
+  NB<T> v;
+  nb_eval<T>(q.x, s, reg == 3, v);
+  const T hh = v.h * v.h;
+  const T u = hh * v.inv_s - T(0.25) * s;                    // b''/b'
+  const T du = T(-3) * hh * v.inv_s * v.inv_s - T(0.25);     // d(b''/b')/ds
+  Objective<T> o;
+  if (reg == 1 || reg == 2) {
+    const T b = v.e * v.B, bp = v.e * T(kInvSqrt2Pi);
+    o.nu = (q.beta - b) / bp;
+    o.h2 = u;
+    o.h3 = u * u + du;
+  } else {
+    const T lnX = nb_log(v);
+    const T qw = T(kInvSqrt2Pi) / v.B;  // b'/b (region 0) or b'/(b_max - b) (region 3)
+    if (reg == 0) {
+      const T iL = T(1) / lnX, k1 = T(1) + T(2) * iL;
+      const T g = iL - T(1) / q.ln_beta;
+      o.nu = g * lnX * lnX / qw;
+      o.h2 = u - qw * k1;
+      o.h3 = o.h2 * o.h2 + du - (qw * u - qw * qw) * k1 + T(2) * qw * qw * iL * iL;
+    } else {
+      const T g = f_log(q.c_beta) - lnX;
+      o.nu = -g / qw;
+      o.h2 = u + qw;
+      o.h3 = o.h2 * o.h2 + du + qw * o.h2;
+    }
+  }
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ T hh3_step(const Objective<T>& o) {
+  const T ds = o.nu * (T(1) + T(0.5) * o.h2 * o.nu) / (T(1) + o.nu * (o.h2 + o.h3 * o.nu / T(6)));
+  return f_finite(ds) ? ds : o.nu;
+}
+
+template <typename T>
+__device__ __forceinline__ T guarded(T s, T ds) {
+  return (s + ds <= T(0.25) * s) ? T(0.25) * s : s + ds;
+}
+
+// Boundaries (six normalised-Black values: b and b' at s_l, s_c, s_h, of which
+// b' at s_c is closed form and only the side of s_c that beta falls on is
+// evaluated), the four-region initial guess, and the region index.
+template <typename T>
+__device__ __forceinline__ T lbr_guess(const Reduced<T>& q, int& reg) {
+  const T x = q.x, beta = q.beta, bmax = q.bmax;
+  const bool xneg = x < T(0);
+  // inflection point s_c = sqrt(2|x|), where h + t = 0 and b'(s_c) = e^{x/2}/sqrt(2 pi)
+  const T sc_eval = xneg ? f_sqrt(T(-2) * x) : T(1);
+  NB<T> vc_;
+  nb_eval<T>(x, sc_eval, false, vc_);
+  const T sc = xneg ? sc_eval : T(0);
+  const T bc = xneg ? vc_.e * vc_.B : T(0);
+  const T vc = bmax * T(kInvSqrt2Pi);
+  // tangent at s_c meets 0 at s_l and b_max at s_h; beta picks one side
+  const bool lower = beta <= bc;
+  T so = lower ? sc - bc / vc : sc + (bmax - bc) / vc;
+  const bool degenerate = !(so > T(0));  // s_l lost to rounding next to x = 0
+  if (degenerate) so = sc > T(0) ? sc : T(1);
+  NB<T> vo_;
+  nb_eval<T>(x, so, false, vo_);
+  const T bo = degenerate ? T(0) : vo_.e * vo_.B;
+  const T vo = vo_.e * T(kInvSqrt2Pi);
+  const T ln_bo = nb_log(vo_);
+  if (lower)
+    reg = (!degenerate && q.ln_beta < ln_bo) ? 0 : 1;
+  else
+    reg = (beta <= bo) ? 2 : 3;
+  T s;
+  if (reg == 1 || reg == 2) {
+    // cubic Hermite of s(beta) with slopes 1/b' on the inflection-bounded interior
+    T b0, b1, s0, s1, d0, d1;
+    if (reg == 1) {
+      b0 = bo; b1 = bc; s0 = degenerate ? T(0) : so; s1 = sc;
+      d1 = T(1) / vc;
+      d0 = degenerate ? sc / bc : T(1) / vo;
+      if (degenerate) d1 = d0;
+    } else {
+      b0 = bc; b1 = bo; s0 = sc; s1 = so;
+      d0 = T(1) / vc;
+      d1 = T(1) / vo;
+    }
+    s = hermite_guess(beta, b0, b1, s0, s1, d0, d1);
+  } else {
+    // wings: invert the limiting form, scaled to match b at the boundary
+    //   lowest:  b ~ c Phi(-|x|/(sqrt3 s))^3   (s -> 0)
+    //   highest: b_max - b ~ c' Phi(-s/2)       (s -> inf)
+    const T za = (reg == 0) ? -f_abs(x) * T(kInvSqrt3) / so : T(-0.5) * so;
+    const T Pa = f_ncdf(za);
+    const T ln_p = (reg == 0) ? f_log(Pa) + (q.ln_beta - ln_bo) * T(1.0 / 3.0)
+                              : f_log(q.c_beta * Pa / (bmax - bo));
+    const T z = ncdfinv_log<T>(ln_p);
+    s = (reg == 0) ? f_abs(x) * T(kInvSqrt3) / f_abs(z) : T(-2) * z;
+  }
+  if (!(s > T(0)) || !f_finite(s)) s = (so > T(0)) ? so : T(1);
+  return s;
+}
+
+// LBR solve: guess, n_min Householder(3) steps, then up to n_max while the
+// last step still moved s by more than conv_tol relative.
+template <typename T>
+__device__ __forceinline__ T lbr_solve(const Reduced<T>& q, int n_min, int n_max, T conv_tol,
+                                       int& reg) {
+  T s = lbr_guess<T>(q, reg);
+  for (int k = 0; k < n_max; k++) {
+    const Objective<T> o = objective<T>(q, s, reg);
+    const T ds = hh3_step<T>(o);
+    s = guarded<T>(s, ds);
+    if (k + 1 >= n_min && !(f_abs(ds) > conv_tol * s)) break;
+  }
+  return s;
+}
+
+__device__ __forceinline__ Reduced<double> reduced64(const Norm& n) {
+  Reduced<double> q;
+  q.beta = n.beta_otm;
+  // out of the money, beta_otm = beta and the direct logarithm applies
+  q.ln_beta = (n.ln_beta != 0.0 && n.beta_otm == n.beta) ? n.ln_beta : log(n.beta_otm);
+  q.c_beta = n.bmax - n.beta_otm;
+  q.x = n.x_otm;
+  q.bmax = n.bmax;
+  return q;
+}
+
+__device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
+  Reduced<float> f;
+  f.beta = (float)q.beta;
+  f.ln_beta = (float)q.ln_beta;
+  f.c_beta = (float)q.c_beta;
+  f.x = (float)q.x;
+  f.bmax = (float)q.bmax;
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Halley x8 + fallback (Section 2.2, second item), FP64
+// ---------------------------------------------------------------------------
+constexpr int kHalleySteps = 8;
+constexpr double kHalleyConvTol = 1e-10;
+
+struct HalleyOut {
+  double s, lo, hi;
+  bool converged;
+};
+
+__device__ __forceinline__ HalleyOut halley_solve(double beta, double x) {
+  double s = kSqrt2Pi * beta;  // Brenner-Subrahmanyam: b ~ s/sqrt(2 pi) at the money
+  double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
+  for (int k = 0; k < kHalleySteps; k++) {
+    NB<double> v;
+    nb_eval<double>(x, s, false, v);
+    const double g = v.e * v.B - beta;
+    if (g < 0.0) {
+      lo = s;
+    } else if (g > 0.0) {
+      hi = s;
+    } else {
+      // g == 0 is the root; a NaN residual leaves the quote unconverged
+      nerr = (g == 0.0) ? 0.0 : hi;
+      break;
+    }
+    const double bp = v.e * kInvSqrt2Pi;
+    const double u = v.h * v.h * v.inv_s - 0.25 * s;
+    // Newton distance to the root relative to s: the convergence test
+    nerr = fabs(g / bp) / s;
+    const double step = -2.0 * g / (2.0 * bp - g * u);
+    double sn = s + step;
+    if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
+    s = sn;
+  }
+  HalleyOut o;
+  o.s = s;
+  o.lo = lo;
+  o.hi = hi;
+  o.converged = isfinite(s) && s > 0.0 && nerr <= kHalleyConvTol;
+  return o;
+}
+
+// bisection on ln b - ln beta in [lo, hi], Newton steps kept when inside
+__device__ __forceinline__ double bisect_fallback(double beta, double x, double lo, double hi) {
+  const double eps = 2.220446049250313e-16;
+  const double ln_beta = log(beta);
+  NB<double> v;
+  if (!isfinite(hi)) {
+    hi = lo > 0.0 ? 2.0 * lo : 1.0;
+    for (int it = 0; it < 64; it++) {
+      nb_eval<double>(x, hi, false, v);
+      if (nb_log(v) > ln_beta) break;
+      lo = hi;
+      hi *= 2.0;
+    }
+  }
+  if (!(lo > 0.0)) {
+    lo = 0.5 * hi;
+    for (int it = 0; it < 1100; it++) {
+      nb_eval<double>(x, lo, false, v);
+      if (nb_log(v) < ln_beta) break;
+      hi = lo;
+      lo *= 0.5;
+    }
+  }
+  double s = 0.5 * (lo + hi);
+  for (int it = 0; it < 200; it++) {
+    nb_eval<double>(x, s, false, v);
+    const double f = nb_log(v) - ln_beta;
+    if (f < 0.0)
+      lo = s;
+    else if (f > 0.0)
+      hi = s;
+    else
+      break;
+    const double qw = kInvSqrt2Pi / v.B;
+    const double sn = s - f / qw;
+    const double next = (sn > lo && sn < hi) ? sn : 0.5 * (lo + hi);
+    const double ds = next - s;
+    s = next;
+    if (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi) break;
+  }
+  return s;
+}
+
+}  // namespace fvd

@@ -1,0 +1,67 @@
+// fv_internal.h -- host-side interface between the C ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace fvk {
+
+enum Prec { P_FP64 = 0, P_MIXED = 1, P_FP32 = 2 };
+
+struct IvArgs {
+  int model;
+  bool f32_inputs;  // price, S_or_F, K, T, r, q point to float when true
+  const void *P, *SF, *K, *T, *r, *q;
+  const int8_t* flag;
+  int64_t n;
+  double* sigma;
+  uint8_t* status;
+};
+
+// grid sizing: blocks for n quotes, capped at `per_sm` resident blocks per SM
+int sm_count();
+int grid_for(int64_t n, int block, int per_sm);
+
+cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
+
+// Halley workspace: [count u32 | pad to 16][idx u32 x n | pad to 16][lo f64 x n][hi f64 x n]
+size_t halley_workspace_bytes(int64_t n);
+cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st);
+
+cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const double* K,
+                         const double* T, const double* r, const double* q, const double* sigma,
+                         int64_t n, double* out, cudaStream_t st);
+cudaError_t launch_greeks(int model, const int8_t* flag, const double* SF, const double* K,
+                          const double* T, const double* r, const double* q, const double* sigma,
+                          int64_t n, double* delta, double* gamma, double* vega, double* theta,
+                          double* rho, cudaStream_t st);
+cudaError_t launch_adjoint(int model, const double* P, const double* SF, const double* K,
+                           const double* T, const double* r, const double* q, const int8_t* flag,
+                           const double* sigma, const uint8_t* status, const double* gsig,
+                           int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
+                           double* gq, cudaStream_t st);
+cudaError_t launch_normalised_black(const double* x, const double* s, const int8_t* theta,
+                                    int64_t n, double* out, cudaStream_t st);
+
+// chains: device descriptor and tile table entry
+struct ChainDesc {
+  const double* P;
+  const double* K;
+  const int8_t* flag;
+  double* sigma;
+  uint8_t* status;
+  int64_t n;
+  double SF, T, r, q;
+};
+struct Tile {
+  int32_t chain;
+  int32_t pad;
+  int64_t offset;
+};
+cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
+                          int block, int qpt, int grid, cudaStream_t st);
+int chains_max_blocks_per_sm(int block);
+
+}  // namespace fvk

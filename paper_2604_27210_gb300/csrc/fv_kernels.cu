@@ -1,0 +1,443 @@
+// fv_kernels.cu -- CUDA kernels (sm_103a) of the implied-volatility library.
+//
+// One thread per quote, grid-stride loops over structure-of-arrays inputs (a
+// warp reads 32 consecutive elements of each array: fully coalesced).  The
+// work per quote is transcendental FP64 arithmetic, so the kernels are bound
+// by the FP64 pipe, not by HBM; no tensor cores are involved.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+namespace fvk {
+
+using namespace fvd;
+
+namespace {
+int g_sm_count[64] = {0};
+}
+
+int sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (g_sm_count[dev] <= 0) {
+    int c = 0;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0)
+      c = 1;
+    g_sm_count[dev] = c;
+  }
+  return g_sm_count[dev];
+}
+
+int grid_for(int64_t n, int block, int per_sm) {
+  const int64_t need = (n + block - 1) / block;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  return (int)std::max<int64_t>(1, std::min(need, cap));
+}
+
+template <typename InT>
+__device__ __forceinline__ double ld(const void* p, int64_t i) {
+  return (double)__ldg(static_cast<const InT*>(p) + i);
+}
+
+// ---------------------------------------------------------------------------
+// implied volatility, LBR: FP64, mixed (FP32 bulk + one FP64 HH3 step), FP32
+// ---------------------------------------------------------------------------
+template <typename InT, int PREC>
+__global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
+    const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
+    const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
+    const int flag = a.flag[i];
+    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    double sigma = qnan();
+    if (nq.status == Q_OK) {
+      if (!nq.solve) {
+        sigma = 0.0;
+      } else {
+        const Reduced<double> q64 = reduced64(nq);
+        int reg = 1;
+        double s;
+        if (PREC == P_FP64) {
+          // two Householder(3) steps, a third where the second still moved s
+          // by more than 2^-20 (quartic convergence: a smaller second step
+          // leaves an error far below one ulp)
+          s = lbr_solve<double>(q64, 2, 3, 0x1p-20, reg);
+        } else {
+          const float s32 = lbr_solve<float>(reduced32(q64), 2, 2, 0.0f, reg);
+          s = (double)s32;
+          if (PREC == P_MIXED) {
+            const Objective<double> o = objective<double>(q64, s, reg);
+            s = guarded<double>(s, hh3_step<double>(o));
+          }
+        }
+        sigma = s / sqrt(T);
+      }
+    }
+    a.sigma[i] = sigma;
+    a.status[i] = (uint8_t)nq.status;
+  }
+}
+
+cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
+  const int block = 256;
+  const int grid = grid_for(a.n, block, 8);
+#define FV_LBR_CASE(IT, P) k_iv_lbr<IT, P><<<grid, block, 0, st>>>(a)
+  if (a.f32_inputs) {
+    if (prec == P_FP64) FV_LBR_CASE(float, P_FP64);
+    else if (prec == P_MIXED) FV_LBR_CASE(float, P_MIXED);
+    else FV_LBR_CASE(float, P_FP32);
+  } else {
+    if (prec == P_FP64) FV_LBR_CASE(double, P_FP64);
+    else if (prec == P_MIXED) FV_LBR_CASE(double, P_MIXED);
+    else FV_LBR_CASE(double, P_FP32);
+  }
+#undef FV_LBR_CASE
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// implied volatility, Halley x8 + compacted bisection fallback
+// ---------------------------------------------------------------------------
+size_t halley_workspace_bytes(int64_t n) {
+  const size_t idx_bytes = ((size_t)n * 4 + 15) / 16 * 16;
+  return 16 + idx_bytes + (size_t)n * 16;
+}
+
+struct HalleyWs {
+  unsigned int* count;
+  unsigned int* idx;
+  double* lo;
+  double* hi;
+};
+
+static HalleyWs halley_ws(void* ws, int64_t n) {
+  char* p = static_cast<char*>(ws);
+  HalleyWs w;
+  w.count = reinterpret_cast<unsigned int*>(p);
+  w.idx = reinterpret_cast<unsigned int*>(p + 16);
+  const size_t idx_bytes = ((size_t)n * 4 + 15) / 16 * 16;
+  w.lo = reinterpret_cast<double*>(p + 16 + idx_bytes);
+  w.hi = w.lo + n;
+  return w;
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
+    const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
+    const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
+    const int flag = a.flag[i];
+    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    double sigma = qnan();
+    bool fallback = false;
+    double lo = 0.0, hi = 0.0;
+    if (nq.status == Q_OK) {
+      if (!nq.solve) {
+        sigma = 0.0;
+      } else {
+        const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm);
+        if (h.converged) {
+          sigma = h.s / sqrt(T);
+        } else {
+          fallback = true;
+          lo = h.lo;
+          hi = h.hi;
+        }
+      }
+    }
+    a.sigma[i] = sigma;
+    a.status[i] = (uint8_t)nq.status;
+    // warp-aggregated append of the quotes that failed the convergence test
+    const unsigned active = __activemask();
+    const unsigned m = __ballot_sync(active, fallback);
+    if (m) {
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(m) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(w.count, (unsigned)__popc(m));
+      base = __shfl_sync(active, base, leader);
+      if (fallback) {
+        const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+        w.idx[pos] = (unsigned)i;
+        w.lo[pos] = lo;
+        w.hi[pos] = hi;
+      }
+    }
+  }
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
+  const int64_t cnt = (int64_t)*w.count;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += stride) {
+    const int64_t i = w.idx[k];
+    const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
+    const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
+    const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
+    const Norm nq = decide(a.model, P, SF, K, T, r, q, a.flag[i]);
+    const double s = bisect_fallback(nq.beta_otm, nq.x_otm, w.lo[k], w.hi[k]);
+    a.sigma[i] = s / sqrt(T);
+  }
+}
+
+cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st) {
+  const HalleyWs w = halley_ws(ws, a.n);
+  cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  const int block = 256;
+  const int grid = grid_for(a.n, block, 8);
+  if (a.f32_inputs) {
+    k_iv_halley<float><<<grid, block, 0, st>>>(a, w);
+    k_halley_fallback<float><<<grid, block, 0, st>>>(a, w);
+  } else {
+    k_iv_halley<double><<<grid, block, 0, st>>>(a, w);
+    k_halley_fallback<double><<<grid, block, 0, st>>>(a, w);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// price, Greeks, adjoint, normalised Black
+// ---------------------------------------------------------------------------
+// e^{-rT} sqrt(F K) for the model
+__device__ __forceinline__ double price_scale(int model, double SF, double K, double T, double r,
+                                              double q) {
+  if (model == M_BLACK76) return exp(-r * T) * sqrt(SF * K);
+  const double qq = model == M_BSM ? q : 0.0;
+  return exp(-0.5 * (r + qq) * T) * sqrt(SF * K);
+}
+
+__global__ void __launch_bounds__(256)
+    k_price(int model, const int8_t* flag, const double* SF, const double* K, const double* T,
+            const double* r, const double* q, const double* sigma, int64_t n, double* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double sf = SF[i], k = K[i], t = T[i], rr = r[i], qq = (model == M_BSM) ? q[i] : 0.0;
+    const double sg = sigma[i];
+    const int th = flag[i];
+    double p = qnan();
+    if (inputs_valid(model, sf, k, t, rr, qq, th) && isfinite(sg) && sg >= 0.0) {
+      const double x = model_x(model, sf, k, t, rr, qq);
+      p = price_scale(model, sf, k, t, rr, qq) * normalised_black(x, sg * sqrt(t), th);
+    }
+    out[i] = p;
+  }
+}
+
+cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const double* K,
+                         const double* T, const double* r, const double* q, const double* sigma,
+                         int64_t n, double* out, cudaStream_t st) {
+  const int block = 256;
+  k_price<<<grid_for(n, block, 8), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, out);
+  return cudaGetLastError();
+}
+
+// d1, the two normal CDFs and the density at d1, shared by Greeks and adjoint
+struct D12 {
+  double d1, s, N1, N2, n1;
+};
+__device__ __forceinline__ D12 d12(double x, double s, int th) {
+  D12 o;
+  o.s = s;
+  o.d1 = x / s + 0.5 * s;
+  const double d2 = o.d1 - s;
+  o.N1 = normcdf(th * o.d1);
+  o.N2 = normcdf(th * d2);
+  o.n1 = kInvSqrt2Pi * exp(-0.5 * o.d1 * o.d1);
+  return o;
+}
+
+__global__ void __launch_bounds__(256)
+    k_greeks(int model, const int8_t* flag, const double* SF, const double* K, const double* T,
+             const double* r, const double* q, const double* sigma, int64_t n, double* delta,
+             double* gamma, double* vega, double* theta, double* rho) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double sf = SF[i], k = K[i], t = T[i], rr = r[i], qq = (model == M_BSM) ? q[i] : 0.0;
+    const double sg = sigma[i];
+    const int th = flag[i];
+    double gd = qnan(), gg = qnan(), gv = qnan(), gt = qnan(), gr = qnan();
+    if (inputs_valid(model, sf, k, t, rr, qq, th) && isfinite(sg) && sg > 0.0) {
+      const double sq = sqrt(t), s = sg * sq;
+      const double x = model_x(model, sf, k, t, rr, qq);
+      const D12 d = d12(x, s, th);
+      const double Dr = exp(-rr * t);
+      if (model == M_BLACK76) {
+        const double V = Dr * sqrt(sf * k) * normalised_black(x, s, th);
+        gd = th * Dr * d.N1;
+        gg = Dr * d.n1 / (sf * s);
+        gv = sf * Dr * d.n1 * sq * 0.01;
+        gt = (-sf * Dr * d.n1 * sg / (2.0 * sq) + rr * V) / 365.0;
+        gr = -t * V * 0.01;
+      } else {
+        const double Dq = exp(-qq * t);
+        gd = th * Dq * d.N1;
+        gg = Dq * d.n1 / (sf * s);
+        gv = sf * Dq * d.n1 * sq * 0.01;
+        gt = (-sf * Dq * d.n1 * sg / (2.0 * sq) - th * rr * k * Dr * d.N2 +
+              th * qq * sf * Dq * d.N1) / 365.0;
+        gr = th * k * t * Dr * d.N2 * 0.01;
+      }
+    }
+    if (delta) delta[i] = gd;
+    if (gamma) gamma[i] = gg;
+    if (vega) vega[i] = gv;
+    if (theta) theta[i] = gt;
+    if (rho) rho[i] = gr;
+  }
+}
+
+cudaError_t launch_greeks(int model, const int8_t* flag, const double* SF, const double* K,
+                          const double* T, const double* r, const double* q, const double* sigma,
+                          int64_t n, double* delta, double* gamma, double* vega, double* theta,
+                          double* rho, cudaStream_t st) {
+  const int block = 256;
+  k_greeks<<<grid_for(n, block, 8), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, delta,
+                                                     gamma, vega, theta, rho);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256)
+    k_adjoint(int model, const double* P, const double* SF, const double* K, const double* T,
+              const double* r, const double* q, const int8_t* flag, const double* sigma,
+              const uint8_t* status, const double* gsig, int64_t n, double* gP, double* gS,
+              double* gK, double* gT, double* gr, double* gq) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double oP = 0.0, oS = 0.0, oK = 0.0, oT = 0.0, orr = 0.0, oq = 0.0;
+    const double sg = sigma[i];
+    if (status[i] == Q_OK && isfinite(sg) && sg > 0.0) {
+      const double sf = SF[i], k = K[i], t = T[i], rr = r[i], qq = (model == M_BSM) ? q[i] : 0.0;
+      const int th = flag[i];
+      if (inputs_valid(model, sf, k, t, rr, qq, th)) {
+        const double sq = sqrt(t), s = sg * sq;
+        const double x = model_x(model, sf, k, t, rr, qq);
+        const D12 d = d12(x, s, th);
+        const double Dr = exp(-rr * t);
+        double vega, VS, VK, VT, Vr, Vq = 0.0;
+        if (model == M_BLACK76) {
+          const double V = P[i];
+          vega = sf * Dr * d.n1 * sq;
+          VS = th * Dr * d.N1;
+          VK = -th * Dr * d.N2;
+          VT = -rr * V + Dr * sf * d.n1 * sg / (2.0 * sq);
+          Vr = -t * V;
+        } else {
+          const double Dq = exp(-qq * t);
+          vega = sf * Dq * d.n1 * sq;
+          VS = th * Dq * d.N1;
+          VK = -th * Dr * d.N2;
+          VT = sf * Dq * d.n1 * sg / (2.0 * sq) - th * qq * sf * Dq * d.N1 +
+               th * rr * k * Dr * d.N2;
+          Vr = th * k * t * Dr * d.N2;
+          Vq = (model == M_BSM) ? -th * sf * t * Dq * d.N1 : 0.0;
+        }
+        if (vega > 0.0) {
+          const double g = gsig[i] / vega;
+          oP = g;
+          oS = -g * VS;
+          oK = -g * VK;
+          oT = -g * VT;
+          orr = -g * Vr;
+          oq = -g * Vq;
+        }
+      }
+    }
+    if (gP) gP[i] = oP;
+    if (gS) gS[i] = oS;
+    if (gK) gK[i] = oK;
+    if (gT) gT[i] = oT;
+    if (gr) gr[i] = orr;
+    if (gq) gq[i] = oq;
+  }
+}
+
+cudaError_t launch_adjoint(int model, const double* P, const double* SF, const double* K,
+                           const double* T, const double* r, const double* q, const int8_t* flag,
+                           const double* sigma, const uint8_t* status, const double* gsig,
+                           int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
+                           double* gq, cudaStream_t st) {
+  const int block = 256;
+  k_adjoint<<<grid_for(n, block, 8), block, 0, st>>>(model, P, SF, K, T, r, q, flag, sigma, status,
+                                                      gsig, n, gP, gS, gK, gT, gr, gq);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_nb(const double* x, const double* s, const int8_t* theta,
+                                            int64_t n, double* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int th = theta[i];
+    const double xv = x[i], sv = s[i];
+    out[i] = (th == 1 || th == -1) && isfinite(xv) && !isnan(sv) ? normalised_black(xv, sv, th)
+                                                                  : qnan();
+  }
+}
+
+cudaError_t launch_normalised_black(const double* x, const double* s, const int8_t* theta,
+                                    int64_t n, double* out, cudaStream_t st) {
+  const int block = 256;
+  k_nb<<<grid_for(n, block, 8), block, 0, st>>>(x, s, theta, n, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batches of chains: persistent CTAs walk a static tile table
+// ---------------------------------------------------------------------------
+template <int QPT>
+__global__ void __launch_bounds__(512) k_chains(int model, const ChainDesc* __restrict__ chains,
+                                                const Tile* __restrict__ tiles, int64_t n_tiles) {
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const Tile tl = tiles[tile];
+    const ChainDesc c = chains[tl.chain];
+#pragma unroll
+    for (int k = 0; k < QPT; k++) {
+      const int64_t j = tl.offset + (int64_t)k * blockDim.x + threadIdx.x;
+      if (j < c.n) {
+        const Norm nq = decide(model, c.P[j], c.SF, c.K[j], c.T, c.r, c.q, c.flag[j]);
+        double sigma = qnan();
+        if (nq.status == Q_OK) {
+          if (!nq.solve) {
+            sigma = 0.0;
+          } else {
+            int reg = 1;
+            const double s = lbr_solve<double>(reduced64(nq), 2, 3, 0x1p-20, reg);
+            sigma = s / sqrt(c.T);
+          }
+        }
+        c.sigma[j] = sigma;
+        c.status[j] = (uint8_t)nq.status;
+      }
+    }
+  }
+}
+
+int chains_max_blocks_per_sm(int block) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chains<1>, block, 0) != cudaSuccess ||
+      b <= 0)
+    b = 1;
+  return b;
+}
+
+cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
+                          int block, int qpt, int grid, cudaStream_t st) {
+  switch (qpt) {
+    case 1: k_chains<1><<<grid, block, 0, st>>>(model, chains, tiles, n_tiles); break;
+    case 2: k_chains<2><<<grid, block, 0, st>>>(model, chains, tiles, n_tiles); break;
+    case 4: k_chains<4><<<grid, block, 0, st>>>(model, chains, tiles, n_tiles); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fvk

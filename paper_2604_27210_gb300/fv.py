@@ -1,0 +1,337 @@
+"""Thin Python binding of libfv.so (include/fv.h), same names as the C ABI.
+
+Argument marshalling only: tensors must already live on the GPU; every step of
+the computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current stream.  There is no CPU fallback: importing this module
+without a built libfv.so raises.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfv.so")
+
+FV_BLACK76, FV_BLACK_SCHOLES, FV_BSM = 0, 1, 2
+FV_LBR, FV_HALLEY = 0, 1
+FV_FP64, FV_MIXED, FV_FP32 = 0, 1, 2
+FV_DTYPE_F64, FV_DTYPE_F32 = 0, 1
+FV_Q_OK, FV_Q_BELOW_INTRINSIC, FV_Q_ABOVE_MAX, FV_Q_INVALID = 0, 1, 2, 3
+FV_SUCCESS, FV_ERR_ARG, FV_ERR_CUDA, FV_ERR_UNSUPPORTED, FV_ERR_NOMEM = 0, -1, -2, -3, -4
+
+# every symbol include/fv.h declares
+EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws",
+           "fv_implied_vol_ex", "fv_greeks", "fv_iv_adjoint", "fv_normalised_black",
+           "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
+           "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_status_string", "fv_last_error"]
+
+
+class FvError(RuntimeError):
+    def __init__(self, code, fn, detail):
+        super().__init__("%s failed (%d): %s" % (fn, code, detail))
+        self.code = code
+
+
+class fv_chain(ctypes.Structure):
+    _fields_ = [("price", ctypes.c_void_p), ("K", ctypes.c_void_p), ("flag", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("status", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("S_or_F", ctypes.c_double), ("T", ctypes.c_double), ("r", ctypes.c_double),
+                ("q", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_N = ctypes.c_int64
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libfv.so is not built (%s): run __graft_entry__.build() "
+                          "or python paper_2604_27210_gb300/build.py" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    E = ctypes.c_int
+    lib.fv_price.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P]
+    lib.fv_implied_vol.argtypes = [_I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P]
+    lib.fv_workspace_size.argtypes = [_I, _N]
+    lib.fv_workspace_size.restype = ctypes.c_size_t
+    lib.fv_implied_vol_ws.argtypes = [_I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P,
+                                      ctypes.c_size_t, _P]
+    lib.fv_implied_vol_ex.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P]
+    lib.fv_greeks.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P, _P, _P, _P]
+    lib.fv_iv_adjoint.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _N,
+                                  _P, _P, _P, _P, _P, _P, _P]
+    lib.fv_normalised_black.argtypes = [_P, _P, _P, _N, _P, _P]
+    lib.fv_chains_plan_create.argtypes = [_I, _I, ctypes.POINTER(fv_chain), _N, _I, _P,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+    lib.fv_implied_vol_chains.argtypes = [_P, _P]
+    lib.fv_implied_vol_chains_direct.argtypes = [_P, _P]
+    lib.fv_chains_plan_info.argtypes = [_P] + [ctypes.POINTER(_I)] * 3 + [ctypes.POINTER(_N)] * 2
+    lib.fv_chains_plan_destroy.argtypes = [_P]
+    lib.fv_status_string.argtypes = [_I]
+    lib.fv_status_string.restype = ctypes.c_char_p
+    lib.fv_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("fv_workspace_size", "fv_status_string", "fv_last_error"):
+            getattr(lib, name).restype = E
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    """The loaded ctypes handle of libfv.so."""
+    return _lib
+
+
+def _check(code, fn):
+    if code != FV_SUCCESS:
+        raise FvError(code, fn, _lib.fv_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, n, dtypes, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s is required" % name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype not in dtypes:
+        raise TypeError("%s has dtype %s, expected one of %s" % (name, t.dtype, dtypes))
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be contiguous with %d elements" % (name, n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_F64 = (torch.float64,)
+_F32 = (torch.float32,)
+_I8 = (torch.int8,)
+_U8 = (torch.uint8,)
+
+
+def _like(t, dtype):
+    return torch.empty(t.numel(), dtype=dtype, device=t.device)
+
+
+def fv_price(model, flag, S_or_F, K, T, r, q, sigma, out=None, stream=None):
+    n = S_or_F.numel()
+    out = _like(S_or_F, torch.float64) if out is None else out
+    _check(_lib.fv_price(model, _ptr(flag, n, _I8, "flag"), _ptr(S_or_F, n, _F64, "S_or_F"),
+                         _ptr(K, n, _F64, "K"), _ptr(T, n, _F64, "T"), _ptr(r, n, _F64, "r"),
+                         _ptr(q, n, _F64, "q", allow_none=model != FV_BSM),
+                         _ptr(sigma, n, _F64, "sigma"), n, _ptr(out, n, _F64, "out"),
+                         _stream(stream)), "fv_price")
+    return out
+
+
+def _iv_outputs(ref, out_sigma, status):
+    if out_sigma is None:
+        out_sigma = _like(ref, torch.float64)
+    if status is None:
+        status = _like(ref, torch.uint8)
+    return out_sigma, status
+
+
+def fv_implied_vol(model, solver, price, S_or_F, K, T, r, q, flag, out_sigma=None, status=None,
+                   stream=None):
+    n = price.numel()
+    out_sigma, status = _iv_outputs(price, out_sigma, status)
+    _check(_lib.fv_implied_vol(model, solver, _ptr(price, n, _F64, "price"),
+                               _ptr(S_or_F, n, _F64, "S_or_F"), _ptr(K, n, _F64, "K"),
+                               _ptr(T, n, _F64, "T"), _ptr(r, n, _F64, "r"),
+                               _ptr(q, n, _F64, "q", allow_none=model != FV_BSM),
+                               _ptr(flag, n, _I8, "flag"), n, _ptr(out_sigma, n, _F64, "out_sigma"),
+                               _ptr(status, n, _U8, "status"), _stream(stream)), "fv_implied_vol")
+    return out_sigma, status
+
+
+def fv_workspace_size(solver, n):
+    return int(_lib.fv_workspace_size(solver, n))
+
+
+def fv_implied_vol_ws(model, solver, price, S_or_F, K, T, r, q, flag, workspace, out_sigma=None,
+                      status=None, stream=None):
+    n = price.numel()
+    out_sigma, status = _iv_outputs(price, out_sigma, status)
+    if workspace is None:
+        wp, wb = None, 0
+    else:
+        if not workspace.is_cuda or not workspace.is_contiguous():
+            raise TypeError("workspace must be a contiguous CUDA tensor")
+        wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    _check(_lib.fv_implied_vol_ws(model, solver, _ptr(price, n, _F64, "price"),
+                                  _ptr(S_or_F, n, _F64, "S_or_F"), _ptr(K, n, _F64, "K"),
+                                  _ptr(T, n, _F64, "T"), _ptr(r, n, _F64, "r"),
+                                  _ptr(q, n, _F64, "q", allow_none=model != FV_BSM),
+                                  _ptr(flag, n, _I8, "flag"), n,
+                                  _ptr(out_sigma, n, _F64, "out_sigma"),
+                                  _ptr(status, n, _U8, "status"), wp, wb, _stream(stream)),
+           "fv_implied_vol_ws")
+    return out_sigma, status
+
+
+def fv_implied_vol_ex(model, solver, precision, price, S_or_F, K, T, r, q, flag, out_sigma=None,
+                      status=None, stream=None):
+    n = price.numel()
+    if price.dtype == torch.float32:
+        dt, dts = FV_DTYPE_F32, _F32
+    else:
+        dt, dts = FV_DTYPE_F64, _F64
+    out_sigma, status = _iv_outputs(price, out_sigma, status)
+    _check(_lib.fv_implied_vol_ex(model, solver, precision, dt, _ptr(price, n, dts, "price"),
+                                  _ptr(S_or_F, n, dts, "S_or_F"), _ptr(K, n, dts, "K"),
+                                  _ptr(T, n, dts, "T"), _ptr(r, n, dts, "r"),
+                                  _ptr(q, n, dts, "q", allow_none=model != FV_BSM),
+                                  _ptr(flag, n, _I8, "flag"), n,
+                                  _ptr(out_sigma, n, _F64, "out_sigma"),
+                                  _ptr(status, n, _U8, "status"), _stream(stream)),
+           "fv_implied_vol_ex")
+    return out_sigma, status
+
+
+def fv_greeks(model, flag, S_or_F, K, T, r, q, sigma, outputs=("delta", "gamma", "vega", "theta",
+                                                               "rho"), stream=None):
+    """Returns a dict name -> tensor for the requested Greeks."""
+    n = S_or_F.numel()
+    res = {k: _like(S_or_F, torch.float64) for k in outputs}
+    ptrs = [ctypes.c_void_p(res[k].data_ptr()) if k in res else None
+            for k in ("delta", "gamma", "vega", "theta", "rho")]
+    _check(_lib.fv_greeks(model, _ptr(flag, n, _I8, "flag"), _ptr(S_or_F, n, _F64, "S_or_F"),
+                          _ptr(K, n, _F64, "K"), _ptr(T, n, _F64, "T"), _ptr(r, n, _F64, "r"),
+                          _ptr(q, n, _F64, "q", allow_none=model != FV_BSM),
+                          _ptr(sigma, n, _F64, "sigma"), n, *ptrs, _stream(stream)), "fv_greeks")
+    return res
+
+
+def fv_iv_adjoint(model, price, S_or_F, K, T, r, q, flag, sigma, status, grad_sigma,
+                  outputs=("P", "S", "K", "T", "r", "q"), stream=None):
+    """Returns a dict input name -> grad_sigma * d sigma / d input."""
+    n = S_or_F.numel()
+    res = {k: _like(S_or_F, torch.float64) for k in outputs}
+    ptrs = [ctypes.c_void_p(res[k].data_ptr()) if k in res else None
+            for k in ("P", "S", "K", "T", "r", "q")]
+    _check(_lib.fv_iv_adjoint(model, _ptr(price, n, _F64, "price", allow_none=model != FV_BLACK76),
+                              _ptr(S_or_F, n, _F64, "S_or_F"), _ptr(K, n, _F64, "K"),
+                              _ptr(T, n, _F64, "T"), _ptr(r, n, _F64, "r"),
+                              _ptr(q, n, _F64, "q", allow_none=model != FV_BSM),
+                              _ptr(flag, n, _I8, "flag"), _ptr(sigma, n, _F64, "sigma"),
+                              _ptr(status, n, _U8, "status"),
+                              _ptr(grad_sigma, n, _F64, "grad_sigma"), n, *ptrs, _stream(stream)),
+           "fv_iv_adjoint")
+    return res
+
+
+def fv_normalised_black(x, s, theta, out=None, stream=None):
+    n = x.numel()
+    out = _like(x, torch.float64) if out is None else out
+    _check(_lib.fv_normalised_black(_ptr(x, n, _F64, "x"), _ptr(s, n, _F64, "s"),
+                                    _ptr(theta, n, _I8, "theta"), n, _ptr(out, n, _F64, "out"),
+                                    _stream(stream)), "fv_normalised_black")
+    return out
+
+
+class fv_chains_plan:
+    """A plan over many option chains (one persistent launch captured in a CUDA graph).
+
+    chains: list of dicts with device tensors price, K, flag, sigma, status and
+    scalars S_or_F, T, r (and q for BSM).  The tensors must outlive the plan.
+    """
+
+    def __init__(self, model, chains, solver=FV_LBR, autotune=True, stream=None):
+        arr = (fv_chain * max(1, len(chains)))()
+        self._keep = chains
+        for i, c in enumerate(chains):
+            n = c["price"].numel()
+            arr[i].price = c["price"].data_ptr() if n else None
+            arr[i].K = c["K"].data_ptr() if n else None
+            arr[i].flag = c["flag"].data_ptr() if n else None
+            arr[i].sigma = c["sigma"].data_ptr() if n else None
+            arr[i].status = c["status"].data_ptr() if n else None
+            arr[i].n = n
+            arr[i].S_or_F = float(c["S_or_F"])
+            arr[i].T = float(c["T"])
+            arr[i].r = float(c["r"])
+            arr[i].q = float(c.get("q", 0.0))
+        h = ctypes.c_void_p()
+        _check(_lib.fv_chains_plan_create(model, solver, arr, len(chains), int(bool(autotune)),
+                                          _stream(stream), ctypes.byref(h)), "fv_chains_plan_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.fv_implied_vol_chains(self._h, _stream(stream)), "fv_implied_vol_chains")
+
+    def run_direct(self, stream=None):
+        _check(_lib.fv_implied_vol_chains_direct(self._h, _stream(stream)),
+               "fv_implied_vol_chains_direct")
+
+    def info(self):
+        b, q, g = _I(), _I(), _I()
+        t, n = _N(), _N()
+        _check(_lib.fv_chains_plan_info(self._h, ctypes.byref(b), ctypes.byref(q), ctypes.byref(g),
+                                        ctypes.byref(t), ctypes.byref(n)), "fv_chains_plan_info")
+        return dict(block=b.value, quotes_per_thread=q.value, grid=g.value, tiles=t.value,
+                    quotes=n.value)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _lib.fv_chains_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fv_chains_plan_create(model, chains, solver=FV_LBR, autotune=True, stream=None):
+    return fv_chains_plan(model, chains, solver, autotune, stream)
+
+
+def fv_implied_vol_chains(plan, stream=None):
+    plan.run(stream)
+
+
+def fv_chains_plan_destroy(plan):
+    plan.destroy()
+
+
+class ImpliedVol(torch.autograd.Function):
+    """sigma = IV(P, S|F, K, T, r, q) with the library's adjoint in backward.
+
+    forward runs fv_implied_vol (FP64 LBR); backward runs fv_iv_adjoint at the
+    converged sigma (implicit-function theorem, no stored iterations).
+    """
+
+    @staticmethod
+    def forward(ctx, price, S_or_F, K, T, r, q, flag, model=FV_BSM, solver=FV_LBR):
+        sigma, status = fv_implied_vol(model, solver, price, S_or_F, K, T, r, q, flag)
+        ctx.model = model
+        ctx.has_q = q is not None
+        ctx.save_for_backward(price, S_or_F, K, T, r, q if q is not None else price, flag, sigma,
+                              status)
+        ctx.mark_non_differentiable(status)
+        return sigma, status
+
+    @staticmethod
+    def backward(ctx, grad_sigma, grad_status):
+        price, S_or_F, K, T, r, q, flag, sigma, status = ctx.saved_tensors
+        q = q if ctx.has_q else None
+        g = fv_iv_adjoint(ctx.model, price, S_or_F, K, T, r, q, flag, sigma, status,
+                          grad_sigma.contiguous())
+        return (g["P"], g["S"], g["K"], g["T"], g["r"], g["q"] if ctx.has_q else None, None, None,
+                None)
+
+
+def implied_volatility_autograd(price, S_or_F, K, T, r, q, flag, model=FV_BSM, solver=FV_LBR):
+    """Differentiable implied volatility (returns sigma; status is discarded)."""
+    return ImpliedVol.apply(price, S_or_F, K, T, r, q, flag, model, solver)[0]

@@ -1,0 +1,115 @@
+"""The C ABI without a GPU: libfv.so loads, exports every symbol include/fv.h
+declares, and rejects bad arguments before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fv.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_27210_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fv_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("fv_price", "fv_implied_vol", "fv_greeks", "fv_iv_adjoint", "fv_implied_vol_ex",
+                 "fv_chains_plan_create", "fv_implied_vol_chains", "fv_chains_plan_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2604_27210_gb300 import fv
+    assert sorted(fv.EXPORTS) == declared_symbols()
+
+
+def _p(v=0x1000):
+    return ctypes.c_void_p(v)
+
+
+def test_argument_errors_before_any_launch(lib):
+    lib.fv_implied_vol.restype = ctypes.c_int
+    lib.fv_last_error.restype = ctypes.c_char_p
+    N = ctypes.c_int64
+    p = _p()
+    # unknown model / solver, n < 0, NULL required pointers, BSM without q
+    assert lib.fv_implied_vol(9, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -1
+    assert b"unknown model" in lib.fv_last_error()
+    assert lib.fv_implied_vol(0, 9, p, p, p, p, p, None, p, N(4), p, p, None) == -1
+    assert lib.fv_implied_vol(0, 0, p, p, p, p, p, None, p, N(-3), p, p, None) == -1
+    assert b"n = -3" in lib.fv_last_error()
+    assert lib.fv_implied_vol(0, 0, p, None, p, p, p, None, p, N(4), p, p, None) == -1
+    assert b"S_or_F" in lib.fv_last_error()
+    assert lib.fv_implied_vol(2, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -1
+    assert b"q is NULL" in lib.fv_last_error()
+    # n = 0 is valid and touches nothing, even with NULL pointers
+    assert lib.fv_implied_vol(0, 0, None, None, None, None, None, None, None, N(0), None, None,
+                              None) == 0
+    lib.fv_price.restype = ctypes.c_int
+    assert lib.fv_price(5, p, p, p, p, p, None, p, N(1), p, None) == -1
+    lib.fv_greeks.restype = ctypes.c_int
+    assert lib.fv_greeks(0, p, p, p, p, p, None, p, N(-1), p, p, p, p, p, None) == -1
+    lib.fv_iv_adjoint.restype = ctypes.c_int
+    assert lib.fv_iv_adjoint(0, None, p, p, p, p, None, p, p, p, p, N(2), p, p, p, p, p, p,
+                             None) == -1  # Black-76 adjoint needs the price
+    lib.fv_implied_vol_ex.restype = ctypes.c_int
+    assert lib.fv_implied_vol_ex(0, 0, 7, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -1
+    assert lib.fv_implied_vol_ex(0, 0, 0, 5, p, p, p, p, p, None, p, N(4), p, p, None) == -1
+    # the Halley solver runs in FP64 only
+    assert lib.fv_implied_vol_ex(0, 1, 1, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -3
+
+
+def test_workspace_size_and_checks(lib):
+    lib.fv_workspace_size.restype = ctypes.c_size_t
+    lib.fv_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int64]
+    assert lib.fv_workspace_size(0, 1000) == 0
+    need = lib.fv_workspace_size(1, 1000)
+    assert need >= 1000 * 20
+    lib.fv_implied_vol_ws.restype = ctypes.c_int
+    N = ctypes.c_int64
+    p = _p()
+    # too small, NULL and misaligned workspaces are argument errors
+    assert lib.fv_implied_vol_ws(0, 1, p, p, p, p, p, None, p, N(1000), p, p, p,
+                                 ctypes.c_size_t(need - 1), None) == -1
+    assert lib.fv_implied_vol_ws(0, 1, p, p, p, p, p, None, p, N(1000), p, p, None,
+                                 ctypes.c_size_t(need), None) == -1
+    assert lib.fv_implied_vol_ws(0, 1, p, p, p, p, p, None, p, N(1000), p, p, _p(0x1008),
+                                 ctypes.c_size_t(need), None) == -1
+
+
+def test_chains_plan_argument_errors(lib):
+    from paper_2604_27210_gb300.fv import fv_chain
+    lib.fv_chains_plan_create.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    arr = (fv_chain * 2)()
+    arr[0].n = 5
+    arr[1].n = -1
+    assert lib.fv_chains_plan_create(0, 0, arr, ctypes.c_int64(2), 0, None, ctypes.byref(h)) == -1
+    assert lib.fv_chains_plan_create(0, 1, arr, ctypes.c_int64(2), 0, None, ctypes.byref(h)) == -3
+    assert lib.fv_chains_plan_create(0, 0, None, ctypes.c_int64(-1), 0, None, ctypes.byref(h)) == -1
+    lib.fv_chains_plan_destroy.restype = ctypes.c_int
+    assert lib.fv_chains_plan_destroy(None) == 0
+
+
+def test_status_strings(lib):
+    lib.fv_status_string.restype = ctypes.c_char_p
+    for code, word in ((0, b"SUCCESS"), (-1, b"ARG"), (-2, b"CUDA"), (-3, b"UNSUPPORTED"),
+                       (-4, b"NOMEM")):
+        assert word in lib.fv_status_string(code)

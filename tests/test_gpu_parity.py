@@ -1,0 +1,493 @@
+"""Parity of the CUDA library against the oracle (needs a GPU).
+
+Floating-point tolerances (spec bars, with the conditioning reading
+recorded in the design doc):
+  - sigma, FP64 paths: relative error <= 1e-12 where the normalised vega
+    b' > 1e-8 and kappa = beta / (s b') <= 1e3; elsewhere (solved quotes) the
+    error is bounded by 1e-12 + 16 eps (1 + kappa), the rounding of the FP64
+    inputs amplified by the conditioning.
+  - sigma, pure FP32 path: relative error <= 1e-5 on the same gate.
+  - price round trip: relative <= 1e-13 where b' > 1e-8.
+  - status: bit-identical for every quote.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2604_27210_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def fv():
+    from paper_2604_27210_gb300 import fv as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    return torch, torch.device("cuda:0")
+
+
+def _dev(torch_dev, a):
+    torch, dev = torch_dev
+    return torch.tensor(np.ascontiguousarray(a), device=dev)
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _iv_ref(w, model=None):
+    model = w["model"] if model is None else model
+    f = lambda k: None if w.get(k) is None else np.asarray(w[k], dtype=np.float64)
+    sig, st = orc.iv(model, f("P"), f("S_or_F"), f("K"), f("T"), f("r"), f("q"), w["flag"])
+    v, kap = orc.conditioning(model, f("P"), f("S_or_F"), f("K"), f("T"), f("r"), f("q"),
+                              w["flag"], sig)
+    return sig, st, v, kap
+
+
+def _check_sigma(got, ref, st, v, kap, tol_gate=1e-12, tol_rest=None, name=""):
+    solved = (st == orc.OK) & (ref > 0)
+    # quotes at intrinsic and failures: exact values
+    assert np.all(got[(st == orc.OK) & (ref == 0)] == 0.0), name
+    assert np.all(np.isnan(got[st != orc.OK])), name
+    assert np.all(np.isfinite(got[solved]) & (got[solved] > 0)), name
+    rel = np.abs(got[solved] - ref[solved]) / ref[solved]
+    gate = (v[solved] > 1e-8) & (kap[solved] <= 1e3)
+    if gate.any():
+        assert rel[gate].max() <= tol_gate, "%s: gated max rel %.3g" % (name, rel[gate].max())
+    if tol_rest is not None:
+        k = np.nan_to_num(kap[solved], nan=np.inf, posinf=np.inf)
+        bound = tol_rest + 16 * EPS * (1 + k)
+        bad = rel > bound
+        assert not bad.any(), "%s: %d quotes beyond the conditioning bound (worst %.3g)" % (
+            name, bad.sum(), rel[bad].max())
+    return rel, gate
+
+
+def _args(torch_dev, w, keys=("P", "S_or_F", "K", "T", "r", "q")):
+    return [None if w.get(k) is None else _dev(torch_dev, w[k]) for k in keys]
+
+
+# ---------------------------------------------------------------------------
+# normalised Black function
+# ---------------------------------------------------------------------------
+def test_normalised_black_against_binary128(fv, torch_dev):
+    xs = np.concatenate([-np.logspace(-8, np.log10(40), 60), [0.0], np.logspace(-8, np.log10(40), 60)])
+    ss = np.logspace(-4, np.log10(50), 90)
+    X, S = np.meshgrid(xs, ss, indexing="ij")
+    X, S = X.ravel(), S.ravel()
+    for th in (1, -1):
+        thv = np.full(X.size, th, np.int8)
+        ref = orc.normalised_black(X, S, thv)
+        got = _np(fv.fv_normalised_black(_dev(torch_dev, X), _dev(torch_dev, S), _dev(torch_dev, thv)))
+        m = ref > 1e-300
+        rel = np.abs(got[m] - ref[m]) / ref[m]
+        # the erfcx difference loses log10(|h|/2t) digits in the deep wing
+        assert rel.max() <= 2e-12
+        h = np.abs(X[m]) / S[m]
+        core = h < 6
+        assert rel[core].max() <= 1e-13
+    # s = 0 is the intrinsic value; s = inf the upper bound
+    x = np.array([0.3, -0.3, 0.0])
+    z = _np(fv.fv_normalised_black(_dev(torch_dev, x), _dev(torch_dev, np.zeros(3)),
+                                   _dev(torch_dev, np.ones(3, np.int8))))
+    np.testing.assert_allclose(z, np.maximum(2 * np.sinh(x / 2), 0), rtol=4 * EPS, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# implied volatility: Black-76 quotes (4,096 at the reference size)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def black76():
+    w = wl.fill_prices(wl.black76_quotes(4096, seed=0), orc.price)
+    return w, _iv_ref(w)
+
+
+@pytest.mark.parametrize("solver", ["lbr", "halley"])
+def test_iv_black76_fp64(fv, torch_dev, black76, solver):
+    w, (ref, st_ref, v, kap) = black76
+    P, F, K, T, r, _ = _args(torch_dev, w)
+    s, st = fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR if solver == "lbr" else fv.FV_HALLEY, P, F,
+                              K, T, r, None, _dev(torch_dev, w["flag"]))
+    assert np.array_equal(_np(st), st_ref)
+    _check_sigma(_np(s), ref, st_ref, v, kap, tol_rest=1e-12, name=solver)
+
+
+def test_iv_round_trip_price(fv, torch_dev, black76):
+    w, (ref, st_ref, v, kap) = black76
+    P, F, K, T, r, _ = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    s, st = fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR, P, F, K, T, r, None, flag)
+    back = _np(fv.fv_price(fv.FV_BLACK76, flag, F, K, T, r, None, s))
+    m = (st_ref == orc.OK) & (v > 1e-8) & (ref > 0)
+    rel = np.abs(back[m] - w["P"][m]) / w["P"][m]
+    assert rel.max() <= 1e-13
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_iv_black76_reduced_precision(fv, torch_dev, black76, prec):
+    w, (ref, st_ref, v, kap) = black76
+    P, F, K, T, r, _ = _args(torch_dev, w)
+    p = fv.FV_MIXED if prec == "mixed" else fv.FV_FP32
+    s, st = fv.fv_implied_vol_ex(fv.FV_BLACK76, fv.FV_LBR, p, P, F, K, T, r, None,
+                                 _dev(torch_dev, w["flag"]))
+    assert np.array_equal(_np(st), st_ref)
+    if prec == "mixed":
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=1e-12, tol_rest=1e-12, name=prec)
+    else:
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=1e-5, name=prec)
+
+
+# ---------------------------------------------------------------------------
+# BSM strike x maturity grid, 5% below intrinsic (reduced grid; full size below)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def bsm_grid_small():
+    w = wl.fill_prices(wl.bsm_grid(512, 96, seed=1), orc.price)
+    return w, _iv_ref(w)
+
+
+@pytest.mark.parametrize("mode", ["lbr", "halley", "mixed", "fp32"])
+def test_iv_bsm_grid(fv, torch_dev, bsm_grid_small, mode):
+    w, (ref, st_ref, v, kap) = bsm_grid_small
+    assert (st_ref == orc.BELOW_INTRINSIC).sum() > 0.03 * st_ref.size
+    args = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    if mode in ("lbr", "halley"):
+        s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR if mode == "lbr" else fv.FV_HALLEY, *args, flag)
+    else:
+        s, st = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR,
+                                     fv.FV_MIXED if mode == "mixed" else fv.FV_FP32, *args, flag)
+    assert np.array_equal(_np(st), st_ref)
+    if mode == "fp32":
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=1e-5, name=mode)
+    else:
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_rest=1e-12, name=mode)
+
+
+def test_iv_fp32_inputs(fv, torch_dev):
+    # FP32 inputs; the oracle inverts the same values widened to FP64
+    w = wl.black76_fp32(8192, seed=2)
+    wl.fill_prices(w, orc.price, price_dtype=np.float32)
+    ref, st_ref, v, kap = _iv_ref(w)
+    torch, dev = torch_dev
+    args = [torch.tensor(w[k], device=dev) for k in ("P", "S_or_F", "K", "T", "r")]
+    flag = _dev(torch_dev, w["flag"])
+    for prec, tol in ((fv.FV_FP64, 1e-12), (fv.FV_MIXED, 1e-12), (fv.FV_FP32, 1e-5)):
+        s, st = fv.fv_implied_vol_ex(fv.FV_BLACK76, fv.FV_LBR, prec, *args, None, flag)
+        assert np.array_equal(_np(st), st_ref)
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=tol, name=str(prec))
+
+
+# ---------------------------------------------------------------------------
+# price, Greeks, adjoint
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_price_against_oracle(fv, torch_dev, model):
+    w = wl.bsm_quotes(8192, seed=5)
+    q = w["q"] if model == 2 else None
+    ref = orc.price(model, w["S_or_F"], w["K"], w["T"], w["r"], q, w["sigma_true"], w["flag"])
+    got = _np(fv.fv_price(model, _dev(torch_dev, w["flag"]), _dev(torch_dev, w["S_or_F"]),
+                          _dev(torch_dev, w["K"]), _dev(torch_dev, w["T"]), _dev(torch_dev, w["r"]),
+                          None if q is None else _dev(torch_dev, q), _dev(torch_dev, w["sigma_true"])))
+    m = ref > 1e-300
+    assert (np.abs(got[m] - ref[m]) / ref[m]).max() <= 1e-12
+
+
+def test_price_grid_wings(fv, torch_dev, bsm_grid_small):
+    w, (ref, st_ref, v, kap) = bsm_grid_small
+    sig = np.where(w["below_mask"], 0.0, w["sigma_true"])
+    pref = orc.price(2, w["S_or_F"], w["K"], w["T"], w["r"], w["q"], sig, w["flag"])
+    got = _np(fv.fv_price(2, _dev(torch_dev, w["flag"]), *[_dev(torch_dev, w[k]) for k in
+                                                           ("S_or_F", "K", "T", "r", "q")],
+                          _dev(torch_dev, sig)))
+    m = pref > 1e-300
+    assert (np.abs(got[m] - pref[m]) / pref[m]).max() <= 2e-12
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_greeks_against_oracle(fv, torch_dev, model):
+    w = wl.bsm_quotes(4096, seed=6)
+    q = w["q"] if model == 2 else None
+    refs = orc.greeks(model, w["S_or_F"], w["K"], w["T"], w["r"], q, w["sigma_true"], w["flag"])
+    got = fv.fv_greeks(model, _dev(torch_dev, w["flag"]), _dev(torch_dev, w["S_or_F"]),
+                       _dev(torch_dev, w["K"]), _dev(torch_dev, w["T"]), _dev(torch_dev, w["r"]),
+                       None if q is None else _dev(torch_dev, q), _dev(torch_dev, w["sigma_true"]))
+    for name, ref in zip(("delta", "gamma", "vega", "theta", "rho"), refs):
+        g = _np(got[name])
+        scale = np.maximum(np.abs(ref), 1e-12)
+        assert (np.abs(g - ref) / scale).max() <= 1e-12, name
+
+
+@pytest.mark.parametrize("model", [0, 2])
+def test_adjoint_against_oracle_and_fd(fv, torch_dev, model):
+    w = wl.bsm_quotes(2048, seed=7)
+    if model == 0:
+        w["q"] = None
+    w = wl.fill_prices(w, orc.price)
+    ins = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    s, st = fv.fv_implied_vol(model, fv.FV_LBR, *ins, flag)
+    gs = _dev(torch_dev, w["grad_sigma"])
+    adj = fv.fv_iv_adjoint(model, *ins, flag, s, st, gs)
+    s_np, st_np = _np(s), _np(st)
+    refs = orc.iv_grad(model, w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["flag"], s_np, st_np,
+                       w["grad_sigma"])
+    v, kap = orc.conditioning(model, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["flag"],
+                              s_np)
+    ok = (st_np == orc.OK) & (s_np > 0) & (v > 1e-8)
+    for name, ref in zip(("P", "S", "K", "T", "r", "q"), refs):
+        g = _np(adj[name])
+        scale = np.maximum(np.abs(ref[ok]), 1e-300)
+        assert (np.abs(g[ok] - ref[ok]) / scale).max() <= 1e-11, name
+    # central finite differences of the GPU implied volatility (h = 1e-6 relative)
+    keys = ["P", "S_or_F", "K", "T", "r"] + (["q"] if model == 2 else [])
+    names = ["P", "S", "K", "T", "r", "q"]
+    for j, key in enumerate(keys):
+        x0 = np.asarray(w[key], dtype=np.float64)
+        h = 1e-6 * np.abs(x0) if key in ("P", "S_or_F", "K", "T") else np.full(x0.size, 1e-6)
+        outs = []
+        for sgn in (1, -1):
+            ww = dict(w)
+            ww[key] = x0 + sgn * h
+            s_h, _ = fv.fv_implied_vol(model, fv.FV_LBR, *_args(torch_dev, ww), flag)
+            outs.append(_np(s_h))
+        fd = (outs[0] - outs[1]) / (2 * h) * w["grad_sigma"]
+        g = _np(adj[names[j]])
+        m = ok & (kap < 1e2)
+        np.testing.assert_allclose(g[m], fd[m], rtol=2e-5, atol=1e-9, err_msg=key)
+
+
+def test_autograd_function(fv, torch_dev):
+    torch, dev = torch_dev
+    w = wl.fill_prices(wl.bsm_quotes(1024, seed=8), orc.price)
+    ins = [torch.tensor(w[k], device=dev, requires_grad=True) for k in
+           ("P", "S_or_F", "K", "T", "r", "q")]
+    flag = _dev(torch_dev, w["flag"])
+    sigma = fv.implied_volatility_autograd(*ins, flag, model=fv.FV_BSM)
+    g = torch.tensor(w["grad_sigma"], device=dev)
+    (sigma * g).sum().backward()
+    s2, st2 = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *[t.detach() for t in ins], flag)
+    assert torch.equal(sigma.detach().nan_to_num(-1), s2.nan_to_num(-1))
+    adj = fv.fv_iv_adjoint(fv.FV_BSM, *[t.detach() for t in ins], flag, s2, st2, g)
+    for t, name in zip(ins, ("P", "S", "K", "T", "r", "q")):
+        assert torch.equal(t.grad, adj[name]), name
+
+
+# ---------------------------------------------------------------------------
+# batches of option chains
+# ---------------------------------------------------------------------------
+def _chain_tensors(torch_dev, c):
+    torch, dev = torch_dev
+    chains = []
+    for j in range(len(c["lens"])):
+        a, b = c["offsets"][j], c["offsets"][j + 1]
+        chains.append(dict(price=_dev(torch_dev, c["P"][a:b]), K=_dev(torch_dev, c["K"][a:b]),
+                           flag=_dev(torch_dev, c["flag"][a:b]),
+                           sigma=torch.empty(b - a, dtype=torch.float64, device=dev),
+                           status=torch.empty(b - a, dtype=torch.uint8, device=dev),
+                           S_or_F=c["F_chain"][j], T=c["T_chain"][j], r=c["r_chain"][j]))
+    return chains
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_chains_match_flat_and_oracle(fv, torch_dev, autotune):
+    c = wl.fill_prices(wl.chains(120, seed=3, max_len=3000), orc.price)
+    chains = _chain_tensors(torch_dev, c)
+    plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=autotune)
+    for ch in chains:
+        ch["sigma"].fill_(-7.0)
+        ch["status"].fill_(9)
+    plan.run()
+    sig = np.concatenate([_np(ch["sigma"]) for ch in chains])
+    st = np.concatenate([_np(ch["status"]) for ch in chains])
+    # the flat kernel over the concatenated arrays gives identical bits
+    s_flat, st_flat = fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR,
+                                        *_args(torch_dev, c, ("P", "S_or_F", "K", "T", "r")), None,
+                                        _dev(torch_dev, c["flag"]))
+    assert np.array_equal(st, _np(st_flat))
+    assert np.array_equal(sig, _np(s_flat), equal_nan=True)
+    ref, st_ref, v, kap = _iv_ref(c)
+    assert np.array_equal(st, st_ref)
+    _check_sigma(sig, ref, st_ref, v, kap, tol_rest=1e-12, name="chains")
+    # the direct launch and a second graph replay agree
+    plan.run_direct()
+    assert np.array_equal(np.concatenate([_np(ch["sigma"]) for ch in chains]), sig, equal_nan=True)
+    info = plan.info()
+    assert info["quotes"] == c["offsets"][-1] and info["tiles"] > 0
+    plan.destroy()
+
+
+def test_chains_with_empty_chains(fv, torch_dev):
+    torch, dev = torch_dev
+    c = wl.fill_prices(wl.chains(5, seed=11, max_len=100), orc.price)
+    chains = _chain_tensors(torch_dev, c)
+    e = lambda dt: torch.empty(0, dtype=dt, device=dev)
+    chains.insert(2, dict(price=e(torch.float64), K=e(torch.float64), flag=e(torch.int8),
+                          sigma=e(torch.float64), status=e(torch.uint8), S_or_F=100.0, T=1.0, r=0.0))
+    plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=False)
+    plan.run()
+    torch.cuda.synchronize()
+    assert plan.info()["quotes"] == c["offsets"][-1]
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 257, 4097])
+def test_ragged_sizes_and_canaries(fv, torch_dev, n):
+    torch, dev = torch_dev
+    w = wl.fill_prices(wl.black76_quotes(n, seed=n), orc.price)
+    ref, st_ref, v, kap = _iv_ref(w)
+    pad = 64
+    sig_buf = torch.full((n + 2 * pad,), 123.0, dtype=torch.float64, device=dev)
+    st_buf = torch.full((n + 2 * pad,), 77, dtype=torch.uint8, device=dev)
+    out_s, out_st = sig_buf[pad:pad + n], st_buf[pad:pad + n]
+    P, F, K, T, r, _ = _args(torch_dev, w)
+    fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR, P, F, K, T, r, None, _dev(torch_dev, w["flag"]),
+                      out_s, out_st)
+    sb, tb = _np(sig_buf), _np(st_buf)
+    assert np.all(sb[:pad] == 123.0) and np.all(sb[pad + n:] == 123.0)
+    assert np.all(tb[:pad] == 77) and np.all(tb[pad + n:] == 77)
+    assert np.array_equal(tb[pad:pad + n], st_ref)
+    _check_sigma(sb[pad:pad + n], ref, st_ref, v, kap, tol_rest=1e-12)
+
+
+def test_misaligned_views(fv, torch_dev):
+    # element offsets of 1 break 16-byte alignment of every array
+    torch, dev = torch_dev
+    n = 1000
+    w = wl.fill_prices(wl.black76_quotes(n, seed=12), orc.price)
+    ref, st_ref, v, kap = _iv_ref(w)
+
+    def off(a, dt):
+        t = torch.zeros(n + 1, dtype=dt, device=dev)
+        t[1:] = torch.tensor(a, dtype=dt, device=dev)
+        return t[1:]
+
+    args = [off(w[k], torch.float64) for k in ("P", "S_or_F", "K", "T", "r")]
+    s = off(np.zeros(n), torch.float64)
+    st = off(np.zeros(n, np.uint8), torch.uint8)
+    fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR, *args, None, off(w["flag"], torch.int8), s, st)
+    assert np.array_equal(_np(st), st_ref)
+    _check_sigma(_np(s), ref, st_ref, v, kap, tol_rest=1e-12)
+
+
+def test_invalid_and_boundary_quotes(fv, torch_dev):
+    nan, inf = float("nan"), float("inf")
+    # (P, F, K, T, r, flag): r = 0 makes the bounds exact
+    rows = [(10.0, 100, 90, 1, 0, 1), (10 * (1 - 1e-12), 100, 90, 1, 0, 1), (-1e-3, 100, 90, 1, 0, -1),
+            (0.0, 100, 90, 1, 0, -1), (100.0, 100, 90, 1, 0, 1), (90.0, 100, 90, 1, 0, -1),
+            (nan, 100, 90, 1, 0, 1), (5.0, 100, 90, 1, 0, 0), (5.0, 100, -90, 1, 0, 1),
+            (5.0, 100, 90, 0, 0, 1), (5.0, inf, 90, 1, 0, 1), (5.0, 100, 90, 1, nan, 1),
+            (12.0, 100, 90, 1, 0, 1), (3.0, 100, 100, 0.5, 0.0, -1), (1e-300, 100, 150, 0.1, 0.0, 1)]
+    a = np.array(rows, dtype=np.float64)
+    w = dict(model=0, P=a[:, 0], S_or_F=a[:, 1], K=a[:, 2], T=a[:, 3], r=a[:, 4], q=None,
+             flag=a[:, 5].astype(np.int8))
+    ref, st_ref, v, kap = _iv_ref(w)
+    for solver in (fv.FV_LBR, fv.FV_HALLEY):
+        s, st = fv.fv_implied_vol(0, solver, *_args(torch_dev, w), _dev(torch_dev, w["flag"]))
+        assert np.array_equal(_np(st), st_ref)
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_rest=1e-12)
+    assert list(st_ref[:12]) == [0, 1, 1, 0, 2, 2, 3, 3, 3, 3, 3, 3]
+
+
+def test_zero_length_is_a_noop(fv, torch_dev):
+    torch, dev = torch_dev
+    e = torch.empty(0, dtype=torch.float64, device=dev)
+    s, st = fv.fv_implied_vol(0, 0, e, e, e, e, e, None, torch.empty(0, dtype=torch.int8, device=dev))
+    assert s.numel() == 0 and st.numel() == 0
+
+
+def test_abi_argument_errors(fv, torch_dev):
+    lib = fv.library()
+    torch, dev = torch_dev
+    x = torch.ones(4, dtype=torch.float64, device=dev)
+    p = ctypes.c_void_p(x.data_ptr())
+    assert lib.fv_implied_vol(7, 0, p, p, p, p, p, None, p, 4, p, p, None) == fv.FV_ERR_ARG
+    assert lib.fv_implied_vol(0, 5, p, p, p, p, p, None, p, 4, p, p, None) == fv.FV_ERR_ARG
+    assert lib.fv_implied_vol(0, 0, p, p, p, p, p, None, p, -1, p, p, None) == fv.FV_ERR_ARG
+    assert lib.fv_implied_vol(0, 0, None, p, p, p, p, None, p, 4, p, p, None) == fv.FV_ERR_ARG
+    assert lib.fv_implied_vol(2, 0, p, p, p, p, p, None, p, 4, p, p, None) == fv.FV_ERR_ARG  # BSM needs q
+    assert lib.fv_implied_vol_ex(0, 1, 1, 0, p, p, p, p, p, None, p, 4, p, p, None) == fv.FV_ERR_UNSUPPORTED
+    assert lib.fv_implied_vol_ws(0, 1, p, p, p, p, p, None, p, 4, p, p, p, 8, None) == fv.FV_ERR_ARG
+    assert b"workspace" in lib.fv_last_error()
+    torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# full reference sizes, in the launch configuration the benchmark times
+# ---------------------------------------------------------------------------
+def _sampled_parity(fv, torch_dev, w, sig, st, model, n_sample=2048, seed=0, tol_gate=1e-12):
+    st_all, _, _ = orc.status(model, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], w.get("q"),
+                              w["flag"])
+    assert np.array_equal(st, st_all)
+    g = np.random.default_rng(seed)
+    idx = np.sort(g.choice(st.size, size=min(n_sample, st.size), replace=False))
+    sub = {k: (None if w.get(k) is None else np.asarray(w[k])[idx]) for k in
+           ("P", "S_or_F", "K", "T", "r", "q", "flag")}
+    sub["model"] = model
+    ref, st_ref, v, kap = _iv_ref(sub)
+    assert np.array_equal(st[idx], st_ref)
+    _check_sigma(sig[idx], ref, st_ref, v, kap, tol_gate=tol_gate,
+                 tol_rest=1e-12 if tol_gate <= 1e-12 else None)
+
+
+def test_full_size_bsm_grid_lbr_and_mixed(fv, torch_dev):
+    w = wl.fill_prices(wl.bsm_grid(4096, 4096, seed=1), orc.price_f64)
+    args = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *args, flag)
+    _sampled_parity(fv, torch_dev, w, _np(s), _np(st), fv.FV_BSM)
+    s, st = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR, fv.FV_MIXED, *args, flag)
+    _sampled_parity(fv, torch_dev, w, _np(s), _np(st), fv.FV_BSM, seed=1)
+
+
+def test_full_size_fp32_inputs_mixed(fv, torch_dev):
+    torch, dev = torch_dev
+    w = wl.black76_fp32(67108864, seed=2)
+    wl.fill_prices(w, orc.price_f64, price_dtype=np.float32)
+    args = [torch.tensor(w[k], device=dev) for k in ("P", "S_or_F", "K", "T", "r")]
+    flag = _dev(torch_dev, w["flag"])
+    s, st = fv.fv_implied_vol_ex(fv.FV_BLACK76, fv.FV_LBR, fv.FV_MIXED, *args, None, flag)
+    w64 = {k: (None if w.get(k) is None else np.asarray(w[k], dtype=np.float64) if k != "flag"
+               else w[k]) for k in ("P", "S_or_F", "K", "T", "r", "q", "flag")}
+    _sampled_parity(fv, torch_dev, w64, _np(s), _np(st), fv.FV_BLACK76)
+
+
+def test_full_size_chains(fv, torch_dev):
+    c = wl.fill_prices(wl.chains(10000, seed=3), orc.price_f64)
+    chains = _chain_tensors(torch_dev, c)
+    plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=False)
+    plan.run()
+    sig = np.concatenate([_np(ch["sigma"]) for ch in chains])
+    st = np.concatenate([_np(ch["status"]) for ch in chains])
+    _sampled_parity(fv, torch_dev, c, sig, st, fv.FV_BLACK76)
+    plan.destroy()
+
+
+def test_full_size_adjoint(fv, torch_dev):
+    w = wl.fill_prices(wl.bsm_quotes(8388608, seed=4), orc.price_f64)
+    ins = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *ins, flag)
+    adj = fv.fv_iv_adjoint(fv.FV_BSM, *ins, flag, s, st, _dev(torch_dev, w["grad_sigma"]))
+    s_np, st_np = _np(s), _np(st)
+    idx = np.random.default_rng(5).choice(s_np.size, 2048, replace=False)
+    sub = lambda k: np.asarray(w[k])[idx]
+    refs = orc.iv_grad(2, sub("S_or_F"), sub("K"), sub("T"), sub("r"), sub("q"), sub("flag"),
+                       s_np[idx], st_np[idx], sub("grad_sigma"))
+    v, kap = orc.conditioning(2, sub("P"), sub("S_or_F"), sub("K"), sub("T"), sub("r"), sub("q"),
+                              sub("flag"), s_np[idx])
+    ok = (st_np[idx] == 0) & (s_np[idx] > 0) & (v > 1e-8)
+    for name, ref in zip(("P", "S", "K", "T", "r", "q"), refs):
+        g = _np(adj[name])[idx]
+        assert (np.abs(g[ok] - ref[ok]) / np.maximum(np.abs(ref[ok]), 1e-300)).max() <= 1e-11, name

@@ -53,6 +53,15 @@ def test_price_equals_risk_neutral_expectation(model):
         assert got == pytest.approx(want, rel=1e-13, abs=1e-300)
 
 
+def test_fp64_textbook_price_agrees_with_binary128():
+    w = wl.bsm_quotes(20000, seed=13)
+    for model in (orc.BLACK76, orc.BSM):
+        a = orc.price_f64(model, w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["sigma_true"], w["flag"])
+        b = orc.price(model, w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["sigma_true"], w["flag"])
+        m = b > 1e-3  # away from the cancellation of deep out-of-the-money quotes
+        assert (np.abs(a[m] - b[m]) / b[m]).max() <= 1e-12
+
+
 def test_put_call_parity():
     w = wl.black76_quotes(512, seed=11)
     for model in (orc.BLACK76, orc.BSM):
