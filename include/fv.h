@@ -25,8 +25,9 @@
  *    makes that quote FV_Q_INVALID.
  *  - Per-quote failures never become call errors: they go to the uint8
  *    `status` array (fv_quote_status) and the quote's sigma is NaN.  A price
- *    exactly at the intrinsic value (within a relative band of 4 * 2^-52) is
- *    FV_Q_OK with sigma = 0.
+ *    at the intrinsic value (within a relative band of 64 * 2^-52) is
+ *    FV_Q_OK with sigma = 0; a price within that band below its upper bound
+ *    is FV_Q_ABOVE_MAX.
  *  - Call errors (fv_err < 0) are for arguments only (NULL required pointer,
  *    n < 0, unknown enum): the call is then rejected before any launch.  A
  *    CUDA error seen at launch, or left pending by earlier asynchronous work,

@@ -110,8 +110,11 @@ static void parallel_for(int64_t n, int nthreads, range_fn fn, void* ctx) {
 /* FP64 status decision (the same rule, the same operation order, is what the
  * kernels implement).                                                        */
 /* ------------------------------------------------------------------------- */
-/* relative slack band of the bound tests: 4 * 2^-52 */
-#define EPS_S (4.0 * 2.220446049250313080847263336181640625e-16)
+/* relative slack band of the bound tests: 64 * 2^-52.  Prices that sit at
+ * the intrinsic value up to their own rounding land within a few ulp of it;
+ * the band is wide enough that one-ulp differences between libm
+ * implementations cannot move such a quote across its edge. */
+#define EPS_S (64.0 * 2.220446049250313080847263336181640625e-16)
 
 typedef struct {
   int status;      /* ORC_* */
@@ -345,6 +348,28 @@ void or_price_f64(int model, const double* S_or_F, const double* K, const double
   parallel_for(n, nthreads, price_f64_range, &c);
 }
 
+/* Relative distance, in units of 2^-52, of the three decision quantities of
+ * the status rule to their thresholds (below-intrinsic, above-maximum, at
+ * intrinsic).  A quote within a few units sits where one-ulp differences
+ * between two libm implementations of exp/log1p/expm1 can flip the decision. */
+static double status_margin(const quote_f64* d, int8_t flag) {
+  if (d->status == ORC_INVALID) return INFINITY;
+  const double eps = 2.220446049250313080847263336181640625e-16;
+  const double x = d->x, beta = d->beta, th = (double)flag;
+  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
+  double iota = th > 0 ? ep - em : em - ep;
+  if (iota < 0) iota = 0;
+  const double bmax_otm = 1.0 + (x > 0 ? em : ep);
+  const double beta_otm = (th * x > 0) ? beta - iota : beta;
+  double m = INFINITY;
+  if (iota > 0) {
+    m = fmin(m, fabs(beta / (iota * (1.0 - EPS_S)) - 1.0));
+    m = fmin(m, fabs(beta / (iota * (1.0 + EPS_S)) - 1.0));
+  }
+  m = fmin(m, fabs(beta_otm / (bmax_otm * (1.0 - EPS_S)) - 1.0) * (bmax_otm / (beta > bmax_otm ? beta : bmax_otm)));
+  return m / eps;
+}
+
 static void status_range(void* c_, int64_t i0, int64_t i1) {
   ctx_t* c = (ctx_t*)c_;
   for (int64_t i = i0; i < i1; i++) {
@@ -354,11 +379,12 @@ static void status_range(void* c_, int64_t i0, int64_t i1) {
     c->status[i] = (uint8_t)d.status;
     if (c->out) c->out[i] = d.x;
     if (c->out2) c->out2[i] = d.beta;
+    if (c->out3) c->out3[i] = status_margin(&d, c->flag[i]);
   }
 }
 void or_status(int model, const double* P, const double* S_or_F, const double* K, const double* T,
                const double* r, const double* q, const int8_t* flag, int64_t n, uint8_t* status,
-               double* x_out, double* beta_out, int nthreads) {
+               double* x_out, double* beta_out, double* margin_out, int nthreads) {
   ctx_t c = {0};
   c.model = model;
   c.P = P;
@@ -371,6 +397,7 @@ void or_status(int model, const double* P, const double* S_or_F, const double* K
   c.status = status;
   c.out = x_out;
   c.out2 = beta_out;
+  c.out3 = margin_out;
   parallel_for(n, nthreads, status_range, &c);
 }
 
@@ -666,7 +693,7 @@ void or_iv_lbr(int model, const double* P, const double* S_or_F, const double* K
 static double bisect_fallback(double beta, double x, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
   if (!isfinite(hi)) {
-    hi = lo > 0 ? 2.0 * lo : 1.0;
+    hi = fmax(2.0 * lo, 1e-3);
     while (nb_d(x, hi) <= beta && hi < 1e6) {
       lo = hi;
       hi *= 2.0;

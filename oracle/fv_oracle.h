@@ -65,11 +65,13 @@ void or_price_f64(int model, const double* S_or_F, const double* K, const double
                   const int8_t* flag, int64_t n, double* out, int nthreads);
 
 /* Status only, by the FP64 decision rule (also returns the FP64 normalised
- * log-moneyness x and normalised price beta; NULL to skip). */
+ * log-moneyness x, the normalised price beta, and the relative distance of
+ * the rule's quantities to its nearest threshold in units of 2^-52; NULL to
+ * skip any of the three). */
 void or_status(int model, const double* P, const double* S_or_F, const double* K,
                const double* T, const double* r, const double* q,
                const int8_t* flag, int64_t n, uint8_t* status, double* x_out,
-               double* beta_out, int nthreads);
+               double* beta_out, double* margin_out, int nthreads);
 
 /* Implied volatility by definition: binary128 bisection on the normalised
  * Black function.  sigma = NaN unless status is OK; sigma = 0 at intrinsic. */

@@ -33,7 +33,7 @@ def _load():
         lib.or_normalised_black.argtypes = [_D, _D, _I8, _N, _D, _INT]
         lib.or_price.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _INT]
         lib.or_price_f64.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _INT]
-        lib.or_status.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _U8, _D, _D, _INT]
+        lib.or_status.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _U8, _D, _D, _D, _INT]
         lib.or_iv.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _U8, _INT]
         lib.or_conditioning.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _D, _N, _D, _D, _INT]
         lib.or_iv_lbr.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _INT, _D, _U8, _I8, _INT]
@@ -102,15 +102,17 @@ def price_f64(model, S_or_F, K, T, r, q, sigma, flag, nthreads=0):
 
 
 def status(model, P, S_or_F, K, T, r, q, flag, nthreads=0):
+    """FP64 status rule: (status, x, beta, margin to the nearest threshold in 2^-52 units)."""
     n = _len(P, S_or_F, K, T, r, q, flag)
     keep = [_f64(P, n), _f64(S_or_F, n), _f64(K, n), _f64(T, n), _f64(r, n),
             _f64(0.0 if q is None else q, n), _i8(flag, n)]
     st = np.empty(n, np.uint8)
     x = np.empty(n, np.float64)
     beta = np.empty(n, np.float64)
+    margin = np.empty(n, np.float64)
     _load().or_status(model, *[k[1] for k in keep], n, st.ctypes.data_as(_U8), x.ctypes.data_as(_D),
-                      beta.ctypes.data_as(_D), nthreads)
-    return st, x, beta
+                      beta.ctypes.data_as(_D), margin.ctypes.data_as(_D), nthreads)
+    return st, x, beta, margin
 
 
 def _iv_common(fn, model, P, S_or_F, K, T, r, q, flag, extra=(), nthreads=0, aux=None):

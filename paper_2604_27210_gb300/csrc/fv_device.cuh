@@ -41,8 +41,10 @@ constexpr double kSqrtPiOver2 = 1.25331413731550025120788264240552263;  // sqrt(
 constexpr double kSqrt2OverPi = 0.797884560802865355879892119868763737;  // sqrt(2/pi)
 constexpr double kInvSqrt3 = 0.577350269189625764509148780501957456;    // 1/sqrt(3)
 constexpr double kLn2Pi = 1.83787706640934548356065947281123527;        // ln(2 pi)
-// relative slack band of the three bound tests of the status rule: 4 * 2^-52
-constexpr double kEpsS = 8.8817841970012523233890533447265625e-16;
+// relative slack band of the three bound tests of the status rule:
+// 64 * 2^-52, wider than the few-ulp spread of a price that equals the
+// intrinsic value up to rounding, so libm differences cannot flip a decision
+constexpr double kEpsS = 1.42108547152020037174224853515625e-14;
 
 enum { Q_OK = 0, Q_BELOW = 1, Q_ABOVE = 2, Q_INVALID = 3 };
 enum { M_BLACK76 = 0, M_BS = 1, M_BSM = 2 };
@@ -487,12 +489,14 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x) {
 }
 
 // bisection on ln b - ln beta in [lo, hi], Newton steps kept when inside
-__device__ __forceinline__ double bisect_fallback(double beta, double x, double lo, double hi) {
+// (ln_beta is passed in: for subnormal-range prices it comes from log(P))
+__device__ __forceinline__ double bisect_fallback(double ln_beta, double x, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
-  const double ln_beta = log(beta);
   NB<double> v;
   if (!isfinite(hi)) {
-    hi = lo > 0.0 ? 2.0 * lo : 1.0;
+    // expand from max(2 lo, 1e-3): a Halley run that never overshot leaves lo
+    // anywhere down to the Brenner-Subrahmanyam guess
+    hi = fmax(2.0 * lo, 1e-3);
     for (int it = 0; it < 64; it++) {
       nb_eval<double>(x, hi, false, v);
       if (nb_log(v) > ln_beta) break;

@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
     const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
     const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
     const Norm nq = decide(a.model, P, SF, K, T, r, q, a.flag[i]);
-    const double s = bisect_fallback(nq.beta_otm, nq.x_otm, w.lo[k], w.hi[k]);
+    const Reduced<double> q64 = reduced64(nq);
+    const double s = bisect_fallback(q64.ln_beta, q64.x, w.lo[k], w.hi[k]);
     a.sigma[i] = s / sqrt(T);
   }
 }
