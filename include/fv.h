@@ -195,6 +195,33 @@ fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_p
 
 fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
 
+/* ---- implied volatility without any device allocation ----------------- */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * may not allocate device memory (a host process that pre-reserves all of it,
+ * an allocator that forbids raw cudaMalloc, a latency-critical path that
+ * cannot take a first-call allocation or the synchronisation of freeing one).
+ * It runs the Halley x8 solver with its bisection fallback exactly as
+ * fv_implied_vol does, but the fallback list lives in a scratch array
+ * compiled into the library: device global memory of about 20 bytes per
+ * quote of capacity (about 5 MiB), held by every GPU that loads the library
+ * until the process exits.
+ *  - n may not exceed FV_NOALLOC_MAX_QUOTES (FV_ERR_ARG otherwise, nothing
+ *    launched); split larger batches.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before capturing the stream into a CUDA graph.
+ *  - Each call clears the scratch's fallback counter on `stream` before use.
+ *    All calls on a device share the one array, so two calls whose GPU work
+ *    overlaps (different streams, or different threads) race and give wrong
+ *    results: serialise them on one stream.
+ *  - Calls cudaMalloc, cudaFree and no allocating routine.
+ * Arguments, outputs and errors as fv_implied_vol with FV_HALLEY. */
+#define FV_NOALLOC_MAX_QUOTES 262144
+fv_err fv_implied_vol_halley_noalloc(fv_model model, const double* price, const double* S_or_F,
+                                     const double* K, const double* T, const double* r,
+                                     const double* q, const int8_t* flag, int64_t n,
+                                     double* out_sigma, uint8_t* status, void* stream);
+
 /* Error reporting. */
 const char* fv_status_string(fv_err err);
 const char* fv_last_error(void);

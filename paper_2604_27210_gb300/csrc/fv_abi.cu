@@ -139,6 +139,10 @@ fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const v
 
 }  // namespace
 
+namespace fvk {
+void set_last_error(const char* msg) { fail(FV_ERR_ARG, "%s", msg); }
+}  // namespace fvk
+
 // ---------------------------------------------------------------------------
 // chains plan
 // ---------------------------------------------------------------------------

@@ -60,6 +60,9 @@ struct Tile {
   int32_t pad;
   int64_t offset;
 };
+// record the message fv_last_error() returns on the calling thread
+void set_last_error(const char* msg);
+
 cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
                           int block, int qpt, int grid, cudaStream_t st);
 int chains_max_blocks_per_sm(int block);

@@ -24,7 +24,8 @@ FV_SUCCESS, FV_ERR_ARG, FV_ERR_CUDA, FV_ERR_UNSUPPORTED, FV_ERR_NOMEM = 0, -1, -
 EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws",
            "fv_implied_vol_ex", "fv_greeks", "fv_iv_adjoint", "fv_normalised_black",
            "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
-           "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_status_string", "fv_last_error"]
+           "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_implied_vol_halley_noalloc",
+           "fv_status_string", "fv_last_error"]
 
 
 class FvError(RuntimeError):
@@ -68,6 +69,7 @@ def _load():
     lib.fv_implied_vol_chains_direct.argtypes = [_P, _P]
     lib.fv_chains_plan_info.argtypes = [_P] + [ctypes.POINTER(_I)] * 3 + [ctypes.POINTER(_N)] * 2
     lib.fv_chains_plan_destroy.argtypes = [_P]
+    lib.fv_implied_vol_halley_noalloc.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P]
     lib.fv_status_string.argtypes = [_I]
     lib.fv_status_string.restype = ctypes.c_char_p
     lib.fv_last_error.restype = ctypes.c_char_p
@@ -176,6 +178,25 @@ def fv_implied_vol_ws(model, solver, price, S_or_F, K, T, r, q, flag, workspace,
                                   _ptr(out_sigma, n, _F64, "out_sigma"),
                                   _ptr(status, n, _U8, "status"), wp, wb, _stream(stream)),
            "fv_implied_vol_ws")
+    return out_sigma, status
+
+
+FV_NOALLOC_MAX_QUOTES = 262144
+
+
+def fv_implied_vol_halley_noalloc(model, price, S_or_F, K, T, r, q, flag, out_sigma=None,
+                                  status=None, stream=None):
+    """Halley implied volatility using the library's built-in scratch array
+    instead of any device allocation (at most FV_NOALLOC_MAX_QUOTES quotes;
+    calls must not overlap on the GPU)."""
+    n = price.numel()
+    out_sigma, status = _iv_outputs(price, out_sigma, status)
+    _check(_lib.fv_implied_vol_halley_noalloc(
+        model, _ptr(price, n, _F64, "price"), _ptr(S_or_F, n, _F64, "S_or_F"),
+        _ptr(K, n, _F64, "K"), _ptr(T, n, _F64, "T"), _ptr(r, n, _F64, "r"),
+        _ptr(q, n, _F64, "q", allow_none=model != FV_BSM), _ptr(flag, n, _I8, "flag"), n,
+        _ptr(out_sigma, n, _F64, "out_sigma"), _ptr(status, n, _U8, "status"), _stream(stream)),
+        "fv_implied_vol_halley_noalloc")
     return out_sigma, status
 
 
