@@ -34,12 +34,14 @@ UNIT = "IV/s"
 # algorithmic HBM bytes per quote: P, S, K, T, r, q (8 B each) + flag (1 B) in,
 # sigma (8 B) + status (1 B) out
 BYTES_PER_QUOTE = 58
-# FP64 flops per quote executed by the LBR kernel on this workload (thread-level
-# DADD + DMUL + 2 DFMA, from the ncu counters summarised in
-# profiles/iv_lbr_fp64_bsm_grid.md); the ALU roofline's algorithmic work
-FP64_FLOPS_PER_QUOTE = {"lbr": None, "mixed": None}
-# nominal FP64 (non-tensor) peak of a GB300 at its 2070 MHz maximum clock
-FP64_PEAK_GFLOPS_NOMINAL = 1250.0
+# FP64 flops per quote the kernels execute on this workload: thread-level
+# DADD + DMUL + 2 x DFMA from ncu's smsp__sass_thread_inst_executed_op_*_pred_on
+# counters on 4,194,304 quotes of the same grid distribution.  This is the
+# ALU roofline's work per quote (the kernels are bound by the FP64 pipe).
+FP64_FLOPS_PER_QUOTE = {"lbr": 1540.0, "mixed": 530.0, "fp32": 281.0}
+# FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock (ncu's sustained peak of
+# the thread-level DFMA counter) x 2 flops x 2070 MHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 SM_MAX_MHZ = 2070.0
 
 
@@ -334,9 +336,11 @@ def main():
     flops_q = FP64_FLOPS_PER_QUOTE.get(args.path)
     if flops_q is not None:
         achieved = flops_q * n / (k_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS_NOMINAL,
-                    "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS_NOMINAL,
-                    "traffic": None, "peak_kind": "nominal FP64 pipe at 2070 MHz (recipe)"}
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                    "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
+                    "traffic": None, "flops_per_quote": flops_q,
+                    "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz "
+                                 "(recipe unit count and clock)"}
     else:
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak, "traffic": None}

@@ -111,9 +111,9 @@ fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
  *             correction; the normalisation, status decision, intrinsic
  *             subtraction and the final residual are FP64 (result within
  *             1e-12 of the FP64 path where the quote is well conditioned).
- *   FV_FP32:  the LBR in FP32 only (relative error about 1e-5); the status
- *             decision is still the FP64 rule, evaluated in FP64 only where
- *             an FP32 evaluation cannot decide it.
+ *   FV_FP32:  the LBR in FP32 only (relative error about 1e-5); the
+ *             normalisation, status decision and intrinsic subtraction stay
+ *             FP64, so the status is the FP64 rule's.
  * in_dtype says whether price, S_or_F, K, T, r, q point to double or float.
  * Only FV_LBR is supported with FV_MIXED / FV_FP32 (else FV_ERR_UNSUPPORTED).
  * out_sigma is always FP64. */

@@ -157,17 +157,21 @@ static void decide_f64(int model, double P, double SF, double K, double T, doubl
   }
   if (!isfinite(x) || !isfinite(beta)) return;
   const double th = (double)flag;
-  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
-  double iota = th > 0 ? ep - em : em - ep;
-  if (iota < 0) iota = 0;
+  /* Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 from expm1
+   * an in-the-money quote's intrinsic value e^{|x|/2} - e^{-|x|/2} is
+   * -E (1 + Em) / Em, accurate near the money and far from it */
+  const double E = expm1(-0.5 * fabs(x));
+  const double Em = exp(-0.5 * fabs(x));
+  const int itm = th * x > 0;
+  const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;
   o->x = x;
   o->beta = beta;
   if (beta < iota * (1.0 - EPS_S)) {
     o->status = ORC_BELOW_INTRINSIC;
     return;
   }
-  const double beta_otm = (th * x > 0) ? beta - iota : beta;
-  const double bmax_otm = 1.0 + (x > 0 ? em : ep); /* e^{-|x|/2} */
+  const double beta_otm = itm ? beta - iota : beta;
+  const double bmax_otm = Em;
   if (beta_otm >= bmax_otm * (1.0 - EPS_S)) {
     o->status = ORC_ABOVE_MAX;
     return;
@@ -356,11 +360,12 @@ static double status_margin(const quote_f64* d, int8_t flag) {
   if (d->status == ORC_INVALID) return INFINITY;
   const double eps = 2.220446049250313080847263336181640625e-16;
   const double x = d->x, beta = d->beta, th = (double)flag;
-  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
-  double iota = th > 0 ? ep - em : em - ep;
-  if (iota < 0) iota = 0;
-  const double bmax_otm = 1.0 + (x > 0 ? em : ep);
-  const double beta_otm = (th * x > 0) ? beta - iota : beta;
+  const double E = expm1(-0.5 * fabs(x));
+  const double Em = exp(-0.5 * fabs(x));
+  const int itm = th * x > 0;
+  const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;
+  const double bmax_otm = Em;
+  const double beta_otm = itm ? beta - iota : beta;
   double m = INFINITY;
   if (iota > 0) {
     m = fmin(m, fabs(beta / (iota * (1.0 - EPS_S)) - 1.0));

@@ -154,9 +154,13 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   // subnormal rounding; its logarithm is taken from P directly
   o.ln_beta = (beta < 1e-280 && P > 0.0) ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K)) : 0.0;
   if (!isfinite(x) || !isfinite(beta)) return o;
-  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
-  double iota = flag > 0 ? __dsub_rn(ep, em) : __dsub_rn(em, ep);
-  if (iota < 0.0) iota = 0.0;
+  // Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 (from expm1,
+  // accurate near the money) an in-the-money quote's intrinsic value is
+  // e^{|x|/2} - e^{-|x|/2} = -E (1 + Em) / Em, accurate for every x
+  const double E = expm1(-0.5 * fabs(x));
+  const double Em = exp(-0.5 * fabs(x));
+  const bool itm = flag * x > 0.0;
+  const double iota = itm ? __ddiv_rn(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em) : 0.0;
   o.x = x;
   o.beta = beta;
   o.iota = iota;
@@ -164,8 +168,8 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
     o.status = Q_BELOW;
     return o;
   }
-  const double beta_otm = (flag * x > 0.0) ? __dsub_rn(beta, iota) : beta;
-  const double bmax = __dadd_rn(1.0, x > 0.0 ? em : ep);
+  const double beta_otm = itm ? __dsub_rn(beta, iota) : beta;
+  const double bmax = Em;
   if (beta_otm >= __dmul_rn(bmax, 1.0 - kEpsS)) {
     o.status = Q_ABOVE;
     return o;
@@ -261,8 +265,11 @@ __device__ __forceinline__ T nb_log(const NB<T>& v) {
 
 // full normalised Black b(x, s, theta) for any x, s >= 0 (FP64)
 __device__ __forceinline__ double normalised_black(double x, double s, int theta) {
-  const double ep = expm1(0.5 * x), em = expm1(-0.5 * x);
-  const double iota = (theta * x > 0.0) ? fabs(ep - em) : 0.0;
+  double iota = 0.0;
+  if (theta * x > 0.0) {
+    const double E = expm1(-0.5 * fabs(x)), Em = exp(-0.5 * fabs(x));
+    iota = -E * (1.0 + Em) / Em;
+  }
   if (!(s > 0.0)) return iota;
   NB<double> v;
   nb_eval<double>(-fabs(x), s, false, v);
@@ -296,6 +303,7 @@ __device__ __forceinline__ T ncdfinv_log(T ln_p) {
 template <typename T>
 struct Reduced {
   T beta, ln_beta, c_beta, x, bmax;
+  T inv_ln_beta, ln_c_beta;  // 1/ln beta (lowest region), ln(b_max - beta) (highest)
 };
 
 template <typename T>
@@ -325,12 +333,12 @@ __device__ __forceinline__ Objective<T> objective(const Reduced<T>& q, T s, int 
     const T qw = T(kInvSqrt2Pi) / v.B;  // b'/b (region 0) or b'/(b_max - b) (region 3)
     if (reg == 0) {
       const T iL = T(1) / lnX, k1 = T(1) + T(2) * iL;
-      const T g = iL - T(1) / q.ln_beta;
+      const T g = iL - q.inv_ln_beta;
       o.nu = g * lnX * lnX / qw;
       o.h2 = u - qw * k1;
       o.h3 = o.h2 * o.h2 + du - (qw * u - qw * qw) * k1 + T(2) * qw * qw * iL * iL;
     } else {
-      const T g = f_log(q.c_beta) - lnX;
+      const T g = q.ln_c_beta - lnX;
       o.nu = -g / qw;
       o.h2 = u + qw;
       o.h3 = o.h2 * o.h2 + du + qw * o.h2;
@@ -348,6 +356,45 @@ __device__ __forceinline__ T hh3_step(const Objective<T>& o) {
 template <typename T>
 __device__ __forceinline__ T guarded(T s, T ds) {
   return (s + ds <= T(0.25) * s) ? T(0.25) * s : s + ds;
+}
+
+// One Householder(3) step whose residual g and first derivative g' are FP64
+// and whose second-order ratios h2 = g''/g', h3 = g'''/g' are FP32: they only
+// shape the correction factor (1 + phi) of the Newton step nu, with
+// phi = nu (-h2/2 - h3 nu/6) / (1 + nu (h2 + h3 nu/6)) = O(nu), so their
+// relative error enters the step at order nu^2.
+__device__ __forceinline__ double hh3_correction(const Reduced<double>& q, double s, int reg) {
+  NB<double> v;
+  nb_eval<double>(q.x, s, reg == 3, v);
+  const float hh = (float)(v.h * v.h), is = (float)v.inv_s, sf = (float)s;
+  const float u = hh * is - 0.25f * sf;
+  const float du = -3.0f * hh * is * is - 0.25f;
+  double nu;
+  float h2, h3;
+  if (reg == 1 || reg == 2) {
+    nu = (q.beta - v.e * v.B) / (v.e * kInvSqrt2Pi);
+    h2 = u;
+    h3 = u * u + du;
+  } else {
+    const double lnX = nb_log(v);
+    const double qw = kInvSqrt2Pi / v.B;
+    const float qf = (float)qw;
+    if (reg == 0) {
+      const double iL = 1.0 / lnX;
+      nu = (iL - q.inv_ln_beta) * lnX * lnX / qw;
+      const float iLf = (float)iL, k1 = 1.0f + 2.0f * iLf;
+      h2 = u - qf * k1;
+      h3 = h2 * h2 + du - (qf * u - qf * qf) * k1 + 2.0f * qf * qf * iLf * iLf;
+    } else {
+      nu = -(q.ln_c_beta - lnX) / qw;
+      h2 = u + qf;
+      h3 = h2 * h2 + du + qf * h2;
+    }
+  }
+  const float nf = (float)nu;
+  const float phi = nf * (-0.5f * h2 - h3 * nf * (1.0f / 6.0f)) / (1.0f + nf * (h2 + h3 * nf * (1.0f / 6.0f)));
+  const double ds = isfinite(phi) ? nu + nu * (double)phi : nu;
+  return guarded<double>(s, isfinite(ds) ? ds : 0.0);
 }
 
 // Boundaries (six normalised-Black values: b and b' at s_l, s_c, s_h, of which
@@ -373,9 +420,11 @@ __device__ __forceinline__ T lbr_guess(const Reduced<T>& q, int& reg) {
   nb_eval<T>(x, so, false, vo_);
   const T bo = degenerate ? T(0) : vo_.e * vo_.B;
   const T vo = vo_.e * T(kInvSqrt2Pi);
-  const T ln_bo = nb_log(vo_);
+  // ln b_l is needed on the lower side only (region test where b_l
+  // underflows the type, and the lowest-region guess)
+  const T ln_bo = lower ? nb_log(vo_) : T(0);
   if (lower)
-    reg = (!degenerate && q.ln_beta < ln_bo) ? 0 : 1;
+    reg = (!degenerate && (bo > T(0) ? beta < bo : q.ln_beta < ln_bo)) ? 0 : 1;
   else
     reg = (beta <= bo) ? 2 : 3;
   T s;
@@ -431,6 +480,8 @@ __device__ __forceinline__ Reduced<double> reduced64(const Norm& n) {
   q.c_beta = n.bmax - n.beta_otm;
   q.x = n.x_otm;
   q.bmax = n.bmax;
+  q.inv_ln_beta = 1.0 / q.ln_beta;
+  q.ln_c_beta = log(q.c_beta);
   return q;
 }
 
@@ -441,6 +492,8 @@ __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
   f.c_beta = (float)q.c_beta;
   f.x = (float)q.x;
   f.bmax = (float)q.bmax;
+  f.inv_ln_beta = (float)q.inv_ln_beta;
+  f.ln_c_beta = (float)q.ln_c_beta;
   return f;
 }
 

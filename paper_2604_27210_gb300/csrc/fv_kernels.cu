@@ -65,16 +65,13 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
         double s;
         if (PREC == P_FP64) {
           // two Householder(3) steps, a third where the second still moved s
-          // by more than 2^-20 (quartic convergence: a smaller second step
+          // by more than 2^-17 (quartic convergence: a smaller second step
           // leaves an error far below one ulp)
-          s = lbr_solve<double>(q64, 2, 3, 0x1p-20, reg);
+          s = lbr_solve<double>(q64, 2, 3, 0x1p-17, reg);
         } else {
           const float s32 = lbr_solve<float>(reduced32(q64), 2, 2, 0.0f, reg);
           s = (double)s32;
-          if (PREC == P_MIXED) {
-            const Objective<double> o = objective<double>(q64, s, reg);
-            s = guarded<double>(s, hh3_step<double>(o));
-          }
+          if (PREC == P_MIXED) s = hh3_correction(q64, s, reg);
         }
         sigma = s / sqrt(T);
       }
@@ -411,7 +408,7 @@ __global__ void __launch_bounds__(512) k_chains(int model, const ChainDesc* __re
             sigma = 0.0;
           } else {
             int reg = 1;
-            const double s = lbr_solve<double>(reduced64(nq), 2, 3, 0x1p-20, reg);
+            const double s = lbr_solve<double>(reduced64(nq), 2, 3, 0x1p-17, reg);
             sigma = s / sqrt(c.T);
           }
         }
