@@ -64,6 +64,13 @@ def max_over_ranks(value, world_size):
     return float(t.item())
 
 
+def aggregate(quotes_per_rank, ms_per_step_local, world_size):
+    """Whole-job throughput: every rank solves its own quotes, the job's step
+    time is the slowest rank's.  Returns (ms_per_step_max, quotes_per_second)."""
+    ms = max_over_ranks(ms_per_step_local, world_size)
+    return ms, world_size * quotes_per_rank / (ms * 1e-3)
+
+
 def barrier(world_size):
     if world_size > 1:
         import torch.distributed as dist
@@ -326,8 +333,7 @@ def main():
         total_ms, kernel_ms = time_steps(torch, lambda: run_path(fv, t, args.path, out, st),
                                          args.steps, args.warmup, ws)
     clocks = clk.summary()
-    ms_step = max_over_ranks(total_ms / args.steps, ws)
-    value = ws * n / (ms_step * 1e-3)
+    ms_step, value = aggregate(n, total_ms / args.steps, ws)
 
     # kernel-level roofline of the dominant (only) kernel of the step
     k_ms = statistics.mean(kernel_ms)
