@@ -38,7 +38,7 @@ BYTES_PER_QUOTE = 58
 # DADD + DMUL + 2 x DFMA from ncu's smsp__sass_thread_inst_executed_op_*_pred_on
 # counters on 4,194,304 quotes of the same grid distribution.  This is the
 # ALU roofline's work per quote (the kernels are bound by the FP64 pipe).
-FP64_FLOPS_PER_QUOTE = {"lbr": 1540.0, "mixed": 530.0, "fp32": 281.0}
+FP64_FLOPS_PER_QUOTE = {"lbr": 1493.0, "mixed": 482.0, "fp32": 195.0}
 # FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock (ncu's sustained peak of
 # the thread-level DFMA counter) x 2 flops x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070

@@ -191,8 +191,8 @@ fv_err upload_tiles(fv_chains_plan* p, const std::vector<fvk::Tile>& tiles, cuda
   return cuda_result(e, "fv_chains_plan_create: tile upload");
 }
 
-int plan_grid(int block, int64_t n_tiles) {
-  const int per_sm = fvk::chains_max_blocks_per_sm(block);
+int plan_grid(int qpt, int64_t n_tiles) {
+  const int per_sm = fvk::chains_max_blocks_per_sm(qpt);
   const int64_t g = std::min<int64_t>((int64_t)fvk::sm_count() * per_sm, std::max<int64_t>(1, n_tiles));
   return (int)g;
 }
@@ -394,8 +394,9 @@ fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* c
                          cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: upload"));
   }
-  // candidates: (block, quotes per thread); the default first
-  const int cand[][2] = {{256, 1}, {128, 1}, {512, 1}, {256, 2}, {128, 2}, {128, 4}};
+  // candidates: (block, quotes per thread); the default first.  A tile is
+  // block * quotes-per-thread quotes of one chain, binned by LBR region.
+  const int cand[][2] = {{256, 4}, {256, 2}, {256, 1}};
   const int n_cand = autotune ? (int)(sizeof(cand) / sizeof(cand[0])) : 1;
   std::vector<fvk::Tile> tiles;
   int best = 0;
@@ -411,7 +412,7 @@ fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* c
         cudaEventDestroy(e1);
         return cleanup(e);
       }
-      const int grid = plan_grid(cand[k][0], p->n_tiles);
+      const int grid = plan_grid(cand[k][1], p->n_tiles);
       // one warm-up launch, then the timed one
       fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, cand[k][0], cand[k][1], grid, st);
       cudaEventRecord(e0, st);
@@ -437,7 +438,7 @@ fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* c
   p->qpt = cand[best][1];
   build_tiles(p, p->block, p->qpt, tiles);
   if ((e = upload_tiles(p, tiles, st)) != FV_SUCCESS) return cleanup(e);
-  p->grid = plan_grid(p->block, p->n_tiles);
+  p->grid = plan_grid(p->qpt, p->n_tiles);
   // capture the persistent launch into a graph on a private stream
   if (p->n_tiles > 0) {
     cudaStream_t cs;

@@ -302,9 +302,23 @@ __device__ __forceinline__ T ncdfinv_log(T ln_p) {
 // (both from FP64 when T is float), and b_max = e^{x/2}.
 template <typename T>
 struct Reduced {
-  T beta, ln_beta, c_beta, x, bmax;
+  T beta, c_beta, x, bmax;
+  // ln beta: 0 until computed (beta < 1 after the reduction, so 0 is free);
+  // preset from log(P) for prices near the bottom of the FP64 range
+  T ln_beta;
   T inv_ln_beta, ln_c_beta;  // 1/ln beta (lowest region), ln(b_max - beta) (highest)
 };
+
+// The logarithms only the wing objectives need, for the region the guess chose.
+template <typename T>
+__device__ __forceinline__ void wing_logs(Reduced<T>& q, int reg) {
+  if (reg == 0) {
+    if (q.ln_beta == T(0)) q.ln_beta = f_log(q.beta);
+    q.inv_ln_beta = T(1) / q.ln_beta;
+  } else if (reg == 3) {
+    q.ln_c_beta = f_log(q.c_beta);
+  }
+}
 
 template <typename T>
 struct Objective {
@@ -363,7 +377,8 @@ __device__ __forceinline__ T guarded(T s, T ds) {
 // shape the correction factor (1 + phi) of the Newton step nu, with
 // phi = nu (-h2/2 - h3 nu/6) / (1 + nu (h2 + h3 nu/6)) = O(nu), so their
 // relative error enters the step at order nu^2.
-__device__ __forceinline__ double hh3_correction(const Reduced<double>& q, double s, int reg) {
+__device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, int reg) {
+  wing_logs<double>(q, reg);
   NB<double> v;
   nb_eval<double>(q.x, s, reg == 3, v);
   const float hh = (float)(v.h * v.h), is = (float)v.inv_s, sf = (float)s;
@@ -401,15 +416,23 @@ __device__ __forceinline__ double hh3_correction(const Reduced<double>& q, doubl
 // b' at s_c is closed form and only the side of s_c that beta falls on is
 // evaluated), the four-region initial guess, and the region index.
 template <typename T>
-__device__ __forceinline__ T lbr_guess(const Reduced<T>& q, int& reg) {
+__device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
   const T x = q.x, beta = q.beta, bmax = q.bmax;
   const bool xneg = x < T(0);
-  // inflection point s_c = sqrt(2|x|), where h + t = 0 and b'(s_c) = e^{x/2}/sqrt(2 pi)
-  const T sc_eval = xneg ? f_sqrt(T(-2) * x) : T(1);
-  NB<T> vc_;
-  nb_eval<T>(x, sc_eval, false, vc_);
-  const T sc = xneg ? sc_eval : T(0);
-  const T bc = xneg ? vc_.e * vc_.B : T(0);
+  // inflection point s_c = sqrt(2|x|): there h + t = 0, h^2 + t^2 = |x|, so
+  // e = e^{x/2} = b_max, erfcx(-(h+t)/sqrt2) = 1 and b'(s_c) = b_max/sqrt(2 pi);
+  // the erfcx form reduces to b_c = b_max (1 - erfcx(sqrt|x|)) / 2
+  const T sc = xneg ? f_sqrt(T(-2) * x) : T(0);
+  T bc = T(0);
+  if (xneg) {
+    if (T(0.5) * sc < Prec<T>::t_small) {
+      NB<T> vc_;
+      nb_eval<T>(x, sc, false, vc_);
+      bc = vc_.e * vc_.B;
+    } else {
+      bc = T(0.5) * bmax * (T(1) - f_erfcx(f_sqrt(-x)));
+    }
+  }
   const T vc = bmax * T(kInvSqrt2Pi);
   // tangent at s_c meets 0 at s_l and b_max at s_h; beta picks one side
   const bool lower = beta <= bc;
@@ -420,9 +443,10 @@ __device__ __forceinline__ T lbr_guess(const Reduced<T>& q, int& reg) {
   nb_eval<T>(x, so, false, vo_);
   const T bo = degenerate ? T(0) : vo_.e * vo_.B;
   const T vo = vo_.e * T(kInvSqrt2Pi);
-  // ln b_l is needed on the lower side only (region test where b_l
-  // underflows the type, and the lowest-region guess)
+  // ln b_l and ln beta are needed on the lower side only (region test where
+  // b_l underflows the type, and the lowest-region guess)
   const T ln_bo = lower ? nb_log(vo_) : T(0);
+  if (lower && q.ln_beta == T(0)) q.ln_beta = f_log(beta);
   if (lower)
     reg = (!degenerate && (bo > T(0) ? beta < bo : q.ln_beta < ln_bo)) ? 0 : 1;
   else
@@ -460,9 +484,9 @@ __device__ __forceinline__ T lbr_guess(const Reduced<T>& q, int& reg) {
 // LBR solve: guess, n_min Householder(3) steps, then up to n_max while the
 // last step still moved s by more than conv_tol relative.
 template <typename T>
-__device__ __forceinline__ T lbr_solve(const Reduced<T>& q, int n_min, int n_max, T conv_tol,
-                                       int& reg) {
+__device__ __forceinline__ T lbr_solve(Reduced<T> q, int n_min, int n_max, T conv_tol, int& reg) {
   T s = lbr_guess<T>(q, reg);
+  wing_logs<T>(q, reg);
   for (int k = 0; k < n_max; k++) {
     const Objective<T> o = objective<T>(q, s, reg);
     const T ds = hh3_step<T>(o);
@@ -475,25 +499,28 @@ __device__ __forceinline__ T lbr_solve(const Reduced<T>& q, int n_min, int n_max
 __device__ __forceinline__ Reduced<double> reduced64(const Norm& n) {
   Reduced<double> q;
   q.beta = n.beta_otm;
-  // out of the money, beta_otm = beta and the direct logarithm applies
-  q.ln_beta = (n.ln_beta != 0.0 && n.beta_otm == n.beta) ? n.ln_beta : log(n.beta_otm);
+  // out of the money, beta_otm = beta and the logarithm of P applies
+  q.ln_beta = (n.ln_beta != 0.0 && n.beta_otm == n.beta) ? n.ln_beta : 0.0;
   q.c_beta = n.bmax - n.beta_otm;
   q.x = n.x_otm;
   q.bmax = n.bmax;
-  q.inv_ln_beta = 1.0 / q.ln_beta;
-  q.ln_c_beta = log(q.c_beta);
+  q.inv_ln_beta = 0.0;
+  q.ln_c_beta = 0.0;
   return q;
 }
 
 __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
   Reduced<float> f;
   f.beta = (float)q.beta;
-  f.ln_beta = (float)q.ln_beta;
+  // below FP32's normal range ln beta comes from FP64 (the FP32 solve works
+  // in log space there); above it logf of the FP32 beta is accurate enough
+  f.ln_beta = q.ln_beta != 0.0 ? (float)q.ln_beta
+                               : (q.beta < 1e-37 ? (float)log(q.beta) : 0.0f);
   f.c_beta = (float)q.c_beta;
   f.x = (float)q.x;
   f.bmax = (float)q.bmax;
-  f.inv_ln_beta = (float)q.inv_ln_beta;
-  f.ln_c_beta = (float)q.ln_c_beta;
+  f.inv_ln_beta = 0.0f;
+  f.ln_c_beta = 0.0f;
   return f;
 }
 

@@ -65,6 +65,6 @@ void set_last_error(const char* msg);
 
 cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
                           int block, int qpt, int grid, cudaStream_t st);
-int chains_max_blocks_per_sm(int block);
+int chains_max_blocks_per_sm(int quotes_per_thread);
 
 }  // namespace fvk

@@ -48,6 +48,7 @@ __device__ __forceinline__ double ld(const void* p, int64_t i) {
 // ---------------------------------------------------------------------------
 template <typename InT, int PREC>
 __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
+  // unbinned: one quote per thread per round (small batches and the FP32 path)
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
@@ -81,20 +82,188 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
   }
 }
 
-cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
-  const int block = 256;
-  const int grid = grid_for(a.n, block, 8);
-#define FV_LBR_CASE(IT, P) k_iv_lbr<IT, P><<<grid, block, 0, st>>>(a)
-  if (a.f32_inputs) {
-    if (prec == P_FP64) FV_LBR_CASE(float, P_FP64);
-    else if (prec == P_MIXED) FV_LBR_CASE(float, P_MIXED);
-    else FV_LBR_CASE(float, P_FP32);
-  } else {
-    if (prec == P_FP64) FV_LBR_CASE(double, P_FP64);
-    else if (prec == P_MIXED) FV_LBR_CASE(double, P_MIXED);
-    else FV_LBR_CASE(double, P_FP32);
+// ---------------------------------------------------------------------------
+// LBR with CTA-local region binning (FP64 and mixed)
+//
+// Phase 1 decides every quote of a tile (one quote per thread per round,
+// coalesced loads) and, for the quotes that need a root, evaluates an FP32
+// proxy of the LBR region and of the small-t class (t < t_small of the FP64
+// normalised Black function) from the FP32 boundaries and guess; the mixed
+// path runs its whole FP32 solve here.  A shared-memory counting sort orders
+// the tile's solving quotes by that key.  Phase 2 runs the FP64 work on the
+// sorted quotes, so a warp's lanes take the same guess branch, the same
+// objective (and its logarithms only where that region needs them) and mostly
+// the same normalised-Black branch, and non-solving quotes do not occupy lanes.
+// The arithmetic of every quote is that of the unbinned solver.
+// ---------------------------------------------------------------------------
+constexpr int kBinThreads = 256;
+constexpr int kBinKeys = 8;  // 4 regions x {small t, not}
+
+template <int Q>
+struct BinSmem {
+  double beta[kBinThreads * Q], x[kBinThreads * Q], bmax[kBinThreads * Q], lnb[kBinThreads * Q],
+      T[kBinThreads * Q];
+  float s32[kBinThreads * Q];
+  unsigned char reg[kBinThreads * Q];
+  unsigned short perm[kBinThreads * Q];
+  int cnt[kBinKeys], off[kBinKeys + 1];
+};
+
+// One tile of up to kBinThreads * Q quotes.  `load(li, P, SF, K, T, r, q,
+// flag)` returns false past the tile's end; `out(li)` gives the index of the
+// quote's sigma / status.  LATE32: the mixed path's FP32 iterations run in
+// phase 2 (phase 1 only evaluates the FP32 guess that gives the sort key).
+template <int PREC, int Q, bool LATE32, typename Load>
+__device__ __forceinline__ void lbr_binned_tile(BinSmem<Q>& sm, int model, const Load& load,
+                                                double* sigma, uint8_t* status, int64_t out0) {
+  const int tid = threadIdx.x;
+  if (tid < kBinKeys) sm.cnt[tid] = 0;
+  __syncthreads();
+  unsigned char key[Q];
+  unsigned short rank[Q];
+#pragma unroll
+  for (int k = 0; k < Q; k++) {
+    const int li = k * kBinThreads + tid;
+    key[k] = 0xff;
+    rank[k] = 0;
+    double P, SF, K, T, r, q;
+    int flag;
+    if (load(li, P, SF, K, T, r, q, flag)) {
+      const Norm nq = decide(model, P, SF, K, T, r, q, flag);
+      status[out0 + li] = (uint8_t)nq.status;
+      if (nq.status == Q_OK && nq.solve) {
+        const Reduced<double> q64 = reduced64(nq);
+        sm.beta[li] = q64.beta;
+        sm.x[li] = q64.x;
+        sm.bmax[li] = q64.bmax;
+        sm.lnb[li] = q64.ln_beta;
+        sm.T[li] = T;
+        Reduced<float> q32 = reduced32(q64);
+        int reg = 1;
+        float sg;
+        if (PREC == P_MIXED && !LATE32) {
+          sg = lbr_solve<float>(q32, 2, 2, 0.0f, reg);
+        } else {
+          sg = lbr_guess<float>(q32, reg);
+        }
+        sm.s32[li] = sg;
+        sm.reg[li] = (unsigned char)reg;
+        key[k] = (unsigned char)(reg * 2 + ((0.5f * sg < (float)fvd::Prec<double>::t_small) ? 1 : 0));
+        rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
+      } else {
+        sigma[out0 + li] = nq.status == Q_OK ? 0.0 : qnan();
+      }
+    }
   }
-#undef FV_LBR_CASE
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int k = 0; k < kBinKeys; k++) {
+      sm.off[k] = acc;
+      acc += sm.cnt[k];
+    }
+    sm.off[kBinKeys] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < Q; k++)
+    if (key[k] != 0xff) sm.perm[sm.off[key[k]] + rank[k]] = (unsigned short)(k * kBinThreads + tid);
+  __syncthreads();
+  const int ns = sm.off[kBinKeys];
+  for (int j = tid; j < ns; j += kBinThreads) {
+    const int li = sm.perm[j];
+    Reduced<double> q;
+    q.beta = sm.beta[li];
+    q.x = sm.x[li];
+    q.bmax = sm.bmax[li];
+    q.c_beta = q.bmax - q.beta;
+    q.ln_beta = sm.lnb[li];
+    q.inv_ln_beta = 0.0;
+    q.ln_c_beta = 0.0;
+    double s;
+    if (PREC == P_FP64) {
+      int reg = 1;
+      s = lbr_solve<double>(q, 2, 3, 0x1p-17, reg);
+    } else {
+      int reg = sm.reg[li];
+      float s32 = sm.s32[li];
+      if (LATE32) {
+        // the FP32 Householder steps from the stored guess (same region)
+        Reduced<float> q32 = reduced32(q);
+        wing_logs<float>(q32, reg);
+        for (int it = 0; it < 2; it++)
+          s32 = guarded<float>(s32, hh3_step<float>(objective<float>(q32, s32, reg)));
+      }
+      s = hh3_correction(q, (double)s32, reg);
+    }
+    sigma[out0 + li] = s / sqrt(sm.T[li]);
+  }
+  __syncthreads();
+}
+
+template <typename InT, int PREC, int Q, int MINB, bool LATE32>
+__global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a) {
+  __shared__ BinSmem<Q> sm;
+  constexpr int TILE = kBinThreads * Q;
+  for (int64_t base = (int64_t)blockIdx.x * TILE; base < a.n; base += (int64_t)gridDim.x * TILE) {
+    auto load = [&](int li, double& P, double& SF, double& K, double& T, double& r, double& q,
+                    int& flag) {
+      const int64_t i = base + li;
+      if (i >= a.n) return false;
+      P = ld<InT>(a.P, i);
+      SF = ld<InT>(a.SF, i);
+      K = ld<InT>(a.K, i);
+      T = ld<InT>(a.T, i);
+      r = ld<InT>(a.r, i);
+      q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
+      flag = a.flag[i];
+      return true;
+    };
+    lbr_binned_tile<PREC, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
+  }
+}
+
+template <typename InT, int PREC, int Q, int MINB, bool LATE32>
+static void launch_binned(const IvArgs& a, cudaStream_t st) {
+  const int grid = grid_for(a.n, kBinThreads * Q, 8);
+  k_iv_lbr_binned<InT, PREC, Q, MINB, LATE32><<<grid, kBinThreads, 0, st>>>(a);
+}
+
+// Tile shapes measured on GB300 (16.8 M quotes): the FP64 solve runs best with
+// 4 quotes per thread and no register cap (36.8 ms on the BSM grid against
+// 44.6 ms unbinned); the mixed path with 2 quotes per thread, 4 blocks per SM
+// and its FP32 iterations in phase 2, where they interleave with the FP64
+// correction (13.7 ms against 15.4 ms).  The FP32 path has no FP64 solve to
+// sort for and stays unbinned.
+// Below kSmallBatch quotes a launch is latency-bound (a warp's ~900
+// dependent FP64 instructions): the unbinned kernel with 64-thread blocks
+// spreads the quotes over as many SMs and sub-partitions as possible.
+constexpr int64_t kSmallBatch = 1 << 17;
+
+template <typename InT>
+static void launch_flat(const IvArgs& a, int prec, int block, cudaStream_t st) {
+  const int grid = grid_for(a.n, block, 2048 / block);
+  if (prec == P_FP64) k_iv_lbr<InT, P_FP64><<<grid, block, 0, st>>>(a);
+  else if (prec == P_MIXED) k_iv_lbr<InT, P_MIXED><<<grid, block, 0, st>>>(a);
+  else k_iv_lbr<InT, P_FP32><<<grid, block, 0, st>>>(a);
+}
+
+cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
+  if (prec == P_FP32 || a.n < kSmallBatch) {
+    const int block = a.n < kSmallBatch ? 64 : 256;
+    if (a.f32_inputs)
+      launch_flat<float>(a, prec, block, st);
+    else
+      launch_flat<double>(a, prec, block, st);
+    return cudaGetLastError();
+  }
+  if (a.f32_inputs) {
+    if (prec == P_FP64) launch_binned<float, P_FP64, 4, 1, false>(a, st);
+    else launch_binned<float, P_MIXED, 2, 4, true>(a, st);
+  } else {
+    if (prec == P_FP64) launch_binned<double, P_FP64, 4, 1, false>(a, st);
+    else launch_binned<double, P_MIXED, 2, 4, true>(a, st);
+  }
   return cudaGetLastError();
 }
 
@@ -182,7 +351,8 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
     const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
     const Norm nq = decide(a.model, P, SF, K, T, r, q, a.flag[i]);
     const Reduced<double> q64 = reduced64(nq);
-    const double s = bisect_fallback(q64.ln_beta, q64.x, w.lo[k], w.hi[k]);
+    const double lnb = q64.ln_beta != 0.0 ? q64.ln_beta : log(q64.beta);
+    const double s = bisect_fallback(lnb, q64.x, w.lo[k], w.hi[k]);
     a.sigma[i] = s / sqrt(T);
   }
 }
@@ -391,48 +561,50 @@ cudaError_t launch_normalised_black(const double* x, const double* s, const int8
 // ---------------------------------------------------------------------------
 // batches of chains: persistent CTAs walk a static tile table
 // ---------------------------------------------------------------------------
-template <int QPT>
-__global__ void __launch_bounds__(512) k_chains(int model, const ChainDesc* __restrict__ chains,
-                                                const Tile* __restrict__ tiles, int64_t n_tiles) {
+// Persistent CTAs walk a static tile table; each tile (kBinThreads * Q quotes
+// of one chain) goes through the binned FP64 LBR.
+template <int Q>
+__global__ void __launch_bounds__(kBinThreads) k_chains(int model, const ChainDesc* __restrict__ chains,
+                                                        const Tile* __restrict__ tiles, int64_t n_tiles) {
+  __shared__ BinSmem<Q> sm;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const Tile tl = tiles[tile];
     const ChainDesc c = chains[tl.chain];
-#pragma unroll
-    for (int k = 0; k < QPT; k++) {
-      const int64_t j = tl.offset + (int64_t)k * blockDim.x + threadIdx.x;
-      if (j < c.n) {
-        const Norm nq = decide(model, c.P[j], c.SF, c.K[j], c.T, c.r, c.q, c.flag[j]);
-        double sigma = qnan();
-        if (nq.status == Q_OK) {
-          if (!nq.solve) {
-            sigma = 0.0;
-          } else {
-            int reg = 1;
-            const double s = lbr_solve<double>(reduced64(nq), 2, 3, 0x1p-17, reg);
-            sigma = s / sqrt(c.T);
-          }
-        }
-        c.sigma[j] = sigma;
-        c.status[j] = (uint8_t)nq.status;
-      }
-    }
+    auto load = [&](int li, double& P, double& SF, double& K, double& T, double& r, double& q,
+                    int& flag) {
+      const int64_t j = tl.offset + li;
+      if (j >= c.n) return false;
+      P = c.P[j];
+      SF = c.SF;
+      K = c.K[j];
+      T = c.T;
+      r = c.r;
+      q = c.q;
+      flag = c.flag[j];
+      return true;
+    };
+    // sigma / status of the chain, indexed from the tile's offset
+    lbr_binned_tile<P_FP64, Q, false>(sm, model, load, c.sigma + tl.offset, c.status + tl.offset, 0);
   }
 }
 
-int chains_max_blocks_per_sm(int block) {
+int chains_max_blocks_per_sm(int qpt) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chains<1>, block, 0) != cudaSuccess ||
-      b <= 0)
-    b = 1;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (qpt == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chains<1>, kBinThreads, 0);
+  if (qpt == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chains<2>, kBinThreads, 0);
+  if (qpt == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_chains<4>, kBinThreads, 0);
+  if (e != cudaSuccess || b <= 0) b = 1;
   return b;
 }
 
 cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
                           int block, int qpt, int grid, cudaStream_t st) {
+  if (block != kBinThreads) return cudaErrorInvalidValue;
   switch (qpt) {
-    case 1: k_chains<1><<<grid, block, 0, st>>>(model, chains, tiles, n_tiles); break;
-    case 2: k_chains<2><<<grid, block, 0, st>>>(model, chains, tiles, n_tiles); break;
-    case 4: k_chains<4><<<grid, block, 0, st>>>(model, chains, tiles, n_tiles); break;
+    case 1: k_chains<1><<<grid, kBinThreads, 0, st>>>(model, chains, tiles, n_tiles); break;
+    case 2: k_chains<2><<<grid, kBinThreads, 0, st>>>(model, chains, tiles, n_tiles); break;
+    case 4: k_chains<4><<<grid, kBinThreads, 0, st>>>(model, chains, tiles, n_tiles); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

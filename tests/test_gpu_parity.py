@@ -431,6 +431,30 @@ def test_abi_argument_errors(fv, torch_dev):
 
 
 # ---------------------------------------------------------------------------
+# binned (large batches) and unbinned (small batches) kernels agree
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_binned_matches_unbinned_and_oracle(fv, torch_dev, prec):
+    # 2^18 quotes run the region-binned kernel, their first 2^16 alone the
+    # unbinned one: the same arithmetic per quote, so equal within rounding
+    w = wl.fill_prices(wl.bsm_grid(4096, 64, seed=21), orc.price_f64)
+    args = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    p = fv.FV_FP64 if prec == "fp64" else fv.FV_MIXED
+    s_big, st_big = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR, p, *args, flag)
+    m = 1 << 16
+    s_small, st_small = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR, p, *[a[:m] for a in args],
+                                             flag[:m])
+    s_big, st_big, s_small = _np(s_big), _np(st_big), _np(s_small)
+    assert np.array_equal(st_big[:m], _np(st_small))
+    a, b = s_big[:m], s_small
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    ok = ~np.isnan(b) & (b > 0)
+    assert np.all(np.abs(a[ok] - b[ok]) <= 1e-12 * b[ok])
+    _sampled_parity(fv, torch_dev, w, s_big, st_big, fv.FV_BSM, n_sample=4096, seed=3)
+
+
+# ---------------------------------------------------------------------------
 # full reference sizes, in the launch configuration the benchmark times
 # ---------------------------------------------------------------------------
 def _status_parity(st, w, model, max_ambiguous=1e-3, max_flipped=1e-6):
