@@ -114,13 +114,32 @@ fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
  *   FV_FP32:  the LBR in FP32 only (relative error about 1e-5); the
  *             normalisation, status decision and intrinsic subtraction stay
  *             FP64, so the status is the FP64 rule's.
+ * FV_HALLEY with FV_FP32 is the paper's throughput path for float32 label
+ * pipelines (Section 2.2): eight Halley sweeps in FP32 on the direct residual
+ * e^{x/2} Phi(h+t) - e^{-x/2} Phi(h-t) with plain FP32 normal CDFs, and an
+ * FP32 bisection fallback on the quotes that fail the convergence test (about
+ * five digits where the normalised vega exceeds 1e-8; the plain residual
+ * loses the deep wings).  It uses the library-owned workspace like
+ * fv_implied_vol.  FV_HALLEY with FV_MIXED is FV_ERR_UNSUPPORTED.
  * in_dtype says whether price, S_or_F, K, T, r, q point to double or float.
- * Only FV_LBR is supported with FV_MIXED / FV_FP32 (else FV_ERR_UNSUPPORTED).
  * out_sigma is always FP64. */
 fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precision,
                          fv_dtype in_dtype, const void* price, const void* S_or_F, const void* K,
                          const void* T, const void* r, const void* q, const int8_t* flag,
                          int64_t n, double* out_sigma, uint8_t* status, void* stream);
+
+/* Implied volatility with strided inputs (Section 2.1: the entry points
+ * accept broadcastable arrays).  `strides` is a HOST array of 7 element
+ * strides for price, S_or_F, K, T, r, q and flag, in that order: quote i reads
+ * element i * stride, so 0 broadcasts one value (a scalar spot, rate or
+ * maturity for a whole strip) and 1 is a contiguous array.  Negative strides
+ * are FV_ERR_ARG.  Outputs stay contiguous.  Otherwise as fv_implied_vol_ex
+ * (the Halley solver takes the library-owned workspace). */
+fv_err fv_implied_vol_strided(fv_model model, fv_solver solver, fv_precision precision,
+                              fv_dtype in_dtype, const void* price, const void* S_or_F,
+                              const void* K, const void* T, const void* r, const void* q,
+                              const int8_t* flag, const int64_t* strides, int64_t n,
+                              double* out_sigma, uint8_t* status, void* stream);
 
 /* The five Greeks (Section 3 "Greeks": vectorized_{delta,gamma,theta,rho,vega}
  * and get_all_greeks, computed in one pass sharing d1/d2).  py_vollib scaling:

@@ -697,6 +697,11 @@ void or_iv_lbr(int model, const double* P, const double* S_or_F, const double* K
  * lowest wing, where b - beta does). */
 static double bisect_fallback(double beta, double x, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
+  /* residual increasing in s: ln b - ln beta, or above b_max / 2 the
+   * log-complement ln(b_max - beta) - ln(b_max - b) */
+  const double bmax = exp(0.5 * x);
+  const int upper = beta > 0.5 * bmax;
+  const double ln_beta = log(beta), ln_c_beta = upper ? log(bmax - beta) : 0.0;
   if (!isfinite(hi)) {
     hi = fmax(2.0 * lo, 1e-3);
     while (nb_d(x, hi) <= beta && hi < 1e6) {
@@ -711,19 +716,26 @@ static double bisect_fallback(double beta, double x, double lo, double hi) {
       lo *= 0.5;
     }
   }
-  const double ln_beta = log(beta);
   double s = 0.5 * (lo + hi);
   for (int it = 0; it < 400; it++) {
-    double L, qb;
-    nb_log_d(x, s, &L, &qb);
-    const double f = L - ln_beta;
+    double f, fp;
+    if (upper) {
+      const double c = nbc_d(x, s);
+      f = ln_c_beta - log(c);
+      fp = vega_d(x, s) / c;
+    } else {
+      double L, qb;
+      nb_log_d(x, s, &L, &qb);
+      f = L - ln_beta;
+      fp = qb;
+    }
     if (f < 0)
       lo = s;
     else if (f > 0)
       hi = s;
     else
       return s;
-    const double sn = s - f / qb;
+    const double sn = s - f / fp;
     const double next = (sn > lo && sn < hi) ? sn : 0.5 * (lo + hi);
     const double ds = next - s;
     s = next;
@@ -736,9 +748,11 @@ static double halley_otm(double beta, double x, int* fell_back) {
   /* Brenner-Subrahmanyam: at the money b ~ s / sqrt(2 pi) */
   double s = SQRT_2PI * beta;
   double lo = 0.0, hi = INFINITY, newton_err = INFINITY;
+  /* g = b - beta, evaluated as (b_max - beta) - (b_max - b) above b_max / 2 */
+  const double bmax = exp(0.5 * x);
+  const int upper = beta > 0.5 * bmax;
   for (int k = 0; k < HALLEY_STEPS; k++) {
-    const double b = nb_d(x, s);
-    const double g = b - beta;
+    const double g = upper ? (bmax - beta) - nbc_d(x, s) : nb_d(x, s) - beta;
     if (g < 0)
       lo = s;
     else if (g > 0)

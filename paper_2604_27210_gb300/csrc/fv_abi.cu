@@ -103,11 +103,16 @@ fv_err cached_workspace(size_t need, void** out) {
 fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const void* P,
               const void* SF, const void* K, const void* T, const void* r, const void* q,
               const int8_t* flag, int64_t n, double* sigma, uint8_t* status, void* ws,
-              size_t ws_bytes, bool use_cache, void* stream) {
+              size_t ws_bytes, bool use_cache, void* stream, const int64_t* strides = nullptr) {
   fv_err e = check_iv_args(fn, model, solver, P, SF, K, T, r, q, flag, n, sigma, status);
   if (e != FV_SUCCESS || n == 0) return e;
-  if (solver == FV_HALLEY && prec != fvk::P_FP64)
-    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 only", fn);
+  if (strides)
+    for (int k = 0; k < 7; k++)
+      if (strides[k] < 0) return fail(FV_ERR_ARG, "%s: stride %d is negative", fn, k);
+  if (solver == FV_HALLEY && prec == fvk::P_MIXED)
+    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 or FP32", fn);
+  if (solver == FV_HALLEY && prec == fvk::P_FP32 && !use_cache)
+    return fail(FV_ERR_UNSUPPORTED, "%s: FP32 Halley takes the library workspace", fn);
   const size_t need = solver == FV_HALLEY ? fvk::halley_workspace_bytes(n) : 0;
   if (solver == FV_HALLEY && !use_cache) {
     if (ws == nullptr) return fail(FV_ERR_ARG, "%s: workspace is NULL", fn);
@@ -131,9 +136,11 @@ fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const v
   a.n = n;
   a.sigma = sigma;
   a.status = status;
+  for (int k = 0; k < 7; k++) a.st[k] = strides ? strides[k] : 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (solver == FV_LBR) return cuda_result(fvk::launch_iv_lbr(a, prec, st), fn);
   if (use_cache && (e = cached_workspace(need, &ws)) != FV_SUCCESS) return e;
+  if (prec == fvk::P_FP32) return cuda_result(fvk::launch_iv_halley32(a, ws, st), fn);
   return cuda_result(fvk::launch_iv_halley(a, ws, st), fn);
 }
 
@@ -266,10 +273,25 @@ fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precisio
     return fail(FV_ERR_ARG, "%s: unknown precision %d", fn, (int)precision);
   if (in_dtype != FV_DTYPE_F64 && in_dtype != FV_DTYPE_F32)
     return fail(FV_ERR_ARG, "%s: unknown input dtype %d", fn, (int)in_dtype);
-  if (solver == FV_HALLEY && precision != FV_FP64)
-    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 only", fn);
+  if (solver == FV_HALLEY && precision == FV_MIXED)
+    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 or FP32", fn);
   return run_iv(fn, model, solver, (int)precision, in_dtype == FV_DTYPE_F32, price, S_or_F, K, T, r,
                 q, flag, n, out_sigma, status, nullptr, 0, true, stream);
+}
+
+fv_err fv_implied_vol_strided(fv_model model, fv_solver solver, fv_precision precision,
+                              fv_dtype in_dtype, const void* price, const void* S_or_F,
+                              const void* K, const void* T, const void* r, const void* q,
+                              const int8_t* flag, const int64_t* strides, int64_t n,
+                              double* out_sigma, uint8_t* status, void* stream) {
+  const char* fn = "fv_implied_vol_strided";
+  if (precision != FV_FP64 && precision != FV_MIXED && precision != FV_FP32)
+    return fail(FV_ERR_ARG, "%s: unknown precision %d", fn, (int)precision);
+  if (in_dtype != FV_DTYPE_F64 && in_dtype != FV_DTYPE_F32)
+    return fail(FV_ERR_ARG, "%s: unknown input dtype %d", fn, (int)in_dtype);
+  if (n > 0) FV_REQUIRE(strides, "strides", fn);
+  return run_iv(fn, model, solver, (int)precision, in_dtype == FV_DTYPE_F32, price, S_or_F, K, T, r,
+                q, flag, n, out_sigma, status, nullptr, 0, true, stream, strides);
 }
 
 fv_err fv_greeks(fv_model model, const int8_t* flag, const double* S_or_F, const double* K,

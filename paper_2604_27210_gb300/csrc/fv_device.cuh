@@ -535,13 +535,19 @@ struct HalleyOut {
   bool converged;
 };
 
-__device__ __forceinline__ HalleyOut halley_solve(double beta, double x) {
+// The residual g = b - beta is evaluated as (b_max - beta) - (b_max - b) when
+// beta > b_max/2: b_max - b then comes from the cancellation-free complement,
+// so g carries an error relative to b_max - b instead of to b_max (the same
+// function, with the same Halley step).
+__device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double bmax) {
+  const bool upper = beta > 0.5 * bmax;
+  const double c_beta = bmax - beta;
   double s = kSqrt2Pi * beta;  // Brenner-Subrahmanyam: b ~ s/sqrt(2 pi) at the money
   double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
   for (int k = 0; k < kHalleySteps; k++) {
     NB<double> v;
-    nb_eval<double>(x, s, false, v);
-    const double g = v.e * v.B - beta;
+    nb_eval<double>(x, s, upper, v);
+    const double g = upper ? c_beta - v.e * v.B : v.e * v.B - beta;
     if (g < 0.0) {
       lo = s;
     } else if (g > 0.0) {
@@ -568,18 +574,25 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x) {
   return o;
 }
 
-// bisection on ln b - ln beta in [lo, hi], Newton steps kept when inside
-// (ln_beta is passed in: for subnormal-range prices it comes from log(P))
-__device__ __forceinline__ double bisect_fallback(double ln_beta, double x, double lo, double hi) {
+// Bisection in [lo, hi] on a residual increasing in s, Newton steps kept when
+// inside: ln b - ln beta, or for beta > b_max/2 the log-complement
+// ln(b_max - beta) - ln(b_max - b) (ln_beta is passed in: for subnormal-range
+// prices it comes from log(P)).
+__device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, double x,
+                                                  double bmax, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
+  const bool upper = beta > 0.5 * bmax;
+  const double ln_c_beta = upper ? log(bmax - beta) : 0.0;
   NB<double> v;
+  // f(s) > 0 iff b(s) > beta
+  auto resid = [&](double s_) {
+    nb_eval<double>(x, s_, upper, v);
+    return upper ? ln_c_beta - nb_log(v) : nb_log(v) - ln_beta;
+  };
   if (!isfinite(hi)) {
-    // expand from max(2 lo, 1e-3): a Halley run that never overshot leaves lo
-    // anywhere down to the Brenner-Subrahmanyam guess
     hi = fmax(2.0 * lo, 1e-3);
     for (int it = 0; it < 64; it++) {
-      nb_eval<double>(x, hi, false, v);
-      if (nb_log(v) > ln_beta) break;
+      if (resid(hi) > 0.0) break;
       lo = hi;
       hi *= 2.0;
     }
@@ -587,28 +600,116 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double x, doub
   if (!(lo > 0.0)) {
     lo = 0.5 * hi;
     for (int it = 0; it < 1100; it++) {
-      nb_eval<double>(x, lo, false, v);
-      if (nb_log(v) < ln_beta) break;
+      if (resid(lo) < 0.0) break;
       hi = lo;
       lo *= 0.5;
     }
   }
   double s = 0.5 * (lo + hi);
   for (int it = 0; it < 200; it++) {
-    nb_eval<double>(x, s, false, v);
-    const double f = nb_log(v) - ln_beta;
+    const double f = resid(s);
     if (f < 0.0)
       lo = s;
     else if (f > 0.0)
       hi = s;
     else
       break;
+    // f' = b'/b (lower form) or b'/(b_max - b) (upper form)
     const double qw = kInvSqrt2Pi / v.B;
     const double sn = s - f / qw;
     const double next = (sn > lo && sn < hi) ? sn : 0.5 * (lo + hi);
     const double ds = next - s;
     s = next;
     if (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi) break;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Halley x8 in FP32 on the direct residual with plain Phi (the paper's
+// throughput path for float32 label pipelines, Section 2.2)
+// ---------------------------------------------------------------------------
+constexpr float kHalley32ConvTol = 1e-5f;
+
+// b(x, s) = e^{x/2} Phi(h+t) - e^{-x/2} Phi(h-t), x <= 0, plain FP32 CDFs;
+// with `upper` the complement b_max - b = e^{x/2} Phi(-h-t) + e^{-x/2} Phi(h-t)
+__device__ __forceinline__ float nb_plain32(float x, float s, float ep, float em, bool upper,
+                                            float& bp, float& u) {
+  const float h = x / s, t = 0.5f * s;
+  bp = ep * (float)kInvSqrt2Pi * expf(-0.5f * (h + t) * (h + t));
+  u = h * h / s - 0.25f * s;
+  return upper ? ep * normcdff(-(h + t)) + em * normcdff(h - t)
+               : ep * normcdff(h + t) - em * normcdff(h - t);
+}
+
+struct Halley32Out {
+  float s, lo, hi;
+  bool converged;
+};
+
+// beta and b_max - beta come from FP64; above b_max/2 the residual is
+// evaluated as (b_max - beta) - (b_max - b), as in the FP64 solver
+__device__ __forceinline__ Halley32Out halley32_solve(float beta, float c_beta, float x) {
+  const float ep = expf(0.5f * x), em = expf(-0.5f * x);
+  const bool upper = c_beta < beta;
+  float s = (float)kSqrt2Pi * beta;
+  float lo = 0.0f, hi = __int_as_float(0x7f800000), nerr = hi;
+  for (int k = 0; k < kHalleySteps; k++) {
+    float bp, u;
+    const float v = nb_plain32(x, s, ep, em, upper, bp, u);
+    const float g = upper ? c_beta - v : v - beta;
+    if (g < 0.0f) {
+      lo = s;
+    } else if (g > 0.0f) {
+      hi = s;
+    } else {
+      nerr = (g == 0.0f) ? 0.0f : hi;
+      break;
+    }
+    nerr = fabsf(g / bp) / s;
+    float sn = s - 2.0f * g / (2.0f * bp - g * u);
+    if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5f * (lo + hi) : 2.0f * s;
+    s = sn;
+  }
+  Halley32Out o;
+  o.s = s;
+  o.lo = lo;
+  o.hi = hi;
+  o.converged = isfinite(s) && s > 0.0f && nerr <= kHalley32ConvTol;
+  return o;
+}
+
+// FP32 bisection on the same residual, Newton steps kept inside the bracket
+__device__ __forceinline__ float bisect32_fallback(float beta, float c_beta, float x, float lo,
+                                                   float hi) {
+  const float ep = expf(0.5f * x), em = expf(-0.5f * x);
+  const bool upper = c_beta < beta;
+  float bp, u;
+  auto resid = [&](float s_) {
+    const float v = nb_plain32(x, s_, ep, em, upper, bp, u);
+    return upper ? c_beta - v : v - beta;
+  };
+  if (!isfinite(hi)) {
+    hi = fmaxf(2.0f * lo, 1e-3f);
+    for (int it = 0; it < 64 && resid(hi) <= 0.0f; it++) {
+      lo = hi;
+      hi *= 2.0f;
+    }
+  }
+  float s = 0.5f * (lo + hi);
+  for (int it = 0; it < 100; it++) {
+    const float g = resid(s);
+    if (g < 0.0f)
+      lo = s;
+    else if (g > 0.0f)
+      hi = s;
+    else
+      break;
+    const float sn = s - g / bp;
+    const float next = (sn > lo && sn < hi) ? sn : 0.5f * (lo + hi);
+    const float ds = next - s;
+    s = next;
+    if (fabsf(ds) <= 2.4e-7f * s || hi - lo <= 4.8e-7f * hi) break;
   }
   return s;
 }

@@ -18,6 +18,9 @@ struct IvArgs {
   int64_t n;
   double* sigma;
   uint8_t* status;
+  // element strides of P, S_or_F, K, T, r, q, flag (1 = contiguous, 0 = one
+  // value broadcast to every quote)
+  int64_t st[7];
 };
 
 // grid sizing: blocks for n quotes, capped at `per_sm` resident blocks per SM
@@ -29,6 +32,8 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
 // Halley workspace: [count u32 | pad to 16][idx u32 x n | pad to 16][lo f64 x n][hi f64 x n]
 size_t halley_workspace_bytes(int64_t n);
 cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st);
+// Halley x8 in FP32 on the plain-Phi residual (same workspace layout)
+cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st);
 
 cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const double* K,
                          const double* T, const double* r, const double* q, const double* sigma,

@@ -43,6 +43,19 @@ __device__ __forceinline__ double ld(const void* p, int64_t i) {
   return (double)__ldg(static_cast<const InT*>(p) + i);
 }
 
+// quote i of an IV call (strided / broadcast inputs)
+template <typename InT>
+__device__ __forceinline__ void load_quote(const IvArgs& a, int64_t i, double& P, double& SF,
+                                           double& K, double& T, double& r, double& q, int& flag) {
+  P = ld<InT>(a.P, i * a.st[0]);
+  SF = ld<InT>(a.SF, i * a.st[1]);
+  K = ld<InT>(a.K, i * a.st[2]);
+  T = ld<InT>(a.T, i * a.st[3]);
+  r = ld<InT>(a.r, i * a.st[4]);
+  q = (a.model == M_BSM) ? ld<InT>(a.q, i * a.st[5]) : 0.0;
+  flag = a.flag[i * a.st[6]];
+}
+
 // ---------------------------------------------------------------------------
 // implied volatility, LBR: FP64, mixed (FP32 bulk + one FP64 HH3 step), FP32
 // ---------------------------------------------------------------------------
@@ -51,10 +64,9 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
   // unbinned: one quote per thread per round (small batches and the FP32 path)
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
-    const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
-    const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
-    const int flag = a.flag[i];
+    double P, SF, K, T, r, q;
+    int flag;
+    load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     double sigma = qnan();
     if (nq.status == Q_OK) {
@@ -210,13 +222,7 @@ __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a) {
                     int& flag) {
       const int64_t i = base + li;
       if (i >= a.n) return false;
-      P = ld<InT>(a.P, i);
-      SF = ld<InT>(a.SF, i);
-      K = ld<InT>(a.K, i);
-      T = ld<InT>(a.T, i);
-      r = ld<InT>(a.r, i);
-      q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
-      flag = a.flag[i];
+      load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
       return true;
     };
     lbr_binned_tile<PREC, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
@@ -297,10 +303,9 @@ template <typename InT>
 __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
-    const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
-    const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
-    const int flag = a.flag[i];
+    double P, SF, K, T, r, q;
+    int flag;
+    load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     double sigma = qnan();
     bool fallback = false;
@@ -309,7 +314,7 @@ __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
       if (!nq.solve) {
         sigma = 0.0;
       } else {
-        const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm);
+        const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax);
         if (h.converged) {
           sigma = h.s / sqrt(T);
         } else {
@@ -346,15 +351,93 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += stride) {
     const int64_t i = w.idx[k];
-    const double P = ld<InT>(a.P, i), SF = ld<InT>(a.SF, i), K = ld<InT>(a.K, i);
-    const double T = ld<InT>(a.T, i), r = ld<InT>(a.r, i);
-    const double q = (a.model == M_BSM) ? ld<InT>(a.q, i) : 0.0;
-    const Norm nq = decide(a.model, P, SF, K, T, r, q, a.flag[i]);
+    double P, SF, K, T, r, q;
+    int flag;
+    load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     const Reduced<double> q64 = reduced64(nq);
     const double lnb = q64.ln_beta != 0.0 ? q64.ln_beta : log(q64.beta);
-    const double s = bisect_fallback(lnb, q64.x, w.lo[k], w.hi[k]);
+    const double s = bisect_fallback(lnb, q64.beta, q64.x, q64.bmax, w.lo[k], w.hi[k]);
     a.sigma[i] = s / sqrt(T);
   }
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(256) k_iv_halley32(IvArgs a, HalleyWs w) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    double P, SF, K, T, r, q;
+    int flag;
+    load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    double sigma = qnan();
+    bool fallback = false;
+    float lo = 0.0f, hi = 0.0f;
+    if (nq.status == Q_OK) {
+      if (!nq.solve) {
+        sigma = 0.0;
+      } else {
+        const Halley32Out h = halley32_solve((float)nq.beta_otm, (float)(nq.bmax - nq.beta_otm),
+                                             (float)nq.x_otm);
+        if (h.converged) {
+          sigma = (double)h.s / sqrt(T);
+        } else {
+          fallback = true;
+          lo = h.lo;
+          hi = h.hi;
+        }
+      }
+    }
+    a.sigma[i] = sigma;
+    a.status[i] = (uint8_t)nq.status;
+    const unsigned active = __activemask();
+    const unsigned m = __ballot_sync(active, fallback);
+    if (m) {
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(m) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(w.count, (unsigned)__popc(m));
+      base = __shfl_sync(active, base, leader);
+      if (fallback) {
+        const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+        w.idx[pos] = (unsigned)i;
+        w.lo[pos] = lo;
+        w.hi[pos] = hi;
+      }
+    }
+  }
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(256) k_halley32_fallback(IvArgs a, HalleyWs w) {
+  const int64_t cnt = (int64_t)*w.count;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += stride) {
+    const int64_t i = w.idx[k];
+    double P, SF, K, T, r, q;
+    int flag;
+    load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    const float s = bisect32_fallback((float)nq.beta_otm, (float)(nq.bmax - nq.beta_otm),
+                                      (float)nq.x_otm, (float)w.lo[k], (float)w.hi[k]);
+    a.sigma[i] = (double)s / sqrt(T);
+  }
+}
+
+cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st) {
+  const HalleyWs w = halley_ws(ws, a.n);
+  cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  const int block = 256;
+  const int grid = grid_for(a.n, block, 8);
+  if (a.f32_inputs) {
+    k_iv_halley32<float><<<grid, block, 0, st>>>(a, w);
+    k_halley32_fallback<float><<<grid, block, 0, st>>>(a, w);
+  } else {
+    k_iv_halley32<double><<<grid, block, 0, st>>>(a, w);
+    k_halley32_fallback<double><<<grid, block, 0, st>>>(a, w);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st) {

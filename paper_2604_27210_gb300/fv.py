@@ -22,7 +22,7 @@ FV_SUCCESS, FV_ERR_ARG, FV_ERR_CUDA, FV_ERR_UNSUPPORTED, FV_ERR_NOMEM = 0, -1, -
 
 # every symbol include/fv.h declares
 EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws",
-           "fv_implied_vol_ex", "fv_greeks", "fv_iv_adjoint", "fv_normalised_black",
+           "fv_implied_vol_ex", "fv_implied_vol_strided", "fv_greeks", "fv_iv_adjoint", "fv_normalised_black",
            "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
            "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_implied_vol_halley_noalloc",
            "fv_status_string", "fv_last_error"]
@@ -59,6 +59,8 @@ def _load():
     lib.fv_implied_vol_ws.argtypes = [_I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P,
                                       ctypes.c_size_t, _P]
     lib.fv_implied_vol_ex.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P]
+    lib.fv_implied_vol_strided.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P,
+                                           ctypes.POINTER(ctypes.c_int64), _N, _P, _P, _P]
     lib.fv_greeks.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P, _P, _P, _P]
     lib.fv_iv_adjoint.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _N,
                                   _P, _P, _P, _P, _P, _P, _P]
@@ -216,6 +218,38 @@ def fv_implied_vol_ex(model, solver, precision, price, S_or_F, K, T, r, q, flag,
                                   _ptr(out_sigma, n, _F64, "out_sigma"),
                                   _ptr(status, n, _U8, "status"), _stream(stream)),
            "fv_implied_vol_ex")
+    return out_sigma, status
+
+
+def fv_implied_vol_strided(model, solver, precision, price, S_or_F, K, T, r, q, flag,
+                           out_sigma=None, status=None, stream=None):
+    """Implied volatility where any input may hold one element (broadcast to
+    every quote, stride 0) or n elements (stride 1)."""
+    ins = [price, S_or_F, K, T, r, q, flag]
+    n = max(t.numel() for t in ins if t is not None)
+    f32 = price.dtype == torch.float32
+    dts = _F32 if f32 else _F64
+    strides = (ctypes.c_int64 * 7)()
+    ptrs = []
+    for k, (t, name) in enumerate(zip(ins, ("price", "S_or_F", "K", "T", "r", "q", "flag"))):
+        if t is None:
+            if name != "q" or model == FV_BSM:
+                raise ValueError("%s is required" % name)
+            ptrs.append(None)
+            strides[k] = 0
+            continue
+        m = t.numel()
+        if m not in (1, n):
+            raise ValueError("%s has %d elements: expected 1 or %d" % (name, m, n))
+        ptrs.append(_ptr(t, m, _I8 if name == "flag" else dts, name))
+        strides[k] = 0 if (m == 1 and n != 1) else 1
+    ref = price if price.numel() == n else S_or_F
+    out_sigma = torch.empty(n, dtype=torch.float64, device=ref.device) if out_sigma is None else out_sigma
+    status = torch.empty(n, dtype=torch.uint8, device=ref.device) if status is None else status
+    _check(_lib.fv_implied_vol_strided(model, solver, precision, FV_DTYPE_F32 if f32 else FV_DTYPE_F64,
+                                       *ptrs, strides, n, _ptr(out_sigma, n, _F64, "out_sigma"),
+                                       _ptr(status, n, _U8, "status"), _stream(stream)),
+           "fv_implied_vol_strided")
     return out_sigma, status
 
 

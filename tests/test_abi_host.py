@@ -72,7 +72,7 @@ def test_argument_errors_before_any_launch(lib):
     lib.fv_implied_vol_ex.restype = ctypes.c_int
     assert lib.fv_implied_vol_ex(0, 0, 7, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -1
     assert lib.fv_implied_vol_ex(0, 0, 0, 5, p, p, p, p, p, None, p, N(4), p, p, None) == -1
-    # the Halley solver runs in FP64 only
+    # the Halley solver has no mixed path
     assert lib.fv_implied_vol_ex(0, 1, 1, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -3
 
 

@@ -157,7 +157,7 @@ def bsm_grid_small():
     return w, _iv_ref(w)
 
 
-@pytest.mark.parametrize("mode", ["lbr", "halley", "mixed", "fp32"])
+@pytest.mark.parametrize("mode", ["lbr", "halley", "mixed", "fp32", "halley32"])
 def test_iv_bsm_grid(fv, torch_dev, bsm_grid_small, mode):
     w, (ref, st_ref, v, kap) = bsm_grid_small
     assert (st_ref == orc.BELOW_INTRINSIC).sum() > 0.03 * st_ref.size
@@ -165,14 +165,59 @@ def test_iv_bsm_grid(fv, torch_dev, bsm_grid_small, mode):
     flag = _dev(torch_dev, w["flag"])
     if mode in ("lbr", "halley"):
         s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR if mode == "lbr" else fv.FV_HALLEY, *args, flag)
+    elif mode == "halley32":
+        s, st = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_HALLEY, fv.FV_FP32, *args, flag)
     else:
         s, st = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR,
                                      fv.FV_MIXED if mode == "mixed" else fv.FV_FP32, *args, flag)
     assert np.array_equal(_np(st), st_ref)
     if mode == "fp32":
         _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=1e-5, name=mode)
+    elif mode == "halley32":
+        # the paper's float32 throughput path (plain-Phi residual): looser
+        _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=1e-4, name=mode)
     else:
         _check_sigma(_np(s), ref, st_ref, v, kap, tol_rest=1e-12, name=mode)
+
+
+def test_halley32_black76(fv, torch_dev, black76):
+    w, (ref, st_ref, v, kap) = black76
+    P, F, K, T, r, _ = _args(torch_dev, w)
+    s, st = fv.fv_implied_vol_ex(fv.FV_BLACK76, fv.FV_HALLEY, fv.FV_FP32, P, F, K, T, r, None,
+                                 _dev(torch_dev, w["flag"]))
+    assert np.array_equal(_np(st), st_ref)
+    # the paper's float32 throughput path: the plain-Phi residual loses about a
+    # digit to cancellation, so its bar is 1e-4 (the LBR FP32 path meets 1e-5)
+    _check_sigma(_np(s), ref, st_ref, v, kap, tol_gate=1e-4, name="halley32")
+
+
+def test_strided_broadcast_matches_arrays(fv, torch_dev):
+    torch, dev = torch_dev
+    # the paper's quick-use call shape: scalar S, t, r; arrays of strikes and flags
+    w = wl.fill_prices(wl.bsm_quotes(3000, seed=31), orc.price)
+    n = w["K"].size
+    scal = dict(S_or_F=100.0, T=0.25, r=0.05, q=0.01)
+    full = {k: np.full(n, v) for k, v in scal.items()}
+    full.update(K=w["K"], flag=w["flag"], model=2)
+    full["P"] = orc.price(2, full["S_or_F"], full["K"], full["T"], full["r"], full["q"],
+                          w["sigma_true"], full["flag"])
+    ref, st_ref, v, kap = _iv_ref(full)
+    one = lambda x: torch.tensor([x], dtype=torch.float64, device=dev)
+    for prec in (fv.FV_FP64, fv.FV_MIXED):
+        s_b, st_b = fv.fv_implied_vol_strided(2, fv.FV_LBR, prec, _dev(torch_dev, full["P"]),
+                                              one(100.0), _dev(torch_dev, full["K"]), one(0.25),
+                                              one(0.05), one(0.01), _dev(torch_dev, full["flag"]))
+        s_a, st_a = fv.fv_implied_vol_ex(2, fv.FV_LBR, prec, *_args(torch_dev, full),
+                                         _dev(torch_dev, full["flag"]))
+        assert torch.equal(st_a, st_b) and np.array_equal(_np(st_b), st_ref)
+        assert torch.equal(s_a.nan_to_num(-1), s_b.nan_to_num(-1))
+        _check_sigma(_np(s_b), ref, st_ref, v, kap, tol_rest=1e-12)
+    # a negative stride is an argument error
+    lib = fv.library()
+    import ctypes
+    st = (ctypes.c_int64 * 7)(1, 1, 1, 1, 1, -1, 1)
+    p = ctypes.c_void_p(s_b.data_ptr())
+    assert lib.fv_implied_vol_strided(2, 0, 0, 0, p, p, p, p, p, p, p, st, n, p, p, None) == fv.FV_ERR_ARG
 
 
 def test_iv_fp32_inputs(fv, torch_dev):
