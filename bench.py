@@ -203,24 +203,26 @@ def time_steps(torch, fn, steps, warmup, world_size):
     return total_ms, kernel_ms
 
 
+E2E_CHUNK = 1 << 21
+
+
 def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
     """The same metric through the public API from pinned host buffers: each step
-    copies the inputs host->device, solves, and reads sigma + status back."""
+    is one fv_implied_vol_host call, which copies that step's inputs to the
+    device and sigma + status back, in 2M-quote chunks overlapped with the
+    solve on two streams."""
     keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
     host = {k: t_dev[k].cpu().pin_memory() for k in keys}
-    dev = {k: torch.empty_like(t_dev[k]) for k in keys}
     n = t_dev["P"].numel()
-    out = torch.empty(n, dtype=torch.float64, device=t_dev["P"].device)
-    st = torch.empty(n, dtype=torch.uint8, device=t_dev["P"].device)
     out_h = torch.empty(n, dtype=torch.float64).pin_memory()
     st_h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    plan = fv.fv_stream_plan_create(E2E_CHUNK)
+    solver = fv.FV_HALLEY if path == "halley" else fv.FV_LBR
+    prec = {"lbr": fv.FV_FP64, "halley": fv.FV_FP64, "mixed": fv.FV_MIXED, "fp32": fv.FV_FP32}[path]
 
     def step():
-        for k in keys:
-            dev[k].copy_(host[k], non_blocking=True)
-        run_path(fv, dev, path, out, st)
-        out_h.copy_(out, non_blocking=True)
-        st_h.copy_(st, non_blocking=True)
+        plan.implied_vol(fv.FV_BSM, solver, prec, host["P"], host["S_or_F"], host["K"], host["T"],
+                         host["r"], host["q"], host["flag"], out_h, st_h)
 
     for _ in range(warmup):
         step()
@@ -237,6 +239,7 @@ def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
     ms = max(e0.elapsed_time(e1), 1e3 * wall) / steps
     h2d = sum(host[k].numel() * host[k].element_size() for k in keys)
     d2h = n * 9
+    plan.destroy()
     return ms, h2d, d2h
 
 

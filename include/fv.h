@@ -214,6 +214,29 @@ fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_p
 
 fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
 
+/* ---- host-resident batches: copies overlapped with the solve ----------- */
+/* A stream plan holds device staging for two chunks of up to chunk_quotes
+ * quotes (inputs, outputs and a Halley workspace) and two CUDA streams.
+ * Created once (allocates device memory); used by fv_implied_vol_host. */
+typedef struct fv_stream_plan fv_stream_plan;
+fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan);
+fv_err fv_stream_plan_destroy(fv_stream_plan* plan);
+
+/* Implied volatility of n quotes whose inputs and outputs are HOST arrays
+ * (page-locked memory lets the copies run concurrently with the solve;
+ * pageable memory works but serialises them).  The batch is cut into chunks
+ * that alternate between the plan's two streams: while chunk k solves, chunk
+ * k+1's inputs travel to the device and chunk k-1's sigma and status travel
+ * back.  The pipeline starts after the work already queued on `stream`, and
+ * `stream` waits for it, so the outputs are in place once `stream` has
+ * completed.  Arguments as fv_implied_vol_ex (contiguous arrays, q may be
+ * NULL unless FV_BSM); one call at a time per plan. */
+fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solver,
+                           fv_precision precision, fv_dtype in_dtype, const void* price,
+                           const void* S_or_F, const void* K, const void* T, const void* r,
+                           const void* q, const int8_t* flag, int64_t n, double* out_sigma,
+                           uint8_t* status, void* stream);
+
 /* ---- implied volatility without any device allocation ----------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
  * may not allocate device memory (a host process that pre-reserves all of it,

@@ -512,6 +512,139 @@ fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_p
   return FV_SUCCESS;
 }
 
+}  // extern "C"
+
+struct fv_stream_plan {
+  int64_t chunk;
+  void* in[2][6];
+  int8_t* flag[2];
+  double* sigma[2];
+  uint8_t* status[2];
+  void* ws[2];
+  size_t ws_bytes;
+  cudaStream_t st[2];
+  cudaEvent_t ev_start, ev_end[2];
+};
+
+extern "C" {
+
+fv_err fv_stream_plan_destroy(fv_stream_plan* p) {
+  if (!p) return FV_SUCCESS;
+  for (int b = 0; b < 2; b++) {
+    if (p->st[b]) cudaStreamSynchronize(p->st[b]);
+    for (int j = 0; j < 6; j++)
+      if (p->in[b][j]) cudaFree(p->in[b][j]);
+    if (p->flag[b]) cudaFree(p->flag[b]);
+    if (p->sigma[b]) cudaFree(p->sigma[b]);
+    if (p->status[b]) cudaFree(p->status[b]);
+    if (p->ws[b]) cudaFree(p->ws[b]);
+    if (p->st[b]) cudaStreamDestroy(p->st[b]);
+    if (p->ev_end[b]) cudaEventDestroy(p->ev_end[b]);
+  }
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  delete p;
+  return FV_SUCCESS;
+}
+
+fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan) {
+  const char* fn = "fv_stream_plan_create";
+  FV_REQUIRE(plan, "plan", fn);
+  *plan = nullptr;
+  if (chunk_quotes <= 0) return fail(FV_ERR_ARG, "%s: chunk_quotes must be positive", fn);
+  fv_err e = pending_error(fn);
+  if (e != FV_SUCCESS) return e;
+  fv_stream_plan* p = new fv_stream_plan();
+  memset(p, 0, sizeof(*p));
+  p->chunk = chunk_quotes;
+  p->ws_bytes = fvk::halley_workspace_bytes(chunk_quotes);
+  const size_t c = (size_t)chunk_quotes;
+  cudaError_t ce = cudaSuccess;
+  for (int b = 0; b < 2 && ce == cudaSuccess; b++) {
+    for (int j = 0; j < 6 && ce == cudaSuccess; j++) ce = cudaMalloc(&p->in[b][j], c * 8);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->flag[b], c);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->sigma[b], c * 8);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->status[b], c);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->ws[b], p->ws_bytes);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->st[b], cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_end[b], cudaEventDisableTiming);
+  }
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    fv_stream_plan_destroy(p);
+    return fail(FV_ERR_NOMEM, "%s: %s", fn, cudaGetErrorString(ce));
+  }
+  *plan = p;
+  return FV_SUCCESS;
+}
+
+fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solver,
+                           fv_precision precision, fv_dtype in_dtype, const void* price,
+                           const void* S_or_F, const void* K, const void* T, const void* r,
+                           const void* q, const int8_t* flag, int64_t n, double* out_sigma,
+                           uint8_t* status, void* stream) {
+  const char* fn = "fv_implied_vol_host";
+  FV_REQUIRE(plan, "plan", fn);
+  if (precision != FV_FP64 && precision != FV_MIXED && precision != FV_FP32)
+    return fail(FV_ERR_ARG, "%s: unknown precision %d", fn, (int)precision);
+  if (in_dtype != FV_DTYPE_F64 && in_dtype != FV_DTYPE_F32)
+    return fail(FV_ERR_ARG, "%s: unknown input dtype %d", fn, (int)in_dtype);
+  fv_err e = check_iv_args(fn, model, solver, price, S_or_F, K, T, r, q, flag, n, out_sigma, status);
+  if (e != FV_SUCCESS || n == 0) return e;
+  if (solver == FV_HALLEY && precision == FV_MIXED)
+    return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 or FP32", fn);
+  if ((e = pending_error(fn)) != FV_SUCCESS) return e;
+  const size_t es = in_dtype == FV_DTYPE_F32 ? 4 : 8;
+  const void* host_in[6] = {price, S_or_F, K, T, r, model == FV_BSM ? q : nullptr};
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  cudaError_t ce = cudaEventRecord(plan->ev_start, caller);
+  for (int b = 0; b < 2 && ce == cudaSuccess; b++) ce = cudaStreamWaitEvent(plan->st[b], plan->ev_start, 0);
+  const int64_t C = plan->chunk;
+  for (int64_t k = 0, off = 0; off < n && ce == cudaSuccess; k++, off += C) {
+    const int b = (int)(k & 1);
+    cudaStream_t s = plan->st[b];
+    const int64_t m = (n - off < C) ? n - off : C;
+    // buffer b's previous chunk finished on this same stream: stream order
+    // keeps its outputs' copies ahead of this chunk's inputs
+    for (int j = 0; j < 6 && ce == cudaSuccess; j++)
+      if (host_in[j])
+        ce = cudaMemcpyAsync(plan->in[b][j], static_cast<const char*>(host_in[j]) + off * es, m * es,
+                             cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(plan->flag[b], flag + off, m, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) break;
+    fvk::IvArgs a;
+    a.model = model;
+    a.f32_inputs = in_dtype == FV_DTYPE_F32;
+    a.P = plan->in[b][0];
+    a.SF = plan->in[b][1];
+    a.K = plan->in[b][2];
+    a.T = plan->in[b][3];
+    a.r = plan->in[b][4];
+    a.q = host_in[5] ? plan->in[b][5] : nullptr;
+    a.flag = plan->flag[b];
+    a.n = m;
+    a.sigma = plan->sigma[b];
+    a.status = plan->status[b];
+    for (int j = 0; j < 7; j++) a.st[j] = 1;
+    if (solver == FV_LBR)
+      ce = fvk::launch_iv_lbr(a, (int)precision, s);
+    else if (precision == FV_FP32)
+      ce = fvk::launch_iv_halley32(a, plan->ws[b], s);
+    else
+      ce = fvk::launch_iv_halley(a, plan->ws[b], s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(out_sigma + off, plan->sigma[b], m * 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(status + off, plan->status[b], m, cudaMemcpyDeviceToHost, s);
+  }
+  for (int b = 0; b < 2 && ce == cudaSuccess; b++) {
+    ce = cudaEventRecord(plan->ev_end[b], plan->st[b]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(caller, plan->ev_end[b], 0);
+  }
+  return cuda_result(ce, fn);
+}
+
 fv_err fv_chains_plan_destroy(fv_chains_plan* plan) {
   if (!plan) return FV_SUCCESS;
   if (plan->exec) cudaGraphExecDestroy(plan->exec);

@@ -24,7 +24,8 @@ FV_SUCCESS, FV_ERR_ARG, FV_ERR_CUDA, FV_ERR_UNSUPPORTED, FV_ERR_NOMEM = 0, -1, -
 EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws",
            "fv_implied_vol_ex", "fv_implied_vol_strided", "fv_greeks", "fv_iv_adjoint", "fv_normalised_black",
            "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
-           "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_implied_vol_halley_noalloc",
+           "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_stream_plan_create",
+           "fv_stream_plan_destroy", "fv_implied_vol_host", "fv_implied_vol_halley_noalloc",
            "fv_status_string", "fv_last_error"]
 
 
@@ -71,6 +72,10 @@ def _load():
     lib.fv_implied_vol_chains_direct.argtypes = [_P, _P]
     lib.fv_chains_plan_info.argtypes = [_P] + [ctypes.POINTER(_I)] * 3 + [ctypes.POINTER(_N)] * 2
     lib.fv_chains_plan_destroy.argtypes = [_P]
+    lib.fv_stream_plan_create.argtypes = [_N, ctypes.POINTER(ctypes.c_void_p)]
+    lib.fv_stream_plan_destroy.argtypes = [_P]
+    lib.fv_implied_vol_host.argtypes = [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P,
+                                        _P]
     lib.fv_implied_vol_halley_noalloc.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P]
     lib.fv_status_string.argtypes = [_I]
     lib.fv_status_string.restype = ctypes.c_char_p
@@ -346,6 +351,72 @@ class fv_chains_plan:
             self.destroy()
         except Exception:
             pass
+
+
+def _host_ptr(t, n, dtypes, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s is required" % name)
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
+    if t.dtype not in dtypes or not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be a contiguous %s tensor with %d elements" % (name, dtypes, n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class fv_stream_plan:
+    """Device staging and two streams for host-resident batches (see
+    fv_implied_vol_host).  Host tensors should be pinned (tensor.pin_memory())
+    for the copies to overlap the solve."""
+
+    def __init__(self, chunk_quotes=1 << 21):
+        h = ctypes.c_void_p()
+        _check(_lib.fv_stream_plan_create(int(chunk_quotes), ctypes.byref(h)), "fv_stream_plan_create")
+        self._h = h
+
+    def implied_vol(self, model, solver, precision, price, S_or_F, K, T, r, q, flag, out_sigma=None,
+                    status=None, stream=None):
+        n = price.numel()
+        f32 = price.dtype == torch.float32
+        dts = _F32 if f32 else _F64
+        if out_sigma is None:
+            out_sigma = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        if status is None:
+            status = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        _check(_lib.fv_implied_vol_host(
+            self._h, model, solver, precision, FV_DTYPE_F32 if f32 else FV_DTYPE_F64,
+            _host_ptr(price, n, dts, "price"), _host_ptr(S_or_F, n, dts, "S_or_F"),
+            _host_ptr(K, n, dts, "K"), _host_ptr(T, n, dts, "T"), _host_ptr(r, n, dts, "r"),
+            _host_ptr(q, n, dts, "q", allow_none=model != FV_BSM), _host_ptr(flag, n, _I8, "flag"), n,
+            _host_ptr(out_sigma, n, _F64, "out_sigma"), _host_ptr(status, n, _U8, "status"),
+            _stream(stream)), "fv_implied_vol_host")
+        return out_sigma, status
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _lib.fv_stream_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fv_stream_plan_create(chunk_quotes=1 << 21):
+    return fv_stream_plan(chunk_quotes)
+
+
+def fv_implied_vol_host(plan, model, solver, precision, price, S_or_F, K, T, r, q, flag,
+                        out_sigma=None, status=None, stream=None):
+    return plan.implied_vol(model, solver, precision, price, S_or_F, K, T, r, q, flag, out_sigma,
+                            status, stream)
+
+
+def fv_stream_plan_destroy(plan):
+    plan.destroy()
 
 
 def fv_chains_plan_create(model, chains, solver=FV_LBR, autotune=True, stream=None):

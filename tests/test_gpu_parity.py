@@ -476,6 +476,28 @@ def test_abi_argument_errors(fv, torch_dev):
 
 
 # ---------------------------------------------------------------------------
+# host-resident batches through the stream plan
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("solver,prec", [(0, 0), (0, 1), (1, 0)])
+def test_host_streaming_matches_device(fv, torch_dev, solver, prec):
+    torch, dev = torch_dev
+    w = wl.fill_prices(wl.bsm_grid(1000, 300, seed=41), orc.price_f64)
+    keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
+    host = {k: torch.tensor(w[k]).pin_memory() for k in keys}
+    plan = fv.fv_stream_plan_create(100000)  # 3 chunks of 100,000 quotes
+    s_h, st_h = plan.implied_vol(fv.FV_BSM, solver, prec, *[host[k] for k in keys])
+    torch.cuda.synchronize()
+    s_d, st_d = fv.fv_implied_vol_ex(fv.FV_BSM, solver, prec, *_args(torch_dev, w),
+                                     _dev(torch_dev, w["flag"]))
+    s_h, s_d = s_h.numpy(), _np(s_d)
+    assert np.array_equal(st_h.numpy(), _np(st_d))
+    assert np.array_equal(np.isnan(s_h), np.isnan(s_d))
+    ok = ~np.isnan(s_d) & (s_d > 0)
+    assert np.all(np.abs(s_h[ok] - s_d[ok]) <= 1e-12 * s_d[ok])
+    plan.destroy()
+
+
+# ---------------------------------------------------------------------------
 # binned (large batches) and unbinned (small batches) kernels agree
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
