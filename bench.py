@@ -38,7 +38,12 @@ BYTES_PER_QUOTE = 58
 # DADD + DMUL + 2 x DFMA from ncu's smsp__sass_thread_inst_executed_op_*_pred_on
 # counters on 4,194,304 quotes of the same grid distribution.  This is the
 # ALU roofline's work per quote (the kernels are bound by the FP64 pipe).
-FP64_FLOPS_PER_QUOTE = {"lbr": 1493.0, "mixed": 482.0, "fp32": 195.0}
+FP64_FLOPS_PER_QUOTE = {"lbr": 1373.0, "mixed": 482.0, "fp32": 195.0}
+# DRAM bytes (read + write) per quote of the same kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid;
+# traffic grows in proportion to the quotes, so a launch's traffic is this x n.
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (206235392 + 25441280) / 4194304,
+                            "mixed": (205772544 + 23978496) / 4194304}
 # FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock (ncu's sustained peak of
 # the thread-level DFMA counter) x 2 flops x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
@@ -309,7 +314,7 @@ def main():
     ap.add_argument("--strikes", type=int, default=4096)
     ap.add_argument("--maturities", type=int, default=4096)
     ap.add_argument("--ref-sample", type=int, default=262144)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 23)
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the selected path (for profiler runs)")
     args = ap.parse_args()
@@ -347,7 +352,9 @@ def main():
         achieved = flops_q * n / (k_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                     "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                    "traffic": None, "flops_per_quote": flops_q,
+                    "traffic": (DRAM_BYTES_PER_QUOTE_NCU[args.path] * n
+                                if args.path in DRAM_BYTES_PER_QUOTE_NCU else None),
+                    "flops_per_quote": flops_q,
                     "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz "
                                  "(recipe unit count and clock)"}
     else:

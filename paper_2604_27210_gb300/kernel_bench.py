@@ -6,7 +6,7 @@ sweeps.  Prints one JSON line per size:
   python -m paper_2604_27210_gb300.kernel_bench --kernel lbr --workload grid \
       --n 4194304 --reps 5 --warmup 2
 
-kernels:   lbr, mixed, fp32, halley, price, greeks, adjoint, chains
+kernels:   lbr, mixed, fp32, halley, halley32, price, greeks, adjoint, chains
 workloads: grid (BSM strike x maturity grid), b76 (Black-76 quotes),
            b76f32 (the same in FP32), bsm (BSM quotes with an upstream
            gradient), chains (option chains; --n is the number of chains)
@@ -78,6 +78,8 @@ def runner(fv, torch, kernel, w, t):
         return lambda: fv.fv_implied_vol(model, fv.FV_LBR, *a, out, st)
     if kernel == "halley":
         return lambda: fv.fv_implied_vol(model, fv.FV_HALLEY, *a, out, st)
+    if kernel == "halley32":
+        return lambda: fv.fv_implied_vol_ex(model, fv.FV_HALLEY, fv.FV_FP32, *a, out, st)
     if kernel == "mixed":
         return lambda: fv.fv_implied_vol_ex(model, fv.FV_LBR, fv.FV_MIXED, *a, out, st)
     if kernel == "fp32":
