@@ -21,14 +21,20 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in SRC + HDR)
 
 
+def compile_library(sources, out: str) -> None:
+    """gcc the given C sources into the shared library ``out``."""
+    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", out] + list(sources) + ["-lm",
+                                                                                       "-lpthread"]
+    subprocess.run(cmd, check=True)
+
+
 def build(force: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", tmp] + SRC + ["-lm", "-lpthread"]
-    subprocess.run(cmd, check=True)
+    compile_library(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
 

@@ -4,6 +4,10 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  Every function takes and returns host
 numpy arrays; model codes are 0 Black-76, 1 Black-Scholes, 2 BSM; status codes
 are 0 OK, 1 below intrinsic, 2 above maximum, 3 invalid.
+
+FV_ORACLE_LIB=<path> loads another build of the same C source instead of
+``oracle/_build/liboracle.so`` (the planted-mistake tests point it at copies
+of the oracle with one mistake each).
 """
 import ctypes
 import os
@@ -27,7 +31,7 @@ _INT = ctypes.c_int
 def _load():
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("FV_ORACLE_LIB") or _build.build()
         lib = ctypes.CDLL(path)
         lib.or_num_threads.restype = _INT
         lib.or_normalised_black.argtypes = [_D, _D, _I8, _N, _D, _INT]

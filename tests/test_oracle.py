@@ -318,6 +318,51 @@ def test_solvers_on_in_the_money_quotes():
         assert np.all(rel <= 8 * EPS * (1 + kap[ok]))
 
 
+@pytest.mark.parametrize("model", [orc.BLACK_SCHOLES, orc.BSM])
+def test_solvers_on_spot_quotes_with_dividends(model):
+    # the FP64 normalisation x = ln(S/K) + (r - q) T feeds both solvers
+    w = wl.fill_prices(wl.bsm_quotes(1024, seed=22), orc.price)
+    if model == orc.BLACK_SCHOLES:
+        w = dict(w, model=model, q=None)
+        wl.fill_prices(w, orc.price)
+    sig, st = orc.iv(model, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["flag"])
+    v, kap = _gate(model, w["P"], w, sig)
+    ok = (st == 0) & (sig > 0)
+    assert ok.mean() > 0.9
+    for fn in (orc.iv_lbr, orc.iv_halley):
+        s2, st2, _ = fn(model, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["flag"])
+        assert np.array_equal(st, st2)
+        rel = np.abs(s2[ok] - sig[ok]) / sig[ok]
+        assert np.all(rel <= 8 * EPS * (1 + kap[ok]))
+
+
+def test_lbr_interior_guess_is_a_hermite_interpolant():
+    # Section 2.2: the interior guess interpolates s(beta) between the
+    # boundary points s_l < s_c < s_h (inflection s_c = sqrt(2|x|), tangent
+    # feet s_l, s_h) with the slopes ds/dbeta = 1/b' there.  The guess is the
+    # LBR's output after zero iterations.
+    for x in (-0.05, -0.5, -2.0):
+        bmax = math.exp(0.5 * x)
+        vega = lambda s: math.exp(-0.5 * ((x / s) ** 2 + (0.5 * s) ** 2)) / math.sqrt(2 * math.pi)
+        b = lambda s: float(orc.normalised_black(np.array([x]), np.array([s]), 1)[0])
+        sc = math.sqrt(-2 * x)
+        bc, vc = b(sc), vega(sc)
+        sl, sh = sc - bc / vc, sc + (bmax - bc) / vc
+        bl, vl, bh, vh = b(sl), vega(sl), b(sh), vega(sh)
+        # quotes at beta = end + k delta, k = 1, 2 (F = 1, K = e^{-x}, T = 1, r = 0)
+        for b0, s0, v0, b1, sign in ((bl, sl, vl, bc, 1), (bc, sc, vc, bl, -1),
+                                     (bc, sc, vc, bh, 1), (bh, sh, vh, bc, -1)):
+            d = 1e-6 * abs(b1 - b0) * sign
+            beta = np.array([b0 + d, b0 + 2 * d])
+            K = np.full(2, math.exp(-x))
+            P = beta * np.sqrt(K)
+            g, st, _ = orc.iv_lbr(0, P, np.ones(2), K, np.ones(2), np.zeros(2), None,
+                                  np.ones(2, np.int8), n_iter=0)
+            assert np.all(st == orc.OK)
+            assert g[0] == pytest.approx(s0 + d / v0, rel=1e-6, abs=1e-9)
+            assert (g[1] - g[0]) / d == pytest.approx(1 / v0, rel=1e-3)
+
+
 # ---------------------------------------------------------------------------
 # Greeks and the implicit-function gradient
 # ---------------------------------------------------------------------------
