@@ -259,6 +259,33 @@ void or_normalised_black(const double* x, const double* s, const int8_t* theta, 
   parallel_for(n, nthreads, nb_range, &c);
 }
 
+/* erfcx in binary128: exp(z^2) erfc(z) directly while erfc(z) stays in the
+ * binary128 range (z < 100, erfc ~ 1e-4345); beyond, the asymptotic series
+ * 1/(z sqrt(pi)) sum_k (-1)^k (2k-1)!! / (2 z^2)^k, whose terms fall below
+ * 1e-34 by k = 10 there.  Below zero: 2 exp(z^2) - erfcx(-z). */
+static q128 erfcx_q(q128 z) {
+  if (z != z) return z; /* NaN */
+  if (z < 0) return 2 * expf128(z * z) - erfcx_q(-z);
+  if (z < 100) return expf128(z * z) * erfcf128(z);
+  const q128 v = 1 / (2 * z * z);
+  q128 term = 1, sum = 1;
+  for (int k = 1; k <= 12; k++) {
+    term *= -(2 * k - 1) * v;
+    sum += term;
+  }
+  return sum / (z * sqrtf128(M_PIf128));
+}
+static void erfcx_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) c->out[i] = (double)erfcx_q((q128)c->x[i]);
+}
+void or_erfcx(const double* z, int64_t n, double* out, int nthreads) {
+  ctx_t c = {0};
+  c.x = z;
+  c.out = out;
+  parallel_for(n, nthreads, erfcx_range, &c);
+}
+
 static int inputs_valid(int model, double SF, double K, double T, double r, double q,
                         int8_t flag) {
   if (!(flag == 1 || flag == -1)) return 0;

@@ -51,6 +51,10 @@ int or_num_threads(void);
 void or_normalised_black(const double* x, const double* s, const int8_t* theta,
                          int64_t n, double* out, int nthreads);
 
+/* erfcx(z) = exp(z^2) erfc(z) in binary128, rounded to double (the function
+ * of the erfcx branch of Section 2.2's normalised Black evaluation). */
+void or_erfcx(const double* z, int64_t n, double* out, int nthreads);
+
 /* Model price at sigma (binary128, rounded).  q is ignored unless model is BSM
  * (may be NULL otherwise).  Invalid inputs give NaN. */
 void or_price(int model, const double* S_or_F, const double* K, const double* T,

@@ -35,6 +35,7 @@ def _load():
         lib = ctypes.CDLL(path)
         lib.or_num_threads.restype = _INT
         lib.or_normalised_black.argtypes = [_D, _D, _I8, _N, _D, _INT]
+        lib.or_erfcx.argtypes = [_D, _N, _D, _INT]
         lib.or_price.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _INT]
         lib.or_price_f64.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _INT]
         lib.or_status.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _U8, _D, _D, _D, _INT]
@@ -82,6 +83,14 @@ def normalised_black(x, s, theta=1, nthreads=0):
     out = np.empty(n, np.float64)
     _load().or_normalised_black(keep[0][1], keep[1][1], keep[2][1], n, out.ctypes.data_as(_D),
                                 nthreads)
+    return out
+
+
+def erfcx(z, nthreads=0):
+    n = _len(z)
+    zz = _f64(z, n)
+    out = np.empty(n, np.float64)
+    _load().or_erfcx(zz[1], n, out.ctypes.data_as(_D), nthreads)
     return out
 
 

@@ -31,6 +31,8 @@
 
 #include <cstdint>
 
+#include "fv_erfcx_table.h"
+
 namespace fvd {
 
 // mathematical constants
@@ -40,6 +42,7 @@ constexpr double kInvSqrt2 = 0.707106781186547524400844362104849039;    // 1/sqr
 constexpr double kSqrtPiOver2 = 1.25331413731550025120788264240552263;  // sqrt(pi/2)
 constexpr double kSqrt2OverPi = 0.797884560802865355879892119868763737;  // sqrt(2/pi)
 constexpr double kInvSqrt3 = 0.577350269189625764509148780501957456;    // 1/sqrt(3)
+constexpr double kInvSqrtPi = 0.564189583547756286948079451560772586;   // 1/sqrt(pi)
 constexpr double kLn2Pi = 1.83787706640934548356065947281123527;        // ln(2 pi)
 // relative slack band of the three bound tests of the status rule:
 // 64 * 2^-52, wider than the few-ulp spread of a price that equals the
@@ -78,7 +81,56 @@ __device__ __forceinline__ double f_exp(double v) { return exp(v); }
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ double f_log(double v) { return log(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
-__device__ __forceinline__ double f_erfcx(double v) { return erfcx(v); }
+// FP64 erfcx(z) = exp(z^2) erfc(z).  FP64 is the scarce unit of this GPU, and
+// the solvers evaluate erfcx more often than any other FP64 function, so it
+// is not the general library routine: for 0 <= z < 128 a degree-10 piecewise
+// Chebyshev interpolant (fv_erfcx_table.h, 68 pieces located from the bits of
+// z, within one ulp); beyond, the asymptotic series (Abramowitz & Stegun
+// 7.1.23) to the term in z^-8, whose first omitted term is below 2^-55 there.
+__device__ __forceinline__ double erfcx_nonneg(double z) {
+  if (z < FV_ERFCX_TABLE_END) {
+    int k;
+    if (z < 0.5) {
+      k = __double2int_rz(z * 8.0);  // exact scaling: k in 0..3
+    } else {
+      // binade 2^e, e = -1..6, and the top three fraction bits: k in 4..67
+      const int hi = __double2hiint(z);
+      k = 4 + (((hi >> 20) - 1022) << 3) + ((hi >> 17) & 7);
+    }
+    // row k: centre, then the coefficients of v^0 .. v^10
+    const double2* c = reinterpret_cast<const double2*>(kErfcxTable + k * FV_ERFCX_STRIDE);
+    const double2 c0 = __ldg(c), c1 = __ldg(c + 1), c2 = __ldg(c + 2), c3 = __ldg(c + 3),
+                  c4 = __ldg(c + 4), c5 = __ldg(c + 5);
+    const double v = z - c0.x;  // exact
+    double p = fma(c5.y, v, c5.x);
+    p = fma(p, v, c4.y);
+    p = fma(p, v, c4.x);
+    p = fma(p, v, c3.y);
+    p = fma(p, v, c3.x);
+    p = fma(p, v, c2.y);
+    p = fma(p, v, c2.x);
+    p = fma(p, v, c1.y);
+    p = fma(p, v, c1.x);
+    return fma(p, v, c0.y);
+  }
+  // z >= 128, +inf (gives 0) or NaN (gives NaN)
+  const double r = 1.0 / z, w = r * r;
+  const double sum = fma(w, fma(w, fma(w, fma(w, 6.5625, -1.875), 0.75), -0.5), 1.0);
+  return kInvSqrtPi * r * sum;
+}
+
+// erfcx for any z: below zero by reflection, erfcx(z) = 2 exp(z^2) - erfcx(-z),
+// with z^2 split exactly into zz + zl so that exp(z^2) = exp(zz) (1 + zl)
+// keeps its relative accuracy up to the overflow at z^2 ~ 709.8.
+__device__ __forceinline__ double erfcx64(double z) {
+  const double p = erfcx_nonneg(fabs(z));
+  if (!(z < 0.0)) return p;
+  const double zz = z * z, zl = fma(z, z, -zz);
+  const double e2 = 2.0 * exp(zz);
+  return isinf(e2) ? e2 : fma(e2, zl, e2) - p;
+}
+
+__device__ __forceinline__ double f_erfcx(double v) { return erfcx64(v); }
 __device__ __forceinline__ float f_erfcx(float v) { return erfcxf(v); }
 __device__ __forceinline__ double f_ncdf(double v) { return normcdf(v); }
 __device__ __forceinline__ float f_ncdf(float v) { return normcdff(v); }

@@ -641,6 +641,18 @@ cudaError_t launch_normalised_black(const double* x, const double* s, const int8
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_erfcx(const double* z, int64_t n, double* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = erfcx64(z[i]);
+}
+
+cudaError_t launch_erfcx(const double* z, int64_t n, double* out, cudaStream_t st) {
+  const int block = 256;
+  k_erfcx<<<grid_for(n, block, 8), block, 0, st>>>(z, n, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // batches of chains: persistent CTAs walk a static tile table
 // ---------------------------------------------------------------------------

@@ -1,7 +1,7 @@
 """Parity of the CUDA library against the oracle (needs a GPU).
 
-Floating-point tolerances (spec bars, with the conditioning reading
-recorded in the design doc):
+Floating-point tolerances (the target accuracy, read with the conditioning
+of each quote):
   - sigma, FP64 paths: relative error <= 1e-12 where the normalised vega
     b' > 1e-8 and kappa = beta / (s b') <= 1e3; elsewhere (solved quotes) the
     error is bounded by 1e-12 + 16 eps (1 + kappa), the rounding of the FP64
@@ -79,6 +79,30 @@ def _args(torch_dev, w, keys=("P", "S_or_F", "K", "T", "r", "q")):
 # ---------------------------------------------------------------------------
 # normalised Black function
 # ---------------------------------------------------------------------------
+def test_erfcx_against_binary128(fv, torch_dev):
+    # the kernels' own erfcx: table below z = 128, asymptotic series above,
+    # reflection below zero; every piece edge and its neighbours included
+    torch, dev = torch_dev
+    g = np.random.default_rng(9)
+    edges = np.array([k / 8 for k in range(5)] + [2.0 ** e * (1 + j / 8) for e in range(-1, 7)
+                                                  for j in range(8)] + [128.0])
+    pos = np.concatenate([g.uniform(0, 0.5, 20000), np.exp(g.uniform(np.log(0.5), np.log(128), 50000)),
+                          np.exp(g.uniform(np.log(128), np.log(1e300), 20000)), edges,
+                          np.nextafter(edges, 0), np.nextafter(edges, np.inf), [0.0, 5e-324]])
+    neg = -np.concatenate([g.uniform(0, 26.6, 40000), np.exp(g.uniform(np.log(1e-300), np.log(1), 5000))])
+    z = np.concatenate([pos, neg])
+    got = _np(fv.fv_erfcx(torch.tensor(z, device=dev)))
+    ref = orc.erfcx(z)
+    fin = np.isfinite(ref)
+    rel = np.abs(got[fin] - ref[fin]) / ref[fin]
+    zf = z[fin]
+    assert rel[zf >= 0].max() <= 4e-16, rel[zf >= 0].max()
+    assert rel[zf < 0].max() <= 8e-16, rel[zf < 0].max()
+    assert np.array_equal(np.isinf(got), np.isinf(ref))
+    sp = _np(fv.fv_erfcx(torch.tensor([np.inf, -np.inf, -27.0, np.nan, -0.0], device=dev)))
+    assert sp[0] == 0 and sp[1] == np.inf and sp[2] == np.inf and np.isnan(sp[3]) and sp[4] == 1.0
+
+
 def test_normalised_black_against_binary128(fv, torch_dev):
     xs = np.concatenate([-np.logspace(-8, np.log10(40), 60), [0.0], np.logspace(-8, np.log10(40), 60)])
     ss = np.logspace(-4, np.log10(50), 90)

@@ -73,6 +73,24 @@ def test_put_call_parity():
         np.testing.assert_allclose(c - p, D * (F - w["K"]), rtol=0, atol=1e-12 * 100)
 
 
+def test_erfcx_against_mpmath():
+    # erfcx(z) = exp(z^2) erfc(z), the function of the erfcx branch of Section 2.2
+    g = np.random.default_rng(3)
+    z = np.concatenate([g.uniform(-26.5, 0, 200), g.uniform(0, 8, 200),
+                        np.exp(g.uniform(np.log(8), np.log(1e300), 200)), [0.0, 99.99, 100.0, 100.01]])
+    got = orc.erfcx(z)
+    mp.mp.dps = 40
+    for zi, gi in zip(z, got):
+        y = mp.mpf(zi)
+        if y > 1e6:  # mpmath's erfc does not reach there: series to 1/z^6 (error < 1e-36)
+            ref = (1 - 1 / (2 * y * y) + 3 / (4 * y ** 4)) / (y * mp.sqrt(mp.pi))
+        else:
+            ref = mp.exp(y ** 2) * mp.erfc(y)
+        assert abs(float((gi - ref) / ref)) <= 2.0 ** -53 * 1.0001, zi
+    sp = orc.erfcx(np.array([np.inf, -np.inf, -27.0, np.nan]))
+    assert sp[0] == 0 and sp[1] == np.inf and sp[2] == np.inf and np.isnan(sp[3])
+
+
 def test_normalised_black_at_the_money_is_erf():
     # x = 0: b(0, s) = Phi(s/2) - Phi(-s/2) = erf(s / (2 sqrt 2))
     s = np.logspace(-6, 1.3, 200)

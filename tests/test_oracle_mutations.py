@@ -22,6 +22,11 @@ MUTANTS = [
      "- em * Phi_q((q128)th * (h - t))", "+ em * Phi_q((q128)th * (h - t))"),
     ("normalised Black: h - t in the forward term",
      "ep * Phi_q((q128)th * (h + t))", "ep * Phi_q((q128)th * (h - t))"),
+    ("erfcx: reflection with exp(-z^2)",
+     "if (z < 0) return 2 * expf128(z * z) - erfcx_q(-z);",
+     "if (z < 0) return 2 * expf128(-z * z) - erfcx_q(-z);"),
+    ("erfcx: asymptotic series with (2k+1)!!",
+     "term *= -(2 * k - 1) * v;", "term *= -(2 * k + 1) * v;"),
     ("complement: wrong sign in the second tail",
      "expf128(-0.5f128 * x) * Phi_q(h - t);", "expf128(-0.5f128 * x) * Phi_q(t - h);"),
     ("normal density: dropped factor 1/2 in the exponent",
