@@ -99,7 +99,8 @@ def test_erfcx_against_binary128(fv, torch_dev):
     assert rel[zf >= 0].max() <= 4e-16, rel[zf >= 0].max()
     assert rel[zf < 0].max() <= 8e-16, rel[zf < 0].max()
     assert np.array_equal(np.isinf(got), np.isinf(ref))
-    sp = _np(fv.fv_erfcx(torch.tensor([np.inf, -np.inf, -27.0, np.nan, -0.0], device=dev)))
+    sp = _np(fv.fv_erfcx(torch.tensor([np.inf, -np.inf, -27.0, np.nan, -0.0], dtype=torch.float64,
+                                      device=dev)))
     assert sp[0] == 0 and sp[1] == np.inf and sp[2] == np.inf and np.isnan(sp[3]) and sp[4] == 1.0
 
 
