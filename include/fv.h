@@ -172,14 +172,18 @@ fv_err fv_iv_adjoint(fv_model model, const double* price, const double* S_or_F, 
 fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta, int64_t n,
                            double* out, void* stream);
 
-/* Scaled complementary error function erfcx(z) = exp(z^2) erfc(z) in FP64,
- * the routine the kernels evaluate the normalised Black function with (the
- * erfcx branch of Section 2.2).  The paper has no counterpart entry point: it
- * exposes the kernels' own erfcx so that it can be checked on its own.
- * z, out: device arrays of n doubles (caller-owned); any z is accepted
- * (erfcx(-inf) = +inf, erfcx(+inf) = 0, NaN gives NaN).  Errors: n < 0 or a
- * NULL pointer with n > 0 -> FV_ERR_ARG before any launch. */
-fv_err fv_erfcx(const double* z, int64_t n, double* out, void* stream);
+/* The kernels' own FP64 special functions, evaluated elementwise:
+ *   FV_MATH_ERFCX  erfcx(z) = exp(z^2) erfc(z), the function the normalised
+ *                  Black evaluation is built on (erfcx branch of Section 2.2);
+ *                  any z (erfcx(-inf) = +inf, erfcx(+inf) = 0);
+ *   FV_MATH_LOG    ln z, the logarithm of the wing objectives (Section 2.2);
+ *                  ln 0 = -inf, negative z gives NaN.
+ * The paper has no counterpart entry point: this exposes what the kernels
+ * compute so that it can be checked on its own.  z, out: device arrays of n
+ * doubles (caller-owned); NaN gives NaN.  Errors: unknown function, n < 0 or
+ * a NULL pointer with n > 0 -> FV_ERR_ARG before any launch. */
+typedef enum { FV_MATH_ERFCX = 0, FV_MATH_LOG = 1 } fv_math_fn;
+fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* stream);
 
 /* ---- batches of option chains (one persistent launch) ------------------ */
 /* One chain: device arrays of n quotes sharing one forward (Black-76) or spot

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfv.so")
 SOURCES = ["fv_kernels.cu", "fv_abi.cu", "fv_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, f) for f in ("fv_device.cuh", "fv_internal.h", "fv_erfcx_table.h")] + [
+HEADERS = [os.path.join(CSRC, f) for f in ("fv_device.cuh", "fv_internal.h", "fv_fp64_tables.h")] + [
     os.path.join(ROOT, "include", "fv.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -362,15 +362,18 @@ fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta
       fvk::launch_normalised_black(x, s, theta, n, out, static_cast<cudaStream_t>(stream)), fn);
 }
 
-fv_err fv_erfcx(const double* z, int64_t n, double* out, void* stream) {
-  const char* fn = "fv_erfcx";
+fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* stream) {
+  const char* fn = "fv_math";
+  if (which != FV_MATH_ERFCX && which != FV_MATH_LOG)
+    return fail(FV_ERR_ARG, "%s: unknown function %d", fn, (int)which);
   if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
   if (n == 0) return FV_SUCCESS;
   FV_REQUIRE(z, "z", fn);
   FV_REQUIRE(out, "out", fn);
   fv_err e = pending_error(fn);
   if (e != FV_SUCCESS) return e;
-  return cuda_result(fvk::launch_erfcx(z, n, out, static_cast<cudaStream_t>(stream)), fn);
+  return cuda_result(fvk::launch_math((int)which, z, n, out, static_cast<cudaStream_t>(stream)),
+                     fn);
 }
 
 fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* chains,

@@ -31,7 +31,7 @@
 
 #include <cstdint>
 
-#include "fv_erfcx_table.h"
+#include "fv_fp64_tables.h"
 
 namespace fvd {
 
@@ -79,12 +79,11 @@ struct Prec<float> {
 
 __device__ __forceinline__ double f_exp(double v) { return exp(v); }
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
-__device__ __forceinline__ double f_log(double v) { return log(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
 // FP64 erfcx(z) = exp(z^2) erfc(z).  FP64 is the scarce unit of this GPU, and
 // the solvers evaluate erfcx more often than any other FP64 function, so it
 // is not the general library routine: for 0 <= z < 128 a degree-10 piecewise
-// Chebyshev interpolant (fv_erfcx_table.h, 68 pieces located from the bits of
+// Chebyshev interpolant (fv_fp64_tables.h, 68 pieces located from the bits of
 // z, within one ulp); beyond, the asymptotic series (Abramowitz & Stegun
 // 7.1.23) to the term in z^-8, whose first omitted term is below 2^-55 there.
 __device__ __forceinline__ double erfcx_nonneg(double z) {
@@ -130,7 +129,44 @@ __device__ __forceinline__ double erfcx64(double z) {
   return isinf(e2) ? e2 : fma(e2, zl, e2) - p;
 }
 
+// FP64 natural logarithm, the table-driven method of P. T. P. Tang (ACM TOMS
+// 16(4), 1990): y = 2^m f with f in [1/sqrt2, sqrt2), F_j = 1 + j/128 the grid
+// point nearest f, r = f c_j - 1 (one rounding; c_j = 1/F_j in FP64, c_0 = 1),
+//   ln y = (m ln2_hi + L_hi[j]) + (m ln2_lo + L_lo[j] + log1p(r))
+// with L_hi + L_lo = -ln(c_j) for the rounded c_j, the first sum exact (both
+// terms on a 2^-42 grid) and log1p(r), |r| <= 0.0056, its Taylor polynomial to
+// r^8 (truncation below 2^-60 relative).  Zero, negative, subnormal, infinite
+// and NaN arguments take the library routine.
+__device__ __forceinline__ double log64(double y) {
+  if (!(y >= 2.2250738585072014e-308 && y <= 1.7976931348623157e308)) return log(y);
+  const int hi = __double2hiint(y), lo = __double2loint(y);
+  const int mant = hi & 0xfffff;
+  int m = (hi >> 20) - 1023, j, ehi;
+  if (mant >= 0x6a09e) {  // f >= sqrt2: take f/2 in [1/sqrt2, 1), j in -37..0
+    m += 1;
+    j = ((mant + (1 << 13)) >> 14) - 64;
+    ehi = 0x3fe00000;
+  } else {                // f in [1, sqrt2), j in 0..53
+    j = (mant + (1 << 12)) >> 13;
+    ehi = 0x3ff00000;
+  }
+  const double f = __hiloint2double(ehi | mant, lo);
+  const double2* t = reinterpret_cast<const double2*>(kLogTable + (j - FV_LOG_J0) * 4);
+  const double2 t0 = __ldg(t), t1 = __ldg(t + 1);  // (c_j, L_hi), (L_lo, pad)
+  const double r = fma(f, t0.x, -1.0);
+  double q = fma(r, -0.125, 1.0 / 7.0);
+  q = fma(q, r, -1.0 / 6.0);
+  q = fma(q, r, 0.2);
+  q = fma(q, r, -0.25);
+  q = fma(q, r, 1.0 / 3.0);
+  q = fma(q, r, -0.5);
+  const double p = fma(r * r, q, r);  // log1p(r)
+  const double md = (double)m;
+  return fma(md, FV_LN2_HI, t0.y) + (fma(md, FV_LN2_LO, t1.x) + p);
+}
+
 __device__ __forceinline__ double f_erfcx(double v) { return erfcx64(v); }
+__device__ __forceinline__ double f_log(double v) { return log64(v); }
 __device__ __forceinline__ float f_erfcx(float v) { return erfcxf(v); }
 __device__ __forceinline__ double f_ncdf(double v) { return normcdf(v); }
 __device__ __forceinline__ float f_ncdf(float v) { return normcdff(v); }
@@ -495,14 +531,24 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
   nb_eval<T>(x, so, false, vo_);
   const T bo = degenerate ? T(0) : vo_.e * vo_.B;
   const T vo = vo_.e * T(kInvSqrt2Pi);
-  // ln b_l and ln beta are needed on the lower side only (region test where
-  // b_l underflows the type, and the lowest-region guess)
-  const T ln_bo = lower ? nb_log(vo_) : T(0);
-  if (lower && q.ln_beta == T(0)) q.ln_beta = f_log(beta);
-  if (lower)
-    reg = (!degenerate && (bo > T(0) ? beta < bo : q.ln_beta < ln_bo)) ? 0 : 1;
-  else
+  // ln b_l, for the region test where b_l underflows the type and for the
+  // lowest-region guess: an FP32 value is enough for both (a wrong side next
+  // to b_l only changes which convergent objective is used)
+  const float ln_bo = (lower && !degenerate)
+                          ? (float)(T(-0.5) * (vo_.h * vo_.h + vo_.t * vo_.t)) + logf((float)vo_.B)
+                          : 0.0f;
+  if (lower) {
+    if (degenerate) {
+      reg = 1;
+    } else if (bo > T(0)) {
+      reg = beta < bo ? 0 : 1;
+    } else {
+      if (q.ln_beta == T(0)) q.ln_beta = f_log(beta);
+      reg = (float)q.ln_beta < ln_bo ? 0 : 1;
+    }
+  } else {
     reg = (beta <= bo) ? 2 : 3;
+  }
   T s;
   if (reg == 1 || reg == 2) {
     // cubic Hermite of s(beta) with slopes 1/b' on the inflection-bounded interior
@@ -522,12 +568,17 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
     // wings: invert the limiting form, scaled to match b at the boundary
     //   lowest:  b ~ c Phi(-|x|/(sqrt3 s))^3   (s -> 0)
     //   highest: b_max - b ~ c' Phi(-s/2)       (s -> inf)
-    const T za = (reg == 0) ? -f_abs(x) * T(kInvSqrt3) / so : T(-0.5) * so;
-    const T Pa = f_ncdf(za);
-    const T ln_p = (reg == 0) ? f_log(Pa) + (q.ln_beta - ln_bo) * T(1.0 / 3.0)
-                              : f_log(q.c_beta * Pa / (bmax - bo));
-    const T z = ncdfinv_log<T>(ln_p);
-    s = (reg == 0) ? f_abs(x) * T(kInvSqrt3) / f_abs(z) : T(-2) * z;
+    // The limiting forms hold to ~1e-2 in s, so the inversion runs in FP32
+    // whatever T is, with ln Phi(z) = ln(erfcx(-z/sqrt2)/2) - z^2/2 (z < 0),
+    // which neither underflows nor cancels.
+    if (reg == 0 && q.ln_beta == T(0)) q.ln_beta = f_log(beta);
+    const float za = (reg == 0) ? -fabsf((float)x) * float(kInvSqrt3) / (float)so
+                                : -0.5f * (float)so;
+    const float ln_pa = logf(0.5f * erfcxf(-za * float(kInvSqrt2))) - 0.5f * za * za;
+    const float ln_p = (reg == 0) ? ln_pa + ((float)q.ln_beta - ln_bo) * (1.0f / 3.0f)
+                                  : ln_pa + logf((float)(q.c_beta / (bmax - bo)));
+    const float z = ncdfinv_log<float>(ln_p);
+    s = (reg == 0) ? f_abs(x) * T(kInvSqrt3) / T(fabsf(z)) : T(-2) * T(z);
   }
   if (!(s > T(0)) || !f_finite(s)) s = (so > T(0)) ? so : T(1);
   return s;
@@ -634,7 +685,7 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
                                                   double bmax, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
   const bool upper = beta > 0.5 * bmax;
-  const double ln_c_beta = upper ? log(bmax - beta) : 0.0;
+  const double ln_c_beta = upper ? log64(bmax - beta) : 0.0;
   NB<double> v;
   // f(s) > 0 iff b(s) > beta
   auto resid = [&](double s_) {

@@ -49,7 +49,7 @@ cudaError_t launch_adjoint(int model, const double* P, const double* SF, const d
                            double* gq, cudaStream_t st);
 cudaError_t launch_normalised_black(const double* x, const double* s, const int8_t* theta,
                                     int64_t n, double* out, cudaStream_t st);
-cudaError_t launch_erfcx(const double* z, int64_t n, double* out, cudaStream_t st);
+cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStream_t st);
 
 // chains: device descriptor and tile table entry
 struct ChainDesc {

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     const Reduced<double> q64 = reduced64(nq);
-    const double lnb = q64.ln_beta != 0.0 ? q64.ln_beta : log(q64.beta);
+    const double lnb = q64.ln_beta != 0.0 ? q64.ln_beta : log64(q64.beta);
     const double s = bisect_fallback(lnb, q64.beta, q64.x, q64.bmax, w.lo[k], w.hi[k]);
     a.sigma[i] = s / sqrt(T);
   }
@@ -641,15 +641,19 @@ cudaError_t launch_normalised_black(const double* x, const double* s, const int8
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_erfcx(const double* z, int64_t n, double* out) {
+template <int FN>
+__global__ void __launch_bounds__(256) k_math(const double* z, int64_t n, double* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = erfcx64(z[i]);
+    out[i] = FN == 0 ? erfcx64(z[i]) : log64(z[i]);
 }
 
-cudaError_t launch_erfcx(const double* z, int64_t n, double* out, cudaStream_t st) {
+cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStream_t st) {
   const int block = 256;
-  k_erfcx<<<grid_for(n, block, 8), block, 0, st>>>(z, n, out);
+  if (fn == 0)
+    k_math<0><<<grid_for(n, block, 8), block, 0, st>>>(z, n, out);
+  else
+    k_math<1><<<grid_for(n, block, 8), block, 0, st>>>(z, n, out);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,178 @@
+"""Write fv_fp64_tables.h: the tables of the kernels' own FP64 erfcx and log.
+
+On this GPU an FP64 operation costs as much issue time as ~70 FP32 ones, and
+the solvers of Section 2.2 spend most of their FP64 work in two functions: the
+scaled complementary error function erfcx(z) = exp(z^2) erfc(z) (the
+normalised Black function is a difference of two erfcx values) and the
+logarithm (the lowest- and highest-region objectives work with ln b).  The
+kernels evaluate both from small tables instead of general library routines.
+
+erfcx on 0 <= z < 128: Chebyshev interpolation (Trefethen, Approximation
+Theory and Approximation Practice, ch. 4) on short pieces, the piecewise
+scheme of S. G. Johnson's Faddeeva package, with pieces laid out so that the
+piece index comes from the bits of z:
+
+  piece k = 0..3:    [k/8, (k+1)/8)                (uniform below 1/2)
+  piece 4 + 8e' + j: [2^e (1 + j/8), 2^e (1 + (j+1)/8)),  e = e' - 1 = -1..6
+
+Each piece stores its centre c and the degree-10 polynomial in v = z - c that
+interpolates erfcx at the 11 Chebyshev points of the piece.  v is exact where
+z and c lie within a factor of two of each other (Sterbenz), which is every
+piece but the first below z = 1/32; there its rounding error is below 2^-58.
+Beyond z = 128 the kernels use the asymptotic series (Abramowitz & Stegun
+7.1.23) instead.
+
+log: the table-driven method of P. T. P. Tang (ACM TOMS 16(4), 1990).  With
+y = 2^m f, f in [1/sqrt2, sqrt2), and F_j = 1 + j/128 the grid point nearest
+f (j = -37..53), the kernels form r = f c_j - 1 with one fused multiply-add,
+c_j = 1/F_j rounded to FP64, and return
+    (m ln2_hi + L_hi[j]) + (m ln2_lo + L_lo[j] + log1p(r)),
+where L_j = -ln(c_j) for the rounded c_j (so the rounding of c_j costs
+nothing), split so that m ln2_hi + L_hi[j] is exact (both on a 2^-42 grid),
+and log1p(r), |r| <= 0.0056, is its Taylor polynomial to r^8.  c_0 = 1, so
+next to y = 1 the result is log1p(y - 1) with y - 1 exact.
+
+Run:  python gen_fp64_tables.py [samples per piece]
+(needs mpmath; prints the worst error of the FP64 erfcx Horner evaluation,
+emulated with exactly rounded fused multiply-adds, against mpmath on a dense
+sample of every piece).
+"""
+import os
+import sys
+
+import mpmath as mp
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "fv_fp64_tables.h")
+
+DEGREE = 10
+STRIDE = 16         # doubles per erfcx piece: centre + 11 coefficients + padding (128 bytes)
+UNIFORM = 4         # pieces of width 1/8 on [0, 1/2)
+SUB = 8             # pieces per binade on [1/2, 128)
+BINADES = range(-1, 7)
+Z_TABLE_END = 128.0
+
+LOG_J = range(-37, 54)   # F_j = 1 + j/128 covers [1/sqrt2, sqrt2)
+LOG_GRID = 2.0 ** -42    # m ln2_hi and L_hi are multiples of this
+
+mp.mp.dps = 50
+
+
+def erfcx(z):
+    return mp.exp(z * z) * mp.erfc(z)
+
+
+def pieces():
+    out = [(mp.mpf(k) / 8, mp.mpf(k + 1) / 8) for k in range(UNIFORM)]
+    for e in BINADES:
+        for j in range(SUB):
+            a = mp.mpf(2) ** e * (1 + mp.mpf(j) / SUB)
+            b = mp.mpf(2) ** e * (1 + mp.mpf(j + 1) / SUB)
+            out.append((a, b))
+    return out
+
+
+def fit(a, b):
+    """Monomial coefficients in v = z - c of the Chebyshev interpolant."""
+    c = (a + b) / 2
+    half = (b - a) / 2
+    n = DEGREE + 1
+    nodes = [half * mp.cos(mp.pi * (k + mp.mpf(1) / 2) / n) for k in range(n)]
+    A = mp.matrix([[v ** j for j in range(n)] for v in nodes])
+    y = mp.matrix([erfcx(c + v) for v in nodes])
+    coef = mp.lu_solve(A, y)
+    return float(c), [float(coef[j]) for j in range(n)]
+
+
+def fma(x, y, z):
+    """FP64 fused multiply-add, exactly rounded (what the GPU's DFMA does)."""
+    return float(mp.mpf(x) * mp.mpf(y) + mp.mpf(z))
+
+
+def horner(coefs, v):
+    p = coefs[-1]
+    for cj in reversed(coefs[:-1]):
+        p = fma(p, v, cj)
+    return p
+
+
+def worst_error(table, samples=64):
+    worst = (0.0, None)
+    for (a, b), (c, coefs) in zip(pieces(), table):
+        for i in range(samples + 1):
+            z = float(a + (b - a) * i / samples)
+            if z >= float(b):
+                z = float(b) - float(b) * 2.0 ** -52
+            v = z - c
+            got = horner(coefs, v)
+            ref = erfcx(mp.mpf(z))
+            err = abs(float((got - ref) / ref))
+            if err > worst[0]:
+                worst = (err, z)
+    return worst
+
+
+def on_grid(v):
+    """Round v to the nearest multiple of LOG_GRID (exact in FP64)."""
+    return float(mp.nint(mp.mpf(v) / LOG_GRID) * LOG_GRID)
+
+
+def log_table():
+    ln2 = mp.log(2)
+    ln2_hi = on_grid(ln2)
+    ln2_lo = float(ln2 - ln2_hi)
+    rows = []
+    for j in LOG_J:
+        c = 1.0 if j == 0 else float(1 / (1 + mp.mpf(j) / 128))
+        L = -mp.log(mp.mpf(c))
+        L_hi = on_grid(L)
+        rows.append((c, L_hi, float(L - L_hi)))
+    return ln2_hi, ln2_lo, rows
+
+
+def write(table, out=OUT):
+    ln2_hi, ln2_lo, lrows = log_table()
+    lines = [
+        "// Generated by gen_fp64_tables.py (beside this file); do not edit.",
+        "#pragma once",
+        "",
+        "// erfcx: piecewise Chebyshev interpolants on 0 <= z < %g; piece k holds its" % Z_TABLE_END,
+        "// centre c_k and the degree-%d polynomial in v = z - c_k (lowest order first)," % DEGREE,
+        "// padded to %d doubles (%d bytes) per piece." % (STRIDE, STRIDE * 8),
+        "#define FV_ERFCX_PIECES %d" % len(table),
+        "#define FV_ERFCX_STRIDE %d" % STRIDE,
+        "#define FV_ERFCX_TABLE_END %.1f" % Z_TABLE_END,
+        "static __device__ __align__(128) const double kErfcxTable[FV_ERFCX_PIECES * FV_ERFCX_STRIDE] = {",
+    ]
+    for c, coefs in table:
+        row = [c] + coefs + [0.0] * (STRIDE - 1 - len(coefs))
+        lines.append("    " + ", ".join(repr(x) for x in row) + ",")
+    lines += [
+        "};",
+        "",
+        "// log: row j + %d holds c_j = 1/(1 + j/128) (rounded; c_0 = 1), L_hi[j] and" % -LOG_J[0],
+        "// L_lo[j] with L_hi + L_lo = -ln(c_j), L_hi and ln2_hi on a 2^-42 grid, and a pad.",
+        "#define FV_LOG_J0 %d" % LOG_J[0],
+        "#define FV_LOG_ROWS %d" % len(lrows),
+        "#define FV_LN2_HI %r" % ln2_hi,
+        "#define FV_LN2_LO %r" % ln2_lo,
+        "static __device__ __align__(32) const double kLogTable[FV_LOG_ROWS * 4] = {",
+    ]
+    for c, hi, lo in lrows:
+        lines.append("    %r, %r, %r, 0.0," % (c, hi, lo))
+    lines.append("};")
+    with open(out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def main(out=OUT, samples=64):
+    table = [fit(a, b) for a, b in pieces()]
+    write(table, out)
+    err, z = worst_error(table, samples)
+    print("%s: %d erfcx pieces, worst relative error %.3e (%.2f ulp of 2^-52) at z = %r"
+          % (out, len(table), err, err / 2.0 ** -52, z))
+    return err
+
+
+if __name__ == "__main__":
+    main(samples=int(sys.argv[1]) if len(sys.argv) > 1 else 64)

@@ -3,6 +3,8 @@
 // python -m paper_2604_27210_gb300.throughput_probe builds and runs it.
 #include <cstdio>
 #include <cuda_runtime.h>
+
+#include "fv_device.cuh"
 #define CK(x) do{cudaError_t e=(x); if(e!=cudaSuccess){printf("ERR %s line %d: %s\n",#x,__LINE__,cudaGetErrorString(e)); return 1;}}while(0)
 constexpr int ITER=1024;
 __global__ void k_dfma(double* out, double b, double c){ double a0=threadIdx.x*1e-3,a1=a0+1,a2=a0+2,a3=a0+3,a4=a0+4,a5=a0+5,a6=a0+6,a7=a0+7;
@@ -13,7 +15,8 @@ __global__ void k_ffma(float* out, float b, float c){ float a0=threadIdx.x*1e-3f
  out[blockIdx.x*blockDim.x+threadIdx.x]=a0+a1+a2+a3+a4+a5+a6+a7;}
 template<int F> __global__ void k_fn64(double* out, double x0, double dx){ double acc=0; double x=x0+threadIdx.x*1e-6;
  for(int i=0;i<64;i++){ double y;
-   if(F==0) y=exp(x); else if(F==1) y=log(x); else if(F==2) y=erfcx(x); else if(F==3) y=erfc(x); else if(F==4) y=1.0/x; else if(F==5) y=sqrt(x); else if (F==6) y=normcdfinv(x*0.1); else y=expm1(x);
+   if(F==0) y=exp(x); else if(F==1) y=log(x); else if(F==2) y=erfcx(x); else if(F==3) y=erfc(x); else if(F==4) y=1.0/x; else if(F==5) y=sqrt(x); else if (F==6) y=normcdfinv(x*0.1); else if (F==7) y=expm1(x);
+   else if(F==8) y=fvd::erfcx64(x); else if(F==9) y=fvd::log64(x); else if(F==10) y=(double)(float)x; else y=3.0/x;
    acc+=y; x+=dx; }
  out[blockIdx.x*blockDim.x+threadIdx.x]=acc;}
 template<int F> __global__ void k_fn32(float* out, float x0, float dx){ float acc=0; float x=x0+threadIdx.x*1e-6f;
@@ -41,6 +44,10 @@ int main(){
  T("sqrt64",f64ops,[&]{k_fn64<5><<<blocks,threads>>>(d,0.5,1e-3);});
  T("ncdfinv64",f64ops,[&]{k_fn64<6><<<blocks,threads>>>(d,0.1,1e-3);});
  T("expm1_64",f64ops,[&]{k_fn64<7><<<blocks,threads>>>(d,-0.3,1e-3);});
+ T("erfcx64_lib",f64ops,[&]{k_fn64<8><<<blocks,threads>>>(d,0.3,1e-2);});
+ T("log64_lib",f64ops,[&]{k_fn64<9><<<blocks,threads>>>(d,0.5,1e-3);});
+ T("cvt_f64_f32",f64ops,[&]{k_fn64<10><<<blocks,threads>>>(d,0.5,1e-3);});
+ T("div64",f64ops,[&]{k_fn64<11><<<blocks,threads>>>(d,0.5,1e-3);});
  T("expf",f32ops,[&]{k_fn32<0><<<blocks,threads>>>(f,-3.0f,1e-3f);});
  T("logf",f32ops,[&]{k_fn32<1><<<blocks,threads>>>(f,0.5f,1e-3f);});
  T("erfcxf",f32ops,[&]{k_fn32<2><<<blocks,threads>>>(f,0.3f,1e-2f);});

@@ -23,7 +23,7 @@ FV_SUCCESS, FV_ERR_ARG, FV_ERR_CUDA, FV_ERR_UNSUPPORTED, FV_ERR_NOMEM = 0, -1, -
 # every symbol include/fv.h declares
 EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws",
            "fv_implied_vol_ex", "fv_implied_vol_strided", "fv_greeks", "fv_iv_adjoint",
-           "fv_normalised_black", "fv_erfcx",
+           "fv_normalised_black", "fv_math",
            "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
            "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_stream_plan_create",
            "fv_stream_plan_destroy", "fv_implied_vol_host", "fv_implied_vol_halley_noalloc",
@@ -67,7 +67,7 @@ def _load():
     lib.fv_iv_adjoint.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _N,
                                   _P, _P, _P, _P, _P, _P, _P]
     lib.fv_normalised_black.argtypes = [_P, _P, _P, _N, _P, _P]
-    lib.fv_erfcx.argtypes = [_P, _N, _P, _P]
+    lib.fv_math.argtypes = [ctypes.c_int, _P, _N, _P, _P]
     lib.fv_chains_plan_create.argtypes = [_I, _I, ctypes.POINTER(fv_chain), _N, _I, _P,
                                           ctypes.POINTER(ctypes.c_void_p)]
     lib.fv_implied_vol_chains.argtypes = [_P, _P]
@@ -301,11 +301,14 @@ def fv_normalised_black(x, s, theta, out=None, stream=None):
     return out
 
 
-def fv_erfcx(z, out=None, stream=None):
+FV_MATH_ERFCX, FV_MATH_LOG = 0, 1
+
+
+def fv_math(which, z, out=None, stream=None):
     n = z.numel()
     out = _like(z, torch.float64) if out is None else out
-    _check(_lib.fv_erfcx(_ptr(z, n, _F64, "z"), n, _ptr(out, n, _F64, "out"), _stream(stream)),
-           "fv_erfcx")
+    _check(_lib.fv_math(which, _ptr(z, n, _F64, "z"), n, _ptr(out, n, _F64, "out"),
+                        _stream(stream)), "fv_math")
     return out
 
 

@@ -2,8 +2,9 @@
 
 Measures FMA issue rates and the throughput of CUDA's math-library calls
 (exp, log, erfcx, erfc, reciprocal, sqrt, normcdfinv, expm1, and their FP32
-forms): the numbers that decide which steps of the implied-volatility path are
-affordable in FP64 on this GPU.  Usage: python -m paper_2604_27210_gb300.throughput_probe
+forms), of the library's own table-driven FP64 erfcx and log, of an FP64 ->
+FP32 -> FP64 conversion pair and of an FP64 division: the numbers that decide
+which steps of the implied-volatility path are affordable in FP64 on this GPU.  Usage: python -m paper_2604_27210_gb300.throughput_probe
 """
 import os
 import subprocess
@@ -18,8 +19,9 @@ def main():
     src = os.path.join(HERE, "csrc", "throughput_probe.cu")
     exe = os.path.join(HERE, "_build", "throughput_probe")
     os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run([_build.nvcc()] + _build.ARCH + ["-O3", "-std=c++17", "--extended-lambda", src,
-                                                   "-o", exe], check=True)
+    subprocess.run([_build.nvcc()] + _build.ARCH + ["-O3", "-std=c++17", "--extended-lambda",
+                                                   "-I", os.path.join(HERE, "csrc"), src, "-o", exe],
+                   check=True)
     r = subprocess.run([exe])
     sys.exit(r.returncode)
 

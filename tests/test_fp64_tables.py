@@ -1,0 +1,136 @@
+"""The FP64 erfcx and log tables of the CUDA kernels, checked on the CPU.
+
+The kernels evaluate erfcx(z) = exp(z^2) erfc(z) on 0 <= z < 128 from
+piecewise Chebyshev interpolants and ln y by Tang's table-driven method
+(csrc/fv_fp64_tables.h, written by csrc/gen_fp64_tables.py).  Here the
+committed header is what the generator writes, and each function, evaluated
+step by step the way the kernel does (table rows located from the bits of the
+argument, exactly rounded fused multiply-adds), is within its error bound of
+mpmath on points the generator never looked at.
+"""
+import importlib.util
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+mp = pytest.importorskip("mpmath")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2604_27210_gb300", "csrc")
+HEADER = os.path.join(CSRC, "fv_fp64_tables.h")
+
+
+def _gen():
+    spec = importlib.util.spec_from_file_location("gen_fp64_tables",
+                                                  os.path.join(CSRC, "gen_fp64_tables.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _table():
+    src = open(HEADER).read()
+    stride = int(re.search(r"#define FV_ERFCX_STRIDE (\d+)", src).group(1))
+    body = src[src.index("{") + 1:src.index("};")]
+    vals = [float(v) for v in body.replace("\n", " ").split(",") if v.strip()]
+    return np.array(vals).reshape(-1, stride)
+
+
+def _log_table():
+    src = open(HEADER).read()
+    j0 = int(re.search(r"#define FV_LOG_J0 (-?\d+)", src).group(1))
+    ln2_hi = float(re.search(r"#define FV_LN2_HI (\S+)", src).group(1))
+    ln2_lo = float(re.search(r"#define FV_LN2_LO (\S+)", src).group(1))
+    body = src[src.index("kLogTable"):]
+    body = body[body.index("{") + 1:body.index("};")]
+    vals = [float(v) for v in body.replace("\n", " ").split(",") if v.strip()]
+    return j0, ln2_hi, ln2_lo, np.array(vals).reshape(-1, 4)
+
+
+def _log64(y, tab):
+    """The kernel's log64 for a positive normal y, operation by operation."""
+    j0, ln2_hi, ln2_lo, rows = tab
+    bits = struct.unpack("<q", struct.pack("<d", y))[0]
+    hi, lo = bits >> 32, bits & 0xffffffff
+    mant = hi & 0xfffff
+    m = (hi >> 20) - 1023
+    if mant >= 0x6a09e:
+        m += 1
+        j = ((mant + (1 << 13)) >> 14) - 64
+        ehi = 0x3fe00000
+    else:
+        j = (mant + (1 << 12)) >> 13
+        ehi = 0x3ff00000
+    f = struct.unpack("<d", struct.pack("<q", ((ehi | mant) << 32) | lo))[0]
+    c, L_hi, L_lo, _ = rows[j - j0]
+    r = _fma(f, c, -1.0)
+    q = _fma(r, -0.125, 1.0 / 7.0)
+    for k in (-1.0 / 6.0, 0.2, -0.25, 1.0 / 3.0, -0.5):
+        q = _fma(q, r, k)
+    p = _fma(r * r, q, r)
+    md = float(m)
+    return _fma(md, ln2_hi, L_hi) + (_fma(md, ln2_lo, L_lo) + p)
+
+
+def _piece(z):
+    if z < 0.5:
+        return int(z * 8.0)
+    hi = struct.unpack("<q", struct.pack("<d", z))[0] >> 32
+    return 4 + (((hi >> 20) - 1022) << 3) + ((hi >> 17) & 7)
+
+
+def _fma(x, y, z):
+    return float(mp.mpf(x) * mp.mpf(y) + mp.mpf(z))
+
+
+def _eval(tab, z):
+    row = tab[_piece(z)]
+    v = z - row[0]
+    p = row[11]
+    for j in range(10, 0, -1):
+        p = _fma(p, v, row[j])
+    return p
+
+
+def test_committed_table_is_the_generators_output(tmp_path):
+    out = str(tmp_path / "table.h")
+    _gen().main(out=out, samples=4)
+    assert open(out).read() == open(HEADER).read()
+
+
+def test_table_within_one_ulp_of_erfcx():
+    mp.mp.dps = 40
+    tab = _table()
+    g = np.random.default_rng(5)
+    # random points in every piece, the piece edges and their neighbours
+    edges = [k / 8 for k in range(5)] + [2.0 ** e * (1 + j / 8) for e in range(-1, 7)
+                                         for j in range(8)]
+    z = np.concatenate([g.uniform(0, 0.5, 300), np.exp(g.uniform(np.log(0.5), np.log(128), 1200)),
+                        edges, np.nextafter(edges, 0), np.nextafter(edges, 200), [0.0, 5e-324]])
+    z = z[(z >= 0) & (z < 128)]
+    worst = 0.0
+    for zi in z:
+        ref = mp.exp(mp.mpf(zi) ** 2) * mp.erfc(mp.mpf(zi))
+        worst = max(worst, abs(float((_eval(tab, float(zi)) - ref) / ref)))
+    assert worst <= 2.0 ** -52, worst
+
+
+def test_log_within_one_ulp():
+    mp.mp.dps = 40
+    tab = _log_table()
+    g = np.random.default_rng(6)
+    y = np.concatenate([np.exp(g.uniform(-700, 700, 1500)), 1 + g.uniform(-0.02, 0.02, 500),
+                        1 + np.exp(g.uniform(-36, -5, 300)), 1 - np.exp(g.uniform(-36, -5, 300)),
+                        g.uniform(0.5, 2.0, 1000), [1.0, 2.0, 0.5, np.sqrt(2), 2.2250738585072014e-308,
+                                                     1.7976931348623157e308]])
+    worst = 0.0
+    for yi in y:
+        ref = mp.log(mp.mpf(float(yi)))
+        if ref == 0:
+            assert _log64(float(yi), tab) == 0.0
+            continue
+        worst = max(worst, abs(float((_log64(float(yi), tab) - ref) / ref)))
+    assert worst <= 2.0 ** -52, worst

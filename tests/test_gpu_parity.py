@@ -91,7 +91,7 @@ def test_erfcx_against_binary128(fv, torch_dev):
                           np.nextafter(edges, 0), np.nextafter(edges, np.inf), [0.0, 5e-324]])
     neg = -np.concatenate([g.uniform(0, 26.6, 40000), np.exp(g.uniform(np.log(1e-300), np.log(1), 5000))])
     z = np.concatenate([pos, neg])
-    got = _np(fv.fv_erfcx(torch.tensor(z, device=dev)))
+    got = _np(fv.fv_math(fv.FV_MATH_ERFCX, torch.tensor(z, device=dev)))
     ref = orc.erfcx(z)
     fin = np.isfinite(ref)
     rel = np.abs(got[fin] - ref[fin]) / ref[fin]
@@ -99,9 +99,29 @@ def test_erfcx_against_binary128(fv, torch_dev):
     assert rel[zf >= 0].max() <= 4e-16, rel[zf >= 0].max()
     assert rel[zf < 0].max() <= 8e-16, rel[zf < 0].max()
     assert np.array_equal(np.isinf(got), np.isinf(ref))
-    sp = _np(fv.fv_erfcx(torch.tensor([np.inf, -np.inf, -27.0, np.nan, -0.0], dtype=torch.float64,
-                                      device=dev)))
+    sp = _np(fv.fv_math(fv.FV_MATH_ERFCX, torch.tensor([np.inf, -np.inf, -27.0, np.nan, -0.0],
+                                                        dtype=torch.float64, device=dev)))
     assert sp[0] == 0 and sp[1] == np.inf and sp[2] == np.inf and np.isnan(sp[3]) and sp[4] == 1.0
+
+
+def test_log_against_extended_precision(fv, torch_dev):
+    # the kernels' own FP64 log (Tang's table-driven method) against numpy's
+    # long double log (binary128 on Arm, 64-bit mantissa on x86)
+    torch, dev = torch_dev
+    g = np.random.default_rng(10)
+    y = np.concatenate([np.exp(g.uniform(-708, 709, 100000)), 1 + g.uniform(-0.02, 0.02, 20000),
+                        1 + np.exp(g.uniform(-36, -5, 5000)), 1 - np.exp(g.uniform(-36, -5, 5000)),
+                        [2.2250738585072014e-308, 1.7976931348623157e308, 0.5, 2.0, 1.0]])
+    got = _np(fv.fv_math(fv.FV_MATH_LOG, torch.tensor(y, device=dev)))
+    ref = np.log(y.astype(np.longdouble))
+    nz = ref != 0
+    rel = np.abs((got[nz] - ref[nz]) / ref[nz]).astype(np.float64)
+    assert rel.max() <= 2.0 ** -52, rel.max()
+    assert np.all(got[~nz] == 0)
+    sp = _np(fv.fv_math(fv.FV_MATH_LOG, torch.tensor([0.0, -1.0, np.inf, np.nan, 5e-324],
+                                                      dtype=torch.float64, device=dev)))
+    assert sp[0] == -np.inf and np.isnan(sp[1]) and sp[2] == np.inf and np.isnan(sp[3])
+    assert sp[4] == pytest.approx(np.log(5e-324), rel=1e-15)
 
 
 def test_normalised_black_against_binary128(fv, torch_dev):
