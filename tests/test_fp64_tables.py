@@ -118,7 +118,7 @@ def test_table_within_one_ulp_of_erfcx():
     assert worst <= 2.0 ** -52, worst
 
 
-def test_log_within_one_ulp():
+def test_log_within_one_and_a_half_ulp():
     mp.mp.dps = 40
     tab = _log_table()
     g = np.random.default_rng(6)
@@ -133,4 +133,6 @@ def test_log_within_one_ulp():
             assert _log64(float(yi), tab) == 0.0
             continue
         worst = max(worst, abs(float((_log64(float(yi), tab) - ref) / ref)))
-    assert worst <= 2.0 ** -52, worst
+    # final rounding (1/2 ulp) plus the second sum's rounding relative to a
+    # result that can be as small as ln(1 + 1/256)
+    assert worst <= 1.5 * 2.0 ** -52, worst

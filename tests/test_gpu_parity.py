@@ -116,7 +116,9 @@ def test_log_against_extended_precision(fv, torch_dev):
     ref = np.log(y.astype(np.longdouble))
     nz = ref != 0
     rel = np.abs((got[nz] - ref[nz]) / ref[nz]).astype(np.float64)
-    assert rel.max() <= 2.0 ** -52, rel.max()
+    # final rounding (1/2 ulp) plus the second sum's rounding relative to a
+    # result that can be as small as ln(1 + 1/256) (up to ~1/2 ulp more)
+    assert rel.max() <= 1.5 * 2.0 ** -52, rel.max()
     assert np.all(got[~nz] == 0)
     sp = _np(fv.fv_math(fv.FV_MATH_LOG, torch.tensor([0.0, -1.0, np.inf, np.nan, 5e-324],
                                                       dtype=torch.float64, device=dev)))
