@@ -38,6 +38,25 @@ int grid_for(int64_t n, int block, int per_sm) {
   return (int)std::max<int64_t>(1, std::min(need, cap));
 }
 
+// Grid of a grid-stride kernel: one wave of resident blocks (SMs x blocks
+// that fit on an SM at once, cached per device), so every block slot walks
+// the same share of the units and no partial second wave leaves SMs idle;
+// fewer blocks when there is less work.
+template <auto Kernel>
+int persistent_grid(int64_t units, int units_per_block, int block) {
+  static int resident[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (resident[dev] <= 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, block, 0) != cudaSuccess || b <= 0)
+      b = 1;
+    resident[dev] = b;
+  }
+  return grid_for(units, units_per_block, resident[dev]);
+}
+
 template <typename InT>
 __device__ __forceinline__ double ld(const void* p, int64_t i) {
   return (double)__ldg(static_cast<const InT*>(p) + i);
@@ -231,8 +250,9 @@ __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a) {
 
 template <typename InT, int PREC, int Q, int MINB, bool LATE32>
 static void launch_binned(const IvArgs& a, cudaStream_t st) {
-  const int grid = grid_for(a.n, kBinThreads * Q, 8);
-  k_iv_lbr_binned<InT, PREC, Q, MINB, LATE32><<<grid, kBinThreads, 0, st>>>(a);
+  constexpr auto kernel = k_iv_lbr_binned<InT, PREC, Q, MINB, LATE32>;
+  const int grid = persistent_grid<kernel>(a.n, kBinThreads * Q, kBinThreads);
+  kernel<<<grid, kBinThreads, 0, st>>>(a);
 }
 
 // Tile shapes measured on GB300 (16.8 M quotes): the FP64 solve runs best with
@@ -246,12 +266,20 @@ static void launch_binned(const IvArgs& a, cudaStream_t st) {
 // spreads the quotes over as many SMs and sub-partitions as possible.
 constexpr int64_t kSmallBatch = 1 << 17;
 
+template <typename InT, int PREC>
+static void launch_flat_prec(const IvArgs& a, int block, cudaStream_t st) {
+  constexpr auto kernel = k_iv_lbr<InT, PREC>;
+  // small batches: one 64-thread block per 64 quotes; large: one resident wave
+  const int grid = block == 256 ? persistent_grid<kernel>(a.n, block, block)
+                                : grid_for(a.n, block, 2048 / block);
+  kernel<<<grid, block, 0, st>>>(a);
+}
+
 template <typename InT>
 static void launch_flat(const IvArgs& a, int prec, int block, cudaStream_t st) {
-  const int grid = grid_for(a.n, block, 2048 / block);
-  if (prec == P_FP64) k_iv_lbr<InT, P_FP64><<<grid, block, 0, st>>>(a);
-  else if (prec == P_MIXED) k_iv_lbr<InT, P_MIXED><<<grid, block, 0, st>>>(a);
-  else k_iv_lbr<InT, P_FP32><<<grid, block, 0, st>>>(a);
+  if (prec == P_FP64) launch_flat_prec<InT, P_FP64>(a, block, st);
+  else if (prec == P_MIXED) launch_flat_prec<InT, P_MIXED>(a, block, st);
+  else launch_flat_prec<InT, P_FP32>(a, block, st);
 }
 
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
@@ -429,13 +457,15 @@ cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   const int block = 256;
-  const int grid = grid_for(a.n, block, 8);
   if (a.f32_inputs) {
-    k_iv_halley32<float><<<grid, block, 0, st>>>(a, w);
-    k_halley32_fallback<float><<<grid, block, 0, st>>>(a, w);
+    k_iv_halley32<float><<<persistent_grid<k_iv_halley32<float>>(a.n, block, block), block, 0, st>>>(a, w);
+    k_halley32_fallback<float>
+        <<<persistent_grid<k_halley32_fallback<float>>(a.n, block, block), block, 0, st>>>(a, w);
   } else {
-    k_iv_halley32<double><<<grid, block, 0, st>>>(a, w);
-    k_halley32_fallback<double><<<grid, block, 0, st>>>(a, w);
+    k_iv_halley32<double>
+        <<<persistent_grid<k_iv_halley32<double>>(a.n, block, block), block, 0, st>>>(a, w);
+    k_halley32_fallback<double>
+        <<<persistent_grid<k_halley32_fallback<double>>(a.n, block, block), block, 0, st>>>(a, w);
   }
   return cudaGetLastError();
 }
@@ -445,13 +475,14 @@ cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   const int block = 256;
-  const int grid = grid_for(a.n, block, 8);
   if (a.f32_inputs) {
-    k_iv_halley<float><<<grid, block, 0, st>>>(a, w);
-    k_halley_fallback<float><<<grid, block, 0, st>>>(a, w);
+    k_iv_halley<float><<<persistent_grid<k_iv_halley<float>>(a.n, block, block), block, 0, st>>>(a, w);
+    k_halley_fallback<float>
+        <<<persistent_grid<k_halley_fallback<float>>(a.n, block, block), block, 0, st>>>(a, w);
   } else {
-    k_iv_halley<double><<<grid, block, 0, st>>>(a, w);
-    k_halley_fallback<double><<<grid, block, 0, st>>>(a, w);
+    k_iv_halley<double><<<persistent_grid<k_iv_halley<double>>(a.n, block, block), block, 0, st>>>(a, w);
+    k_halley_fallback<double>
+        <<<persistent_grid<k_halley_fallback<double>>(a.n, block, block), block, 0, st>>>(a, w);
   }
   return cudaGetLastError();
 }
@@ -488,7 +519,7 @@ cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const 
                          const double* T, const double* r, const double* q, const double* sigma,
                          int64_t n, double* out, cudaStream_t st) {
   const int block = 256;
-  k_price<<<grid_for(n, block, 8), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, out);
+  k_price<<<persistent_grid<k_price>(n, block, block), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, out);
   return cudaGetLastError();
 }
 
@@ -552,7 +583,7 @@ cudaError_t launch_greeks(int model, const int8_t* flag, const double* SF, const
                           int64_t n, double* delta, double* gamma, double* vega, double* theta,
                           double* rho, cudaStream_t st) {
   const int block = 256;
-  k_greeks<<<grid_for(n, block, 8), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, delta,
+  k_greeks<<<persistent_grid<k_greeks>(n, block, block), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, delta,
                                                      gamma, vega, theta, rho);
   return cudaGetLastError();
 }
@@ -618,7 +649,7 @@ cudaError_t launch_adjoint(int model, const double* P, const double* SF, const d
                            int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
                            double* gq, cudaStream_t st) {
   const int block = 256;
-  k_adjoint<<<grid_for(n, block, 8), block, 0, st>>>(model, P, SF, K, T, r, q, flag, sigma, status,
+  k_adjoint<<<persistent_grid<k_adjoint>(n, block, block), block, 0, st>>>(model, P, SF, K, T, r, q, flag, sigma, status,
                                                       gsig, n, gP, gS, gK, gT, gr, gq);
   return cudaGetLastError();
 }
@@ -637,7 +668,7 @@ __global__ void __launch_bounds__(256) k_nb(const double* x, const double* s, co
 cudaError_t launch_normalised_black(const double* x, const double* s, const int8_t* theta,
                                     int64_t n, double* out, cudaStream_t st) {
   const int block = 256;
-  k_nb<<<grid_for(n, block, 8), block, 0, st>>>(x, s, theta, n, out);
+  k_nb<<<persistent_grid<k_nb>(n, block, block), block, 0, st>>>(x, s, theta, n, out);
   return cudaGetLastError();
 }
 
@@ -651,9 +682,9 @@ __global__ void __launch_bounds__(256) k_math(const double* z, int64_t n, double
 cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStream_t st) {
   const int block = 256;
   if (fn == 0)
-    k_math<0><<<grid_for(n, block, 8), block, 0, st>>>(z, n, out);
+    k_math<0><<<persistent_grid<k_math<0>>(n, block, block), block, 0, st>>>(z, n, out);
   else
-    k_math<1><<<grid_for(n, block, 8), block, 0, st>>>(z, n, out);
+    k_math<1><<<persistent_grid<k_math<1>>(n, block, block), block, 0, st>>>(z, n, out);
   return cudaGetLastError();
 }
 
