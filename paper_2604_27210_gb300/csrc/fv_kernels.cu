@@ -255,12 +255,13 @@ static void launch_binned(const IvArgs& a, cudaStream_t st) {
   kernel<<<grid, kBinThreads, 0, st>>>(a);
 }
 
-// Tile shapes measured on GB300 (16.8 M quotes): the FP64 solve runs best with
-// 4 quotes per thread and no register cap (36.8 ms on the BSM grid against
-// 44.6 ms unbinned); the mixed path with 2 quotes per thread, 4 blocks per SM
-// and its FP32 iterations in phase 2, where they interleave with the FP64
-// correction (13.7 ms against 15.4 ms).  The FP32 path has no FP64 solve to
-// sort for and stays unbinned.
+// Tile shapes measured on GB300 (16.8 M quotes of the BSM grid, one resident
+// wave of blocks): the FP64 solve runs best with 1 quote per thread and 4
+// blocks per SM (22.8 ms; 2 quotes per thread 23.1 ms, 4 with no register cap
+// 23.4 ms); the mixed path with 2 quotes per thread, 4 blocks per SM and its
+// FP32 iterations in phase 2, where they interleave with the FP64 correction
+// (11.8 ms; 1 or 2 quotes per thread at 3 to 5 blocks per SM within 0.6 %).
+// The FP32 path has no FP64 solve to sort for and stays unbinned.
 // Below kSmallBatch quotes a launch is latency-bound (a warp's ~900
 // dependent FP64 instructions): the unbinned kernel with 64-thread blocks
 // spreads the quotes over as many SMs and sub-partitions as possible.
@@ -292,10 +293,10 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
     return cudaGetLastError();
   }
   if (a.f32_inputs) {
-    if (prec == P_FP64) launch_binned<float, P_FP64, 4, 1, false>(a, st);
+    if (prec == P_FP64) launch_binned<float, P_FP64, 1, 4, false>(a, st);
     else launch_binned<float, P_MIXED, 2, 4, true>(a, st);
   } else {
-    if (prec == P_FP64) launch_binned<double, P_FP64, 4, 1, false>(a, st);
+    if (prec == P_FP64) launch_binned<double, P_FP64, 1, 4, false>(a, st);
     else launch_binned<double, P_MIXED, 2, 4, true>(a, st);
   }
   return cudaGetLastError();
