@@ -30,6 +30,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "fv_fp64_tables.h"
 
@@ -464,9 +465,10 @@ __device__ __forceinline__ T guarded(T s, T ds) {
 // and whose second-order ratios h2 = g''/g', h3 = g'''/g' are FP32: they only
 // shape the correction factor (1 + phi) of the Newton step nu, with
 // phi = nu (-h2/2 - h3 nu/6) / (1 + nu (h2 + h3 nu/6)) = O(nu), so their
-// relative error enters the step at order nu^2.
-__device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, int reg) {
-  wing_logs<double>(q, reg);
+// relative error enters the step at order nu^2.  Returns the step ds (0 where
+// it is not finite); the FP64 solver iterates it, the mixed solver applies it
+// once after its FP32 iterations.
+__device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg) {
   NB<double> v;
   nb_eval<double>(q.x, s, reg == 3, v);
   const float hh = (float)(v.h * v.h), is = (float)v.inv_s, sf = (float)s;
@@ -480,16 +482,17 @@ __device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, in
     h3 = u * u + du;
   } else {
     const double lnX = nb_log(v);
-    const double qw = kInvSqrt2Pi / v.B;
-    const float qf = (float)qw;
+    // b/b' (region 0) or (b_max - b)/b' (region 3): B sqrt(2 pi), no division
+    const double bq = v.B * kSqrt2Pi;
+    const float qf = 1.0f / (float)bq;
     if (reg == 0) {
       const double iL = 1.0 / lnX;
-      nu = (iL - q.inv_ln_beta) * lnX * lnX / qw;
+      nu = (iL - q.inv_ln_beta) * lnX * lnX * bq;
       const float iLf = (float)iL, k1 = 1.0f + 2.0f * iLf;
       h2 = u - qf * k1;
       h3 = h2 * h2 + du - (qf * u - qf * qf) * k1 + 2.0f * qf * qf * iLf * iLf;
     } else {
-      nu = -(q.ln_c_beta - lnX) / qw;
+      nu = -(q.ln_c_beta - lnX) * bq;
       h2 = u + qf;
       h3 = h2 * h2 + du + qf * h2;
     }
@@ -497,7 +500,12 @@ __device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, in
   const float nf = (float)nu;
   const float phi = nf * (-0.5f * h2 - h3 * nf * (1.0f / 6.0f)) / (1.0f + nf * (h2 + h3 * nf * (1.0f / 6.0f)));
   const double ds = isfinite(phi) ? nu + nu * (double)phi : nu;
-  return guarded<double>(s, isfinite(ds) ? ds : 0.0);
+  return isfinite(ds) ? ds : 0.0;
+}
+
+__device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, int reg) {
+  wing_logs<double>(q, reg);
+  return guarded<double>(s, hh3_ds_mixed(q, s, reg));
 }
 
 // Boundaries (six normalised-Black values: b and b' at s_l, s_c, s_h, of which
@@ -591,8 +599,12 @@ __device__ __forceinline__ T lbr_solve(Reduced<T> q, int n_min, int n_max, T con
   T s = lbr_guess<T>(q, reg);
   wing_logs<T>(q, reg);
   for (int k = 0; k < n_max; k++) {
-    const Objective<T> o = objective<T>(q, s, reg);
-    const T ds = hh3_step<T>(o);
+    // FP64: residual and Newton step in FP64, second-order ratios in FP32
+    T ds;
+    if constexpr (std::is_same<T, double>::value)
+      ds = hh3_ds_mixed(q, s, reg);
+    else
+      ds = hh3_step<T>(objective<T>(q, s, reg));
     s = guarded<T>(s, ds);
     if (k + 1 >= n_min && !(f_abs(ds) > conv_tol * s)) break;
   }
