@@ -38,12 +38,16 @@ BYTES_PER_QUOTE = 58
 # DADD + DMUL + 2 x DFMA from ncu's smsp__sass_thread_inst_executed_op_*_pred_on
 # counters on 4,194,304 quotes of the same grid distribution.  This is the
 # ALU roofline's work per quote (the kernels are bound by the FP64 pipe).
-FP64_FLOPS_PER_QUOTE = {"lbr": 1373.0, "mixed": 482.0, "fp32": 195.0}
+FP64_FLOPS_PER_QUOTE = {"lbr": 682.0, "mixed": 359.0, "fp32": 195.0}
 # DRAM bytes (read + write) per quote of the same kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid;
 # traffic grows in proportion to the quotes, so a launch's traffic is this x n.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (206235392 + 25441280) / 4194304,
-                            "mixed": (205772544 + 23978496) / 4194304}
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205751296 + 25234944) / 4194304,
+                            "mixed": (205695488 + 24467456) / 4194304}
+# share of cycles the FP64 pipe was busy in the same captures (the flops above
+# leave out conversions, compares and the FP64 steps of divisions and square
+# roots, which occupy the pipe too)
+FP64_PIPE_BUSY_NCU = {"lbr": 0.847, "mixed": 0.813, "fp32": 0.838}
 # FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock (ncu's sustained peak of
 # the thread-level DFMA counter) x 2 flops x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
@@ -355,6 +359,7 @@ def main():
                     "traffic": (DRAM_BYTES_PER_QUOTE_NCU[args.path] * n
                                 if args.path in DRAM_BYTES_PER_QUOTE_NCU else None),
                     "flops_per_quote": flops_q,
+                    "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU.get(args.path),
                     "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz "
                                  "(recipe unit count and clock)"}
     else:
