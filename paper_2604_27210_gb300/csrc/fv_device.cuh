@@ -592,11 +592,12 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
   return s;
 }
 
-// LBR solve: guess, n_min Householder(3) steps, then up to n_max while the
-// last step still moved s by more than conv_tol relative.
+// LBR iterations from the guess s of region reg: n_min Householder(3) steps,
+// then up to n_max while the last step still moved s by more than conv_tol
+// relative.
 template <typename T>
-__device__ __forceinline__ T lbr_solve(Reduced<T> q, int n_min, int n_max, T conv_tol, int& reg) {
-  T s = lbr_guess<T>(q, reg);
+__device__ __forceinline__ T lbr_iterate(Reduced<T> q, T s, int reg, int n_min, int n_max,
+                                         T conv_tol) {
   wing_logs<T>(q, reg);
   for (int k = 0; k < n_max; k++) {
     // FP64: residual and Newton step in FP64, second-order ratios in FP32
@@ -609,6 +610,13 @@ __device__ __forceinline__ T lbr_solve(Reduced<T> q, int n_min, int n_max, T con
     if (k + 1 >= n_min && !(f_abs(ds) > conv_tol * s)) break;
   }
   return s;
+}
+
+// LBR solve: guess, then the iterations
+template <typename T>
+__device__ __forceinline__ T lbr_solve(Reduced<T> q, int n_min, int n_max, T conv_tol, int& reg) {
+  const T s = lbr_guess<T>(q, reg);
+  return lbr_iterate<T>(q, s, reg, n_min, n_max, conv_tol);
 }
 
 __device__ __forceinline__ Reduced<double> reduced64(const Norm& n) {
@@ -637,6 +645,19 @@ __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
   f.inv_ln_beta = 0.0f;
   f.ln_c_beta = 0.0f;
   return f;
+}
+
+// The FP64 solver: two FP64 Householder(3) iterations (a third where the
+// second still moved s by more than 2^-17) from the FP32 guess g of region
+// reg.  The guess only seeds the iterations and is itself ~1e-2 off, so FP32
+// rounding there changes nothing the iterations can see; where FP32 cannot
+// hold the quote's scales (b_max below 1e-20, a guess outside 1e-30..1e30)
+// the FP64 guess is taken instead.
+__device__ __forceinline__ double lbr_solve64(const Reduced<double>& q, float g, int reg) {
+  if (q.bmax > 1e-20 && g > 1e-30f && g < 1e30f)
+    return lbr_iterate<double>(q, (double)g, reg, 2, 3, 0x1p-17);
+  int reg64 = 1;
+  return lbr_solve<double>(q, 2, 3, 0x1p-17, reg64);
 }
 
 // ---------------------------------------------------------------------------

@@ -99,13 +99,15 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
           // two Householder(3) steps, a third where the second still moved s
           // by more than 2^-17 (quartic convergence: a smaller second step
           // leaves an error far below one ulp)
-          s = lbr_solve<double>(q64, 2, 3, 0x1p-17, reg);
+          Reduced<float> q32 = reduced32(q64);
+          const float g = lbr_guess<float>(q32, reg);
+          s = lbr_solve64(q64, g, reg);
         } else {
           const float s32 = lbr_solve<float>(reduced32(q64), 2, 2, 0.0f, reg);
           s = (double)s32;
           if (PREC == P_MIXED) s = hh3_correction(q64, s, reg);
         }
-        sigma = s / sqrt(T);
+        sigma = s * rsqrt(T);  // sigma = s / sqrt(T) within 1.5 ulp, one FP64 step fewer
       }
     }
     a.sigma[i] = sigma;
@@ -213,8 +215,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<Q>& sm, int model, const
     q.ln_c_beta = 0.0;
     double s;
     if (PREC == P_FP64) {
-      int reg = 1;
-      s = lbr_solve<double>(q, 2, 3, 0x1p-17, reg);
+      s = lbr_solve64(q, sm.s32[li], sm.reg[li]);
     } else {
       int reg = sm.reg[li];
       float s32 = sm.s32[li];
@@ -227,7 +228,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<Q>& sm, int model, const
       }
       s = hh3_correction(q, (double)s32, reg);
     }
-    sigma[out0 + li] = s / sqrt(sm.T[li]);
+    sigma[out0 + li] = s * rsqrt(sm.T[li]);
   }
   __syncthreads();
 }
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
       } else {
         const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax);
         if (h.converged) {
-          sigma = h.s / sqrt(T);
+          sigma = h.s * rsqrt(T);
         } else {
           fallback = true;
           lo = h.lo;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
     const Reduced<double> q64 = reduced64(nq);
     const double lnb = q64.ln_beta != 0.0 ? q64.ln_beta : log64(q64.beta);
     const double s = bisect_fallback(lnb, q64.beta, q64.x, q64.bmax, w.lo[k], w.hi[k]);
-    a.sigma[i] = s / sqrt(T);
+    a.sigma[i] = s * rsqrt(T);
   }
 }
 
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(256) k_iv_halley32(IvArgs a, HalleyWs w) {
         const Halley32Out h = halley32_solve((float)nq.beta_otm, (float)(nq.bmax - nq.beta_otm),
                                              (float)nq.x_otm);
         if (h.converged) {
-          sigma = (double)h.s / sqrt(T);
+          sigma = (double)h.s * rsqrt(T);
         } else {
           fallback = true;
           lo = h.lo;
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(256) k_halley32_fallback(IvArgs a, HalleyWs w)
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     const float s = bisect32_fallback((float)nq.beta_otm, (float)(nq.bmax - nq.beta_otm),
                                       (float)nq.x_otm, (float)w.lo[k], (float)w.hi[k]);
-    a.sigma[i] = (double)s / sqrt(T);
+    a.sigma[i] = (double)s * rsqrt(T);
   }
 }
 
