@@ -78,9 +78,31 @@ struct Prec<float> {
   static constexpr float ln_p_floor = -80.0f;
 };
 
-__device__ __forceinline__ double f_exp(double v) { return exp(v); }
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
+// FP64 exponential, the table-driven method of P. T. P. Tang (ACM TOMS
+// 15(2), 1989): k = round(v 64/ln2), r = v - k ln2/64 (36-bit head, exact
+// product), j = k mod 64, m = floor(k/64),
+//   exp(v) = 2^m (T_hi[j] + (T_hi[j] expm1(r) + T_lo[j])),
+// T_hi + T_lo = 2^(j/64), expm1(r) to r^6 for |r| <= ln2/128.  Arguments whose
+// result is subnormal, infinite or NaN take the library routine; below
+// -745.2 the result is 0.
+__device__ __forceinline__ double exp64(double v) {
+  if (!(v > -708.3 && v < 709.7)) return v < -745.2 ? 0.0 : exp(v);
+  const double t = fma(v, FV_EXP_INV_LN2_64, 6755399441055744.0);  // 1.5 * 2^52: round to integer
+  const int k = __double2loint(t);
+  const double kd = t - 6755399441055744.0;
+  double r = fma(kd, -FV_EXP_LN2_64_HI, v);
+  r = fma(kd, -FV_EXP_LN2_64_LO, r);
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(r * r, q, r);  // expm1(r)
+  const double2 tj = __ldg(reinterpret_cast<const double2*>(kExpTable) + (k & 63));
+  return (tj.x + fma(tj.x, p, tj.y)) * __hiloint2double(((k >> 6) + 1023) << 20, 0);
+}
+
 // FP64 erfcx(z) = exp(z^2) erfc(z).  FP64 is the scarce unit of this GPU, and
 // the solvers evaluate erfcx more often than any other FP64 function, so it
 // is not the general library routine: for 0 <= z < 128 a degree-10 piecewise
@@ -126,7 +148,7 @@ __device__ __forceinline__ double erfcx64(double z) {
   const double p = erfcx_nonneg(fabs(z));
   if (!(z < 0.0)) return p;
   const double zz = z * z, zl = fma(z, z, -zz);
-  const double e2 = 2.0 * exp(zz);
+  const double e2 = 2.0 * exp64(zz);
   return isinf(e2) ? e2 : fma(e2, zl, e2) - p;
 }
 
@@ -167,6 +189,7 @@ __device__ __forceinline__ double log64(double y) {
 }
 
 __device__ __forceinline__ double f_erfcx(double v) { return erfcx64(v); }
+__device__ __forceinline__ double f_exp(double v) { return exp64(v); }
 __device__ __forceinline__ double f_log(double v) { return log64(v); }
 __device__ __forceinline__ float f_erfcx(float v) { return erfcxf(v); }
 __device__ __forceinline__ double f_ncdf(double v) { return normcdf(v); }
@@ -201,16 +224,23 @@ struct Norm {
 // relative to itself; log(F/K) would carry one ulp of 1 in absolute error.
 __device__ __forceinline__ double log_moneyness(double SF, double K) {
   return (SF >= 0.5 * K && SF <= 2.0 * K) ? log1p(__ddiv_rn(__dsub_rn(SF, K), K))
-                                          : log(__ddiv_rn(SF, K));
+                                          : log64(__ddiv_rn(SF, K));
 }
 
-__device__ __forceinline__ bool pos_finite(double v) { return isfinite(v) && v > 0.0; }
+// finiteness tests on the bit pattern (integer unit, not the FP64 pipe)
+__device__ __forceinline__ bool bits_finite(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool pos_finite(double v) {
+  const long long b = __double_as_longlong(v);  // > 0: positive, nonzero; below +inf: finite
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
 
 __device__ __forceinline__ bool inputs_valid(int model, double SF, double K, double T, double r,
                                              double q, int flag) {
   if (!(flag == 1 || flag == -1)) return false;
-  if (!pos_finite(SF) || !pos_finite(K) || !pos_finite(T) || !isfinite(r)) return false;
-  if (model == M_BSM && !isfinite(q)) return false;
+  if (!pos_finite(SF) || !pos_finite(K) || !pos_finite(T) || !bits_finite(r)) return false;
+  if (model == M_BSM && !bits_finite(q)) return false;
   return true;
 }
 
@@ -224,7 +254,9 @@ __device__ __forceinline__ double model_x(int model, double SF, double K, double
 }
 
 // The status rule: every product and sum rounded as written (no contraction),
-// so the decision matches an FP64 evaluation of the same expressions.
+// so the decision matches an FP64 evaluation of the same expressions up to the
+// last-place differences of exp / expm1 / log1p / log implementations, which
+// the 64-ulp band of the bound tests absorbs.
 __device__ __forceinline__ Norm decide(int model, double P, double SF, double K, double T,
                                        double r, double q, int flag) {
   Norm o;
@@ -232,7 +264,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   o.solve = false;
   o.x = o.beta = o.iota = o.beta_otm = o.x_otm = o.ln_beta = 0.0;
   o.bmax = 1.0;
-  if (!isfinite(P) || !inputs_valid(model, SF, K, T, r, q, flag)) return o;
+  if (!bits_finite(P) || !inputs_valid(model, SF, K, T, r, q, flag)) return o;
   const double qq = model == M_BSM ? q : 0.0;
   const double x = model_x(model, SF, K, T, r, qq);
   double beta;
@@ -242,14 +274,17 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   // beta of a price near the bottom of the FP64 range has lost digits to
   // subnormal rounding; its logarithm is taken from P directly
   o.ln_beta = (beta < 1e-280 && P > 0.0) ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K)) : 0.0;
-  if (!isfinite(x) || !isfinite(beta)) return o;
+  if (!bits_finite(x) || !bits_finite(beta)) return o;
   // Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 (from expm1,
   // accurate near the money) an in-the-money quote's intrinsic value is
   // e^{|x|/2} - e^{-|x|/2} = -E (1 + Em) / Em, accurate for every x
-  const double E = expm1(-0.5 * fabs(x));
   const double Em = exp(-0.5 * fabs(x));
-  const bool itm = flag * x > 0.0;
-  const double iota = itm ? __ddiv_rn(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em) : 0.0;
+  const bool itm = flag > 0 ? x > 0.0 : x < 0.0;
+  double iota = 0.0;
+  if (itm) {
+    const double E = expm1(-0.5 * fabs(x));
+    iota = __ddiv_rn(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em);
+  }
   o.x = x;
   o.beta = beta;
   o.iota = iota;

@@ -1,11 +1,12 @@
-"""Write fv_fp64_tables.h: the tables of the kernels' own FP64 erfcx and log.
+"""Write fv_fp64_tables.h: the tables of the kernels' own FP64 erfcx, log and exp.
 
 On this GPU an FP64 operation costs as much issue time as ~70 FP32 ones, and
 the solvers of Section 2.2 spend most of their FP64 work in two functions: the
 scaled complementary error function erfcx(z) = exp(z^2) erfc(z) (the
 normalised Black function is a difference of two erfcx values) and the
-logarithm (the lowest- and highest-region objectives work with ln b).  The
-kernels evaluate both from small tables instead of general library routines.
+logarithm (the lowest- and highest-region objectives work with ln b), and
+every evaluation takes one exponential.  The kernels evaluate all three from
+small tables instead of general library routines.
 
 erfcx on 0 <= z < 128: Chebyshev interpolation (Trefethen, Approximation
 Theory and Approximation Practice, ch. 4) on short pieces, the piecewise
@@ -32,6 +33,13 @@ nothing), split so that m ln2_hi + L_hi[j] is exact (both on a 2^-42 grid),
 and log1p(r), |r| <= 0.0056, is its Taylor polynomial to r^8.  c_0 = 1, so
 next to y = 1 the result is log1p(y - 1) with y - 1 exact.
 
+exp: the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989).  With
+k = round(v 64/ln2), r = v - k ln2/64 (ln2/64 split into a 36-bit head, so
+k ln2_64_hi is exact, and a tail) and j = k mod 64, m = floor(k/64):
+    exp(v) = 2^m (T_hi[j] + (T_hi[j] expm1(r) + T_lo[j])),
+T_hi + T_lo = 2^(j/64) to 2^-106 and expm1(r), |r| <= ln2/128, its Taylor
+polynomial to r^6.
+
 Run:  python gen_fp64_tables.py [samples per piece]
 (needs mpmath; prints the worst error of the FP64 erfcx Horner evaluation,
 emulated with exactly rounded fused multiply-adds, against mpmath on a dense
@@ -53,6 +61,7 @@ BINADES = range(-1, 7)
 Z_TABLE_END = 128.0
 
 LOG_J = range(-37, 54)   # F_j = 1 + j/128 covers [1/sqrt2, sqrt2)
+EXP_N = 64
 LOG_GRID = 2.0 ** -42    # m ln2_hi and L_hi are multiples of this
 
 mp.mp.dps = 50
@@ -130,8 +139,23 @@ def log_table():
     return ln2_hi, ln2_lo, rows
 
 
+def exp_table():
+    ln2_64 = mp.log(2) / EXP_N
+    e = int(mp.floor(mp.log(ln2_64, 2)))
+    q = mp.mpf(2) ** (e - 35)               # 36 significant bits
+    hi = float(mp.nint(ln2_64 / q) * q)
+    lo = float(ln2_64 - hi)
+    rows = []
+    for j in range(EXP_N):
+        t = mp.mpf(2) ** (mp.mpf(j) / EXP_N)
+        t_hi = float(t)
+        rows.append((t_hi, float(t - t_hi)))
+    return float(EXP_N / mp.log(2)), hi, lo, rows
+
+
 def write(table, out=OUT):
     ln2_hi, ln2_lo, lrows = log_table()
+    inv, e_hi, e_lo, erows = exp_table()
     lines = [
         "// Generated by gen_fp64_tables.py (beside this file); do not edit.",
         "#pragma once",
@@ -160,6 +184,18 @@ def write(table, out=OUT):
     ]
     for c, hi, lo in lrows:
         lines.append("    %r, %r, %r, 0.0," % (c, hi, lo))
+    lines += [
+        "};",
+        "",
+        "// exp: row j holds T_hi[j], T_lo[j] with T_hi + T_lo = 2^(j/64); ln2/64 = LN2_64_HI +",
+        "// LN2_64_LO with a 36-bit head.",
+        "#define FV_EXP_INV_LN2_64 %r" % inv,
+        "#define FV_EXP_LN2_64_HI %r" % e_hi,
+        "#define FV_EXP_LN2_64_LO %r" % e_lo,
+        "static __device__ __align__(16) const double kExpTable[%d * 2] = {" % EXP_N,
+    ]
+    for hi, lo in erows:
+        lines.append("    %r, %r," % (hi, lo))
     lines.append("};")
     with open(out, "w") as f:
         f.write("\n".join(lines) + "\n")

@@ -75,6 +75,34 @@ def _log64(y, tab):
     return _fma(md, ln2_hi, L_hi) + (_fma(md, ln2_lo, L_lo) + p)
 
 
+def _exp_table():
+    src = open(HEADER).read()
+    inv = float(re.search(r"#define FV_EXP_INV_LN2_64 (\S+)", src).group(1))
+    hi = float(re.search(r"#define FV_EXP_LN2_64_HI (\S+)", src).group(1))
+    lo = float(re.search(r"#define FV_EXP_LN2_64_LO (\S+)", src).group(1))
+    body = src[src.index("kExpTable"):]
+    body = body[body.index("{") + 1:body.index("};")]
+    vals = [float(v) for v in body.replace("\n", " ").split(",") if v.strip()]
+    return inv, hi, lo, np.array(vals).reshape(-1, 2)
+
+
+def _exp64(v, tab):
+    """The kernel's exp64 for -708.3 < v < 709.7, operation by operation."""
+    inv, hi, lo, rows = tab
+    big = 6755399441055744.0
+    t = _fma(v, inv, big)
+    k = int(t - big)
+    kd = t - big
+    r = _fma(kd, -hi, v)
+    r = _fma(kd, -lo, r)
+    q = _fma(r, 1.0 / 720.0, 1.0 / 120.0)
+    for c in (1.0 / 24.0, 1.0 / 6.0, 0.5):
+        q = _fma(q, r, c)
+    p = _fma(r * r, q, r)
+    t_hi, t_lo = rows[k & 63]
+    return (t_hi + _fma(t_hi, p, t_lo)) * 2.0 ** (k >> 6)
+
+
 def _piece(z):
     if z < 0.5:
         return int(z * 8.0)
@@ -136,3 +164,19 @@ def test_log_within_one_and_a_half_ulp():
     # final rounding (1/2 ulp) plus the second sum's rounding relative to a
     # result that can be as small as ln(1 + 1/256)
     assert worst <= 1.5 * 2.0 ** -52, worst
+
+
+def test_exp_within_one_ulp():
+    mp.mp.dps = 40
+    tab = _exp_table()
+    # the split head of ln2/64 has 36 significant bits: k ln2_64_hi is exact for |k| < 2^17
+    hi = tab[1]
+    assert (int(hi * 2 ** 42) == hi * 2 ** 42) and abs(int(hi * 2 ** 42)) < 2 ** 36
+    g = np.random.default_rng(7)
+    v = np.concatenate([g.uniform(-708.3, 709.7, 2000), g.uniform(-1e-3, 1e-3, 500),
+                        g.uniform(-1, 1, 500), [0.0, 1.0, -1.0, 709.69, -708.29]])
+    worst = 0.0
+    for vi in v:
+        ref = mp.exp(mp.mpf(float(vi)))
+        worst = max(worst, abs(float((_exp64(float(vi), tab) - ref) / ref)))
+    assert worst <= 2.0 ** -52, worst

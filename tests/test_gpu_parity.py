@@ -126,6 +126,24 @@ def test_log_against_extended_precision(fv, torch_dev):
     assert sp[4] == pytest.approx(np.log(5e-324), rel=1e-15)
 
 
+def test_exp_against_extended_precision(fv, torch_dev):
+    # the kernels' own FP64 exp (Tang's table-driven method) against numpy's
+    # long double exp; subnormal, overflowing and NaN arguments included
+    torch, dev = torch_dev
+    g = np.random.default_rng(11)
+    v = np.concatenate([g.uniform(-708, 709.5, 100000), g.uniform(-1e-3, 1e-3, 20000),
+                        g.uniform(-30, 5, 20000), [0.0, -0.0, 1.0, -1.0, 709.7, -708.3]])
+    got = _np(fv.fv_math(fv.FV_MATH_EXP, torch.tensor(v, device=dev)))
+    ref = np.exp(v.astype(np.longdouble))
+    rel = np.abs((got - ref) / ref).astype(np.float64)
+    # Tang's bound: the final rounding plus the polynomial's, about 0.54 ulp
+    assert rel.max() <= 2.0 ** -52, rel.max()
+    sp = _np(fv.fv_math(fv.FV_MATH_EXP, torch.tensor([-745.3, -740.0, 710.0, np.inf, -np.inf, np.nan],
+                                                      dtype=torch.float64, device=dev)))
+    assert sp[0] == 0 and sp[1] == pytest.approx(np.exp(-740.0), rel=1e-12) and sp[2] == np.inf
+    assert sp[3] == np.inf and sp[4] == 0 and np.isnan(sp[5])
+
+
 def test_normalised_black_against_binary128(fv, torch_dev):
     xs = np.concatenate([-np.logspace(-8, np.log10(40), 60), [0.0], np.logspace(-8, np.log10(40), 60)])
     ss = np.logspace(-4, np.log10(50), 90)
