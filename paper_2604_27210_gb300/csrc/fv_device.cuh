@@ -270,7 +270,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   double beta;
   const double rate = model == M_BLACK76 ? __dmul_rn(r, T)
                                          : __dmul_rn(__dmul_rn(0.5, __dadd_rn(r, qq)), T);
-  beta = __ddiv_rn(__dmul_rn(P, exp(rate)), sqrt(__dmul_rn(SF, K)));
+  beta = __ddiv_rn(__dmul_rn(P, exp64(rate)), sqrt(__dmul_rn(SF, K)));
   // beta of a price near the bottom of the FP64 range has lost digits to
   // subnormal rounding; its logarithm is taken from P directly
   o.ln_beta = (beta < 1e-280 && P > 0.0) ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K)) : 0.0;
@@ -278,7 +278,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   // Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 (from expm1,
   // accurate near the money) an in-the-money quote's intrinsic value is
   // e^{|x|/2} - e^{-|x|/2} = -E (1 + Em) / Em, accurate for every x
-  const double Em = exp(-0.5 * fabs(x));
+  const double Em = exp64(-0.5 * fabs(x));
   const bool itm = flag > 0 ? x > 0.0 : x < 0.0;
   double iota = 0.0;
   if (itm) {
@@ -391,7 +391,7 @@ __device__ __forceinline__ T nb_log(const NB<T>& v) {
 __device__ __forceinline__ double normalised_black(double x, double s, int theta) {
   double iota = 0.0;
   if (theta * x > 0.0) {
-    const double E = expm1(-0.5 * fabs(x)), Em = exp(-0.5 * fabs(x));
+    const double E = expm1(-0.5 * fabs(x)), Em = exp64(-0.5 * fabs(x));
     iota = -E * (1.0 + Em) / Em;
   }
   if (!(s > 0.0)) return iota;
