@@ -212,13 +212,13 @@ def time_steps(torch, fn, steps, warmup, world_size):
     return total_ms, kernel_ms
 
 
-E2E_CHUNK = 1 << 21
+E2E_CHUNK = 1 << 20
 
 
 def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
     """The same metric through the public API from pinned host buffers: each step
     is one fv_implied_vol_host call, which copies that step's inputs to the
-    device and sigma + status back, in 2M-quote chunks overlapped with the
+    device and sigma + status back, in 1M-quote chunks overlapped with the
     solve on two streams."""
     keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
     host = {k: t_dev[k].cpu().pin_memory() for k in keys}

@@ -698,7 +698,7 @@ cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStr
 // Persistent CTAs walk a static tile table; each tile (kBinThreads * Q quotes
 // of one chain) goes through the binned FP64 LBR.
 template <int Q>
-__global__ void __launch_bounds__(kBinThreads) k_chains(int model, const ChainDesc* __restrict__ chains,
+__global__ void __launch_bounds__(kBinThreads, Q == 1 ? 4 : 1) k_chains(int model, const ChainDesc* __restrict__ chains,
                                                         const Tile* __restrict__ tiles, int64_t n_tiles) {
   __shared__ BinSmem<Q> sm;
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
