@@ -257,11 +257,11 @@ static void launch_binned(const IvArgs& a, cudaStream_t st) {
 }
 
 // Tile shapes measured on GB300 (16.8 M quotes of the BSM grid, one resident
-// wave of blocks): the FP64 solve runs best with 1 quote per thread and 4
-// blocks per SM (22.8 ms; 2 quotes per thread 23.1 ms, 4 with no register cap
-// 23.4 ms); the mixed path with 2 quotes per thread, 4 blocks per SM and its
-// FP32 iterations in phase 2, where they interleave with the FP64 correction
-// (11.8 ms; 1 or 2 quotes per thread at 3 to 5 blocks per SM within 0.6 %).
+// wave of blocks): the FP64 solve runs best with 2 quotes per thread and 4
+// blocks per SM (13.8 ms; 2 x 3 13.9 ms, 1 x 4 14.2 ms, 1 x 5 14.4 ms); the
+// mixed path with 2 quotes per thread, 4 blocks per SM and its FP32
+// iterations in phase 2, where they interleave with the FP64 correction
+// (10.9 ms; 1 or 2 quotes per thread at 3 to 5 blocks per SM within 1.2 %).
 // The FP32 path has no FP64 solve to sort for and stays unbinned.
 // Below kSmallBatch quotes a launch is latency-bound (a warp's ~900
 // dependent FP64 instructions): the unbinned kernel with 64-thread blocks
@@ -294,10 +294,10 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
     return cudaGetLastError();
   }
   if (a.f32_inputs) {
-    if (prec == P_FP64) launch_binned<float, P_FP64, 1, 4, false>(a, st);
+    if (prec == P_FP64) launch_binned<float, P_FP64, 2, 4, false>(a, st);
     else launch_binned<float, P_MIXED, 2, 4, true>(a, st);
   } else {
-    if (prec == P_FP64) launch_binned<double, P_FP64, 1, 4, false>(a, st);
+    if (prec == P_FP64) launch_binned<double, P_FP64, 2, 4, false>(a, st);
     else launch_binned<double, P_MIXED, 2, 4, true>(a, st);
   }
   return cudaGetLastError();
