@@ -529,14 +529,28 @@ cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const 
 struct D12 {
   double d1, s, N1, N2, n1;
 };
+// e^{-z^2/2} with z^2 split exactly into zz + zl (so the exponent's rounding
+// does not grow with z^2)
+__device__ __forceinline__ double gauss64(double z) {
+  const double zz = z * z, zl = fma(z, z, -zz);
+  const double e = exp64(-0.5 * zz);
+  return fma(e, -0.5 * zl, e);
+}
+// Phi(z) from the table erfcx and ez = e^{-z^2/2}: the lower tail
+// erfcx(|z|/sqrt2) ez / 2 (no cancellation), or one minus it above zero
+__device__ __forceinline__ double ncdf64(double z, double ez) {
+  const double tail = 0.5 * erfcx64(fabs(z) * kInvSqrt2) * ez;
+  return z <= 0.0 ? tail : 1.0 - tail;
+}
 __device__ __forceinline__ D12 d12(double x, double s, int th) {
   D12 o;
   o.s = s;
   o.d1 = x / s + 0.5 * s;
   const double d2 = o.d1 - s;
-  o.N1 = normcdf(th * o.d1);
-  o.N2 = normcdf(th * d2);
-  o.n1 = kInvSqrt2Pi * exp(-0.5 * o.d1 * o.d1);
+  const double e1 = gauss64(o.d1), e2 = gauss64(d2);
+  o.N1 = ncdf64(th * o.d1, e1);
+  o.N2 = ncdf64(th * d2, e2);
+  o.n1 = kInvSqrt2Pi * e1;
   return o;
 }
 
