@@ -718,55 +718,62 @@ void or_iv_lbr(int model, const double* P, const double* S_or_F, const double* K
 #define HALLEY_STEPS 8
 #define HALLEY_CONV_TOL 1e-10
 
-/* Fallback: bisection on the monotone residual ln b(s) - ln beta inside
- * [lo, hi], each bisection replaced by a Newton step when that step stays in
- * the bracket (Newton on the log residual does not crawl in the exponential
- * lowest wing, where b - beta does). */
+/* Fallback: bisection inside [lo, hi] on a residual increasing in s, each
+ * bisection replaced by a Newton step when that step stays in the bracket.
+ * The residual is the transformed objective of the LBR wings (Section 2.2),
+ * under which Newton does not crawl where b is exponentially small:
+ *   beta <= b_max/2:  f = 1/ln beta - 1/ln b,               f' = (b'/b) / ln^2 b
+ *   beta >  b_max/2:  f = ln(b_max - beta) - ln(b_max - b),  f' = b'/(b_max - b)
+ * Without an upper end the Newton step (at least doubling s, at most x16)
+ * grows the bracket; without a lower end it shrinks it (at least halving,
+ * at most /16). */
+static double fallback_resid(double x, double s, int upper, double ln_c_beta, double inv_ln_beta,
+                             double* fp) {
+  const double vega = vega_d(x, s);
+  if (upper) {
+    const double c = nbc_d(x, s);
+    *fp = vega / c;
+    return ln_c_beta - log(c);
+  }
+  double L, qb;
+  nb_log_d(x, s, &L, &qb);
+  *fp = qb / (L * L);
+  return inv_ln_beta - 1.0 / L;
+}
+
 static double bisect_fallback(double beta, double x, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
-  /* residual increasing in s: ln b - ln beta, or above b_max / 2 the
-   * log-complement ln(b_max - beta) - ln(b_max - b) */
   const double bmax = exp(0.5 * x);
   const int upper = beta > 0.5 * bmax;
-  const double ln_beta = log(beta), ln_c_beta = upper ? log(bmax - beta) : 0.0;
-  if (!isfinite(hi)) {
-    hi = fmax(2.0 * lo, 1e-3);
-    while (nb_d(x, hi) <= beta && hi < 1e6) {
-      lo = hi;
-      hi *= 2.0;
-    }
-  }
-  if (!(lo > 0)) {
-    lo = 0.5 * hi;
-    while (nb_d(x, lo) >= beta && lo > 1e-300) {
-      hi = lo;
-      lo *= 0.5;
-    }
-  }
-  double s = 0.5 * (lo + hi);
+  const double ln_c_beta = upper ? log(bmax - beta) : 0.0;
+  const double inv_ln_beta = upper ? 0.0 : 1.0 / log(beta);
+  double s;
+  if (lo > 0 && isfinite(hi))
+    s = 0.5 * (lo + hi);
+  else if (isfinite(hi))
+    s = 0.5 * hi;
+  else
+    s = fmax(2.0 * lo, 1e-3);
   for (int it = 0; it < 400; it++) {
-    double f, fp;
-    if (upper) {
-      const double c = nbc_d(x, s);
-      f = ln_c_beta - log(c);
-      fp = vega_d(x, s) / c;
-    } else {
-      double L, qb;
-      nb_log_d(x, s, &L, &qb);
-      f = L - ln_beta;
-      fp = qb;
-    }
-    if (f < 0)
-      lo = s;
-    else if (f > 0)
+    double fp;
+    const double f = fallback_resid(x, s, upper, ln_c_beta, inv_ln_beta, &fp);
+    /* a NaN residual comes from b underflowing at s far below the root */
+    if (f > 0)
       hi = s;
+    else if (f < 0 || f != f)
+      lo = s;
     else
       return s;
-    const double sn = s - f / fp;
-    const double next = (sn > lo && sn < hi) ? sn : 0.5 * (lo + hi);
-    const double ds = next - s;
-    s = next;
-    if (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi) break;
+    double sn = s - f / fp;
+    if (!isfinite(hi))
+      sn = (isfinite(sn) && sn > s) ? fmin(sn, 16.0 * s) : 2.0 * s;
+    else if (!(lo > 0))
+      sn = (isfinite(sn) && sn > 0 && sn < s) ? fmax(sn, s / 16.0) : 0.5 * s;
+    else if (!(sn > lo && sn < hi))
+      sn = 0.5 * (lo + hi);
+    const double ds = sn - s;
+    s = sn;
+    if (lo > 0 && isfinite(hi) && (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi)) break;
   }
   return s;
 }

@@ -745,53 +745,55 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
   return o;
 }
 
-// Bisection in [lo, hi] on a residual increasing in s, Newton steps kept when
-// inside: ln b - ln beta, or for beta > b_max/2 the log-complement
-// ln(b_max - beta) - ln(b_max - b) (ln_beta is passed in: for subnormal-range
-// prices it comes from log(P)).
+// Bisection in [lo, hi] on a residual increasing in s, each bisection replaced
+// by a Newton step when that step stays in the bracket.  The residual is the
+// transformed objective of the LBR wings (Section 2.2), under which Newton does
+// not crawl where b is exponentially small:
+//   beta <= b_max/2:  f = 1/ln beta - 1/ln b,               f' = (b'/b) / ln^2 b
+//   beta >  b_max/2:  f = ln(b_max - beta) - ln(b_max - b),  f' = b'/(b_max - b)
+// Without an upper end the Newton step (at least doubling s, at most x16)
+// grows the bracket; without a lower end it shrinks it (at least halving, at
+// most /16).  ln_beta is passed in: for subnormal-range prices it comes from
+// log(P).
 __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, double x,
                                                   double bmax, double lo, double hi) {
   const double eps = 2.220446049250313e-16;
   const bool upper = beta > 0.5 * bmax;
   const double ln_c_beta = upper ? log64(bmax - beta) : 0.0;
-  NB<double> v;
-  // f(s) > 0 iff b(s) > beta
-  auto resid = [&](double s_) {
-    nb_eval<double>(x, s_, upper, v);
-    return upper ? ln_c_beta - nb_log(v) : nb_log(v) - ln_beta;
-  };
-  if (!isfinite(hi)) {
-    hi = fmax(2.0 * lo, 1e-3);
-    for (int it = 0; it < 64; it++) {
-      if (resid(hi) > 0.0) break;
-      lo = hi;
-      hi *= 2.0;
+  const double inv_ln_beta = upper ? 0.0 : 1.0 / ln_beta;
+  const bool has_hi = isfinite(hi);
+  double s = (lo > 0.0 && has_hi) ? 0.5 * (lo + hi) : (has_hi ? 0.5 * hi : fmax(2.0 * lo, 1e-3));
+  for (int it = 0; it < 400; it++) {
+    NB<double> v;
+    nb_eval<double>(x, s, upper, v);
+    const double L = nb_log(v);
+    const double qw = kInvSqrt2Pi / v.B;  // b'/b (lower) or b'/(b_max - b) (upper)
+    double f, fp;
+    if (upper) {
+      f = ln_c_beta - L;
+      fp = qw;
+    } else {
+      const double iL = 1.0 / L;
+      f = inv_ln_beta - iL;
+      fp = qw * iL * iL;
     }
-  }
-  if (!(lo > 0.0)) {
-    lo = 0.5 * hi;
-    for (int it = 0; it < 1100; it++) {
-      if (resid(lo) < 0.0) break;
-      hi = lo;
-      lo *= 0.5;
-    }
-  }
-  double s = 0.5 * (lo + hi);
-  for (int it = 0; it < 200; it++) {
-    const double f = resid(s);
-    if (f < 0.0)
-      lo = s;
-    else if (f > 0.0)
+    // a NaN residual comes from b underflowing at s far below the root
+    if (f > 0.0)
       hi = s;
+    else if (f < 0.0 || f != f)
+      lo = s;
     else
       break;
-    // f' = b'/b (lower form) or b'/(b_max - b) (upper form)
-    const double qw = kInvSqrt2Pi / v.B;
-    const double sn = s - f / qw;
-    const double next = (sn > lo && sn < hi) ? sn : 0.5 * (lo + hi);
-    const double ds = next - s;
-    s = next;
-    if (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi) break;
+    double sn = s - f / fp;
+    if (!isfinite(hi))
+      sn = (isfinite(sn) && sn > s) ? fmin(sn, 16.0 * s) : 2.0 * s;
+    else if (!(lo > 0.0))
+      sn = (isfinite(sn) && sn > 0.0 && sn < s) ? fmax(sn, s * 0.0625) : 0.5 * s;
+    else if (!(sn > lo && sn < hi))
+      sn = 0.5 * (lo + hi);
+    const double ds = sn - s;
+    s = sn;
+    if (lo > 0.0 && isfinite(hi) && (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi)) break;
   }
   return s;
 }

@@ -86,8 +86,8 @@ MUTANTS = [
     ("Halley: residual b - beta with the wrong sign",
      "const double g = upper ? (bmax - beta) - nbc_d(x, s) : nb_d(x, s) - beta;",
      "const double g = upper ? (bmax - beta) - nbc_d(x, s) : beta - nb_d(x, s);"),
-    ("Halley fallback: log residual with the wrong sign",
-     "f = L - ln_beta;", "f = ln_beta - L;"),
+    ("Halley fallback: transformed residual with the wrong sign",
+     "return inv_ln_beta - 1.0 / L;", "return 1.0 / L - inv_ln_beta;"),
     # Greeks and the gradient
     ("Greeks: theta without the sign change",
      "c->out4[i] = (double)(-p.dT / 365.0f128);", "c->out4[i] = (double)(p.dT / 365.0f128);"),
