@@ -710,44 +710,32 @@ struct HalleyOut {
 // beta > b_max/2: b_max - b then comes from the cancellation-free complement,
 // so g carries an error relative to b_max - b instead of to b_max (the same
 // function, with the same Halley step).
-// warp_mask: the lanes of the warp that call this together (every one of them
-// takes the same number of sweeps).  A warp stops sweeping once every lane's
-// Newton distance is below the tolerance: the step after it took s to within
-// ~(1e-10)^3 of the root, so the remaining sweeps of the eight would leave s
-// where it is.
-__device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double bmax,
-                                                  unsigned warp_mask) {
+__device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double bmax) {
   const bool upper = beta > 0.5 * bmax;
   const double c_beta = bmax - beta;
   double s = kSqrt2Pi * beta;  // Brenner-Subrahmanyam: b ~ s/sqrt(2 pi) at the money
   double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
-  bool done = false;
   for (int k = 0; k < kHalleySteps; k++) {
-    if (!done) {
-      NB<double> v;
-      nb_eval<double>(x, s, upper, v);
-      const double g = upper ? c_beta - v.e * v.B : v.e * v.B - beta;
-      if (g < 0.0) {
-        lo = s;
-      } else if (g > 0.0) {
-        hi = s;
-      } else {
-        // g == 0 is the root; a NaN residual leaves the quote unconverged
-        nerr = (g == 0.0) ? 0.0 : hi;
-        done = true;
-      }
-      if (!done) {
-        const double bp = v.e * kInvSqrt2Pi;
-        const double u = v.h * v.h * v.inv_s - 0.25 * s;
-        // Newton distance to the root relative to s: the convergence test
-        nerr = fabs(g / bp) / s;
-        const double step = -2.0 * g / (2.0 * bp - g * u);
-        double sn = s + step;
-        if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
-        s = sn;
-      }
+    NB<double> v;
+    nb_eval<double>(x, s, upper, v);
+    const double g = upper ? c_beta - v.e * v.B : v.e * v.B - beta;
+    if (g < 0.0) {
+      lo = s;
+    } else if (g > 0.0) {
+      hi = s;
+    } else {
+      // g == 0 is the root; a NaN residual leaves the quote unconverged
+      nerr = (g == 0.0) ? 0.0 : hi;
+      break;
     }
-    if (__all_sync(warp_mask, done || nerr <= kHalleyConvTol)) break;
+    const double bp = v.e * kInvSqrt2Pi;
+    const double u = v.h * v.h * v.inv_s - 0.25 * s;
+    // Newton distance to the root relative to s: the convergence test
+    nerr = fabs(g / bp) / s;
+    const double step = -2.0 * g / (2.0 * bp - g * u);
+    double sn = s + step;
+    if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
+    s = sn;
   }
   HalleyOut o;
   o.s = s;

@@ -331,44 +331,40 @@ static HalleyWs halley_ws(void* ws, int64_t n) {
 
 template <typename InT>
 __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // a warp's lanes take the same trips (lane 0's index decides), so the warp
-  // votes below always see all 32 lanes
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < a.n; i0 += stride) {
-    const int64_t i = i0 + lane;
-    const bool valid = i < a.n;
-    double P = 0.0, SF = 0.0, K = 0.0, T = 1.0, r = 0.0, q = 0.0;
-    int flag = 0;
-    if (valid) load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    double P, SF, K, T, r, q;
+    int flag;
+    load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
-    const bool solving = valid && nq.status == Q_OK && nq.solve;
-    const unsigned solvers = __ballot_sync(0xffffffffu, solving);
     double sigma = qnan();
     bool fallback = false;
     double lo = 0.0, hi = 0.0;
-    if (nq.status == Q_OK && !nq.solve) sigma = 0.0;
-    if (solving) {
-      const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax, solvers);
-      if (h.converged) {
-        sigma = h.s * rsqrt(T);
+    if (nq.status == Q_OK) {
+      if (!nq.solve) {
+        sigma = 0.0;
       } else {
-        fallback = true;
-        lo = h.lo;
-        hi = h.hi;
+        const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax);
+        if (h.converged) {
+          sigma = h.s * rsqrt(T);
+        } else {
+          fallback = true;
+          lo = h.lo;
+          hi = h.hi;
+        }
       }
     }
-    if (valid) {
-      a.sigma[i] = sigma;
-      a.status[i] = (uint8_t)nq.status;
-    }
+    a.sigma[i] = sigma;
+    a.status[i] = (uint8_t)nq.status;
     // warp-aggregated append of the quotes that failed the convergence test
-    const unsigned m = __ballot_sync(0xffffffffu, fallback);
+    const unsigned active = __activemask();
+    const unsigned m = __ballot_sync(active, fallback);
     if (m) {
+      const int lane = threadIdx.x & 31;
       const int leader = __ffs(m) - 1;
       unsigned base = 0;
       if (lane == leader) base = atomicAdd(w.count, (unsigned)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      base = __shfl_sync(active, base, leader);
       if (fallback) {
         const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
         w.idx[pos] = (unsigned)i;
