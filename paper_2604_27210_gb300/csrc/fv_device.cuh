@@ -356,13 +356,14 @@ __device__ __forceinline__ T small_t_series(T h, T t, T R) {
 }
 
 // b(x, s) for x <= 0 (or its complement b_max - b when comp), scaled by e.
+// with_e = false leaves o.e unset: the wing objectives use only B and ln b.
 template <typename T>
-__device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o) {
+__device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e) {
   o.inv_s = T(1) / s;
   o.h = x * o.inv_s;
   o.t = T(0.5) * s;
   const T h = o.h, t = o.t;
-  o.e = f_exp(T(-0.5) * (h * h + t * t));
+  o.e = with_e ? f_exp(T(-0.5) * (h * h + t * t)) : T(0);
   const bool small = (t < Prec<T>::t_small) && !comp;
   const T a1 = small ? -h * T(kInvSqrt2) : (comp ? (h + t) : -(h + t)) * T(kInvSqrt2);
   const T Y1 = f_erfcx(a1);
@@ -396,7 +397,7 @@ __device__ __forceinline__ double normalised_black(double x, double s, int theta
   }
   if (!(s > 0.0)) return iota;
   NB<double> v;
-  nb_eval<double>(-fabs(x), s, false, v);
+  nb_eval<double>(-fabs(x), s, false, v, true);
   return iota + v.e * v.B;
 }
 
@@ -456,7 +457,7 @@ struct Objective {
 template <typename T>
 __device__ __forceinline__ Objective<T> objective(const Reduced<T>& q, T s, int reg) {
   NB<T> v;
-  nb_eval<T>(q.x, s, reg == 3, v);
+  nb_eval<T>(q.x, s, reg == 3, v, reg == 1 || reg == 2);
   const T hh = v.h * v.h;
   const T u = hh * v.inv_s - T(0.25) * s;                    // b''/b'
   const T du = T(-3) * hh * v.inv_s * v.inv_s - T(0.25);     // d(b''/b')/ds
@@ -505,7 +506,7 @@ __device__ __forceinline__ T guarded(T s, T ds) {
 // once after its FP32 iterations.
 __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg) {
   NB<double> v;
-  nb_eval<double>(q.x, s, reg == 3, v);
+  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2);
   const float hh = (float)(v.h * v.h), is = (float)v.inv_s, sf = (float)s;
   const float u = hh * is - 0.25f * sf;
   const float du = -3.0f * hh * is * is - 0.25f;
@@ -558,7 +559,7 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
   if (xneg) {
     if (T(0.5) * sc < Prec<T>::t_small) {
       NB<T> vc_;
-      nb_eval<T>(x, sc, false, vc_);
+      nb_eval<T>(x, sc, false, vc_, true);
       bc = vc_.e * vc_.B;
     } else {
       bc = T(0.5) * bmax * (T(1) - f_erfcx(f_sqrt(-x)));
@@ -571,7 +572,7 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
   const bool degenerate = !(so > T(0));  // s_l lost to rounding next to x = 0
   if (degenerate) so = sc > T(0) ? sc : T(1);
   NB<T> vo_;
-  nb_eval<T>(x, so, false, vo_);
+  nb_eval<T>(x, so, false, vo_, true);
   const T bo = degenerate ? T(0) : vo_.e * vo_.B;
   const T vo = vo_.e * T(kInvSqrt2Pi);
   // ln b_l, for the region test where b_l underflows the type and for the
@@ -717,7 +718,7 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
   double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
   for (int k = 0; k < kHalleySteps; k++) {
     NB<double> v;
-    nb_eval<double>(x, s, upper, v);
+    nb_eval<double>(x, s, upper, v, true);
     const double g = upper ? c_beta - v.e * v.B : v.e * v.B - beta;
     if (g < 0.0) {
       lo = s;
@@ -765,7 +766,7 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
   double s = (lo > 0.0 && has_hi) ? 0.5 * (lo + hi) : (has_hi ? 0.5 * hi : fmax(2.0 * lo, 1e-3));
   for (int it = 0; it < 400; it++) {
     NB<double> v;
-    nb_eval<double>(x, s, upper, v);
+    nb_eval<double>(x, s, upper, v, false);
     const double L = nb_log(v);
     const double qw = kInvSqrt2Pi / v.B;  // b'/b (lower) or b'/(b_max - b) (upper)
     double f, fp;
