@@ -80,3 +80,48 @@ def test_accuracy_grid_all_paths():
                     "(b' > 1e-8, kappa <= 1e3)\n" % (X.size, 121, 120, solved.sum(), gate.sum()))
     for name, got, bar in bars:
         assert got <= bar, (name, got, bar)
+
+
+def test_extreme_grid_all_paths():
+    # beyond the accuracy figure's range: log-moneyness to +-20 and total
+    # volatility from 1e-4 to 20, where b underflows FP64, the erfcx arguments
+    # reach the asymptotic branch and the Halley sweeps mostly fall back
+    import torch
+    from paper_2604_27210_gb300 import fv
+
+    xs = np.concatenate([-np.logspace(-8, np.log10(20.0), 50), [0.0], np.logspace(-8, np.log10(20.0), 50)])
+    ss = np.logspace(-4, np.log10(20.0), 80)
+    X, S = np.meshgrid(xs, ss, indexing="ij")
+    X, S = np.concatenate([X.ravel(), X.ravel()]), np.concatenate([S.ravel(), S.ravel()])
+    n = X.size
+    flag = np.concatenate([np.ones(n // 2, np.int8), -np.ones(n // 2, np.int8)])
+    F, K, T, r = np.ones(n), np.exp(-X), np.ones(n), np.zeros(n)
+    P = orc.price(0, F, K, T, r, None, S, flag)
+    ref, st = orc.iv(0, P, F, K, T, r, None, flag)
+    v, kap = orc.conditioning(0, P, F, K, T, r, None, flag, ref)
+    # subnormal prices carry a few significant bits: their sigma is checked for
+    # being a positive number only
+    normal = P >= 1e-290
+    dev = torch.device("cuda:0")
+    t = [torch.tensor(a, device=dev) for a in (P, F, K, T, r)]
+    ft = torch.tensor(flag, device=dev)
+    paths = (("LBR FP64", lambda: fv.fv_implied_vol(0, fv.FV_LBR, *t, None, ft), 1e-12, 1e-12),
+             ("Halley FP64", lambda: fv.fv_implied_vol(0, fv.FV_HALLEY, *t, None, ft), 1e-12, 1e-12),
+             ("mixed", lambda: fv.fv_implied_vol_ex(0, fv.FV_LBR, fv.FV_MIXED, *t, None, ft), 1e-12,
+              1e-12),
+             ("LBR FP32", lambda: fv.fv_implied_vol_ex(0, fv.FV_LBR, fv.FV_FP32, *t, None, ft), 1e-5,
+              None))
+    for name, fn, tol_gate, tol_rest in paths:
+        s_gpu, st_gpu = fn()
+        s_gpu, st_gpu = s_gpu.cpu().numpy(), st_gpu.cpu().numpy()
+        assert np.array_equal(st_gpu, st), name
+        solved = (st == orc.OK) & (ref > 0)
+        assert np.all(np.isfinite(s_gpu[solved]) & (s_gpu[solved] > 0)), name
+        assert np.all(s_gpu[(st == orc.OK) & (ref == 0)] == 0), name
+        chk = solved & normal & np.isfinite(ref)
+        rel = np.abs(s_gpu[chk] - ref[chk]) / ref[chk]
+        gate = (v[chk] > 1e-8) & (kap[chk] <= 1e3)
+        assert rel[gate].max() <= tol_gate, (name, rel[gate].max())
+        if tol_rest is not None:
+            bound = tol_rest + 16 * EPS * (1 + np.nan_to_num(kap[chk], nan=np.inf))
+            assert np.all(rel <= bound), (name, (rel > bound).sum(), rel[rel > bound].max())
