@@ -105,28 +105,26 @@ __device__ __forceinline__ double exp64(double v) {
 
 // FP64 erfcx(z) = exp(z^2) erfc(z).  FP64 is the scarce unit of this GPU, and
 // the solvers evaluate erfcx more often than any other FP64 function, so it
-// is not the general library routine: for 0 <= z < 128 a degree-10 piecewise
-// Chebyshev interpolant (fv_fp64_tables.h, 68 pieces located from the bits of
-// z, within one ulp); beyond, the asymptotic series (Abramowitz & Stegun
+// is not the general library routine: for 0 <= z < 128 a degree-8 piecewise
+// Chebyshev interpolant (fv_fp64_tables.h, 136 pieces located from the bits of
+// z, within 1.2 ulp); beyond, the asymptotic series (Abramowitz & Stegun
 // 7.1.23) to the term in z^-8, whose first omitted term is below 2^-55 there.
 __device__ __forceinline__ double erfcx_nonneg(double z) {
   if (z < FV_ERFCX_TABLE_END) {
     int k;
     if (z < 0.5) {
-      k = __double2int_rz(z * 8.0);  // exact scaling: k in 0..3
+      k = __double2int_rz(z * 16.0);  // exact scaling: k in 0..7
     } else {
-      // binade 2^e, e = -1..6, and the top three fraction bits: k in 4..67
+      // binade 2^e, e = -1..6, and the top four fraction bits: k in 8..135
       const int hi = __double2hiint(z);
-      k = 4 + (((hi >> 20) - 1022) << 3) + ((hi >> 17) & 7);
+      k = 8 + (((hi >> 20) - 1022) << 4) + ((hi >> 16) & 15);
     }
-    // row k: centre, then the coefficients of v^0 .. v^10
+    // row k: centre, then the coefficients of v^0 .. v^8
     const double2* c = reinterpret_cast<const double2*>(kErfcxTable + k * FV_ERFCX_STRIDE);
     const double2 c0 = __ldg(c), c1 = __ldg(c + 1), c2 = __ldg(c + 2), c3 = __ldg(c + 3),
-                  c4 = __ldg(c + 4), c5 = __ldg(c + 5);
+                  c4 = __ldg(c + 4);
     const double v = z - c0.x;  // exact
-    double p = fma(c5.y, v, c5.x);
-    p = fma(p, v, c4.y);
-    p = fma(p, v, c4.x);
+    double p = fma(c4.y, v, c4.x);
     p = fma(p, v, c3.y);
     p = fma(p, v, c3.x);
     p = fma(p, v, c2.y);

@@ -13,13 +13,13 @@ Theory and Approximation Practice, ch. 4) on short pieces, the piecewise
 scheme of S. G. Johnson's Faddeeva package, with pieces laid out so that the
 piece index comes from the bits of z:
 
-  piece k = 0..3:    [k/8, (k+1)/8)                (uniform below 1/2)
-  piece 4 + 8e' + j: [2^e (1 + j/8), 2^e (1 + (j+1)/8)),  e = e' - 1 = -1..6
+  piece k = 0..7:     [k/16, (k+1)/16)                  (uniform below 1/2)
+  piece 8 + 16e' + j: [2^e (1 + j/16), 2^e (1 + (j+1)/16)),  e = e' - 1 = -1..6
 
-Each piece stores its centre c and the degree-10 polynomial in v = z - c that
-interpolates erfcx at the 11 Chebyshev points of the piece.  v is exact where
+Each piece stores its centre c and the degree-8 polynomial in v = z - c that
+interpolates erfcx at the 9 Chebyshev points of the piece.  v is exact where
 z and c lie within a factor of two of each other (Sterbenz), which is every
-piece but the first below z = 1/32; there its rounding error is below 2^-58.
+piece but the first below z = 1/64; there its rounding error is below 2^-59.
 Beyond z = 128 the kernels use the asymptotic series (Abramowitz & Stegun
 7.1.23) instead.
 
@@ -53,10 +53,10 @@ import mpmath as mp
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "fv_fp64_tables.h")
 
-DEGREE = 10
-STRIDE = 16         # doubles per erfcx piece: centre + 11 coefficients + padding (128 bytes)
-UNIFORM = 4         # pieces of width 1/8 on [0, 1/2)
-SUB = 8             # pieces per binade on [1/2, 128)
+DEGREE = 8
+STRIDE = 10         # doubles per erfcx piece: centre + 9 coefficients (80 bytes, five 16-byte loads)
+UNIFORM = 8         # pieces of width 1/16 on [0, 1/2)
+SUB = 16            # pieces per binade on [1/2, 128)
 BINADES = range(-1, 7)
 Z_TABLE_END = 128.0
 
@@ -72,7 +72,7 @@ def erfcx(z):
 
 
 def pieces():
-    out = [(mp.mpf(k) / 8, mp.mpf(k + 1) / 8) for k in range(UNIFORM)]
+    out = [(mp.mpf(k) / (2 * UNIFORM), mp.mpf(k + 1) / (2 * UNIFORM)) for k in range(UNIFORM)]
     for e in BINADES:
         for j in range(SUB):
             a = mp.mpf(2) ** e * (1 + mp.mpf(j) / SUB)
@@ -162,8 +162,9 @@ def write(table, out=OUT):
         "",
         "// erfcx: piecewise Chebyshev interpolants on 0 <= z < %g; piece k holds its" % Z_TABLE_END,
         "// centre c_k and the degree-%d polynomial in v = z - c_k (lowest order first)," % DEGREE,
-        "// padded to %d doubles (%d bytes) per piece." % (STRIDE, STRIDE * 8),
+        "// %d doubles (%d bytes) per piece." % (STRIDE, STRIDE * 8),
         "#define FV_ERFCX_PIECES %d" % len(table),
+        "#define FV_ERFCX_DEGREE %d" % DEGREE,
         "#define FV_ERFCX_STRIDE %d" % STRIDE,
         "#define FV_ERFCX_TABLE_END %.1f" % Z_TABLE_END,
         "static __device__ __align__(128) const double kErfcxTable[FV_ERFCX_PIECES * FV_ERFCX_STRIDE] = {",

@@ -105,9 +105,9 @@ def _exp64(v, tab):
 
 def _piece(z):
     if z < 0.5:
-        return int(z * 8.0)
+        return int(z * 16.0)
     hi = struct.unpack("<q", struct.pack("<d", z))[0] >> 32
-    return 4 + (((hi >> 20) - 1022) << 3) + ((hi >> 17) & 7)
+    return 8 + (((hi >> 20) - 1022) << 4) + ((hi >> 16) & 15)
 
 
 def _fma(x, y, z):
@@ -115,10 +115,10 @@ def _fma(x, y, z):
 
 
 def _eval(tab, z):
-    row = tab[_piece(z)]
+    row = tab[_piece(z)]  # centre, then the coefficients of v^0 .. v^8
     v = z - row[0]
-    p = row[11]
-    for j in range(10, 0, -1):
+    p = row[9]
+    for j in range(8, 0, -1):
         p = _fma(p, v, row[j])
     return p
 
@@ -129,13 +129,13 @@ def test_committed_table_is_the_generators_output(tmp_path):
     assert open(out).read() == open(HEADER).read()
 
 
-def test_table_within_one_ulp_of_erfcx():
+def test_table_within_one_and_a_quarter_ulp_of_erfcx():
     mp.mp.dps = 40
     tab = _table()
     g = np.random.default_rng(5)
     # random points in every piece, the piece edges and their neighbours
-    edges = [k / 8 for k in range(5)] + [2.0 ** e * (1 + j / 8) for e in range(-1, 7)
-                                         for j in range(8)]
+    edges = [k / 16 for k in range(9)] + [2.0 ** e * (1 + j / 16) for e in range(-1, 7)
+                                          for j in range(16)]
     z = np.concatenate([g.uniform(0, 0.5, 300), np.exp(g.uniform(np.log(0.5), np.log(128), 1200)),
                         edges, np.nextafter(edges, 0), np.nextafter(edges, 200), [0.0, 5e-324]])
     z = z[(z >= 0) & (z < 128)]
@@ -143,7 +143,8 @@ def test_table_within_one_ulp_of_erfcx():
     for zi in z:
         ref = mp.exp(mp.mpf(zi) ** 2) * mp.erfc(mp.mpf(zi))
         worst = max(worst, abs(float((_eval(tab, float(zi)) - ref) / ref)))
-    assert worst <= 2.0 ** -52, worst
+    # degree-8 interpolation error (up to ~0.6 ulp) plus the Horner rounding
+    assert worst <= 1.25 * 2.0 ** -52, worst
 
 
 def test_log_within_one_and_a_half_ulp():

@@ -84,8 +84,8 @@ def test_erfcx_against_binary128(fv, torch_dev):
     # reflection below zero; every piece edge and its neighbours included
     torch, dev = torch_dev
     g = np.random.default_rng(9)
-    edges = np.array([k / 8 for k in range(5)] + [2.0 ** e * (1 + j / 8) for e in range(-1, 7)
-                                                  for j in range(8)] + [128.0])
+    edges = np.array([k / 16 for k in range(9)] + [2.0 ** e * (1 + j / 16) for e in range(-1, 7)
+                                                   for j in range(16)] + [128.0])
     pos = np.concatenate([g.uniform(0, 0.5, 20000), np.exp(g.uniform(np.log(0.5), np.log(128), 50000)),
                           np.exp(g.uniform(np.log(128), np.log(1e300), 20000)), edges,
                           np.nextafter(edges, 0), np.nextafter(edges, np.inf), [0.0, 5e-324]])
