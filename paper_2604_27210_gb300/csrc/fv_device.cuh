@@ -151,33 +151,31 @@ __device__ __forceinline__ double erfcx64(double z) {
 }
 
 // FP64 natural logarithm, the table-driven method of P. T. P. Tang (ACM TOMS
-// 16(4), 1990): y = 2^m f with f in [1/sqrt2, sqrt2), F_j = 1 + j/128 the grid
+// 16(4), 1990): y = 2^m f with f in [1/sqrt2, sqrt2), F_j = 1 + j/256 the grid
 // point nearest f, r = f c_j - 1 (one rounding; c_j = 1/F_j in FP64, c_0 = 1),
 //   ln y = (m ln2_hi + L_hi[j]) + (m ln2_lo + L_lo[j] + log1p(r))
 // with L_hi + L_lo = -ln(c_j) for the rounded c_j, the first sum exact (both
-// terms on a 2^-42 grid) and log1p(r), |r| <= 0.0056, its Taylor polynomial to
-// r^8 (truncation below 2^-60 relative).  Zero, negative, subnormal, infinite
+// terms on a 2^-42 grid) and log1p(r), |r| <= 0.0028, its Taylor polynomial to
+// r^6 (truncation below 2^-58 relative).  Zero, negative, subnormal, infinite
 // and NaN arguments take the library routine.
 __device__ __forceinline__ double log64(double y) {
   if (!(y >= 2.2250738585072014e-308 && y <= 1.7976931348623157e308)) return log(y);
   const int hi = __double2hiint(y), lo = __double2loint(y);
   const int mant = hi & 0xfffff;
   int m = (hi >> 20) - 1023, j, ehi;
-  if (mant >= 0x6a09e) {  // f >= sqrt2: take f/2 in [1/sqrt2, 1), j in -37..0
+  if (mant >= 0x6a09e) {  // f >= sqrt2: take f/2 in [1/sqrt2, 1), j in -75..0
     m += 1;
-    j = ((mant + (1 << 13)) >> 14) - 64;
+    j = ((mant + (1 << 12)) >> 13) - 128;
     ehi = 0x3fe00000;
-  } else {                // f in [1, sqrt2), j in 0..53
-    j = (mant + (1 << 12)) >> 13;
+  } else {                // f in [1, sqrt2), j in 0..106
+    j = (mant + (1 << 11)) >> 12;
     ehi = 0x3ff00000;
   }
   const double f = __hiloint2double(ehi | mant, lo);
   const double2* t = reinterpret_cast<const double2*>(kLogTable + (j - FV_LOG_J0) * 4);
   const double2 t0 = __ldg(t), t1 = __ldg(t + 1);  // (c_j, L_hi), (L_lo, pad)
   const double r = fma(f, t0.x, -1.0);
-  double q = fma(r, -0.125, 1.0 / 7.0);
-  q = fma(q, r, -1.0 / 6.0);
-  q = fma(q, r, 0.2);
+  double q = fma(r, -1.0 / 6.0, 0.2);
   q = fma(q, r, -0.25);
   q = fma(q, r, 1.0 / 3.0);
   q = fma(q, r, -0.5);
@@ -220,9 +218,20 @@ struct Norm {
 
 // ln(F/K): near the money F - K is exact (Sterbenz) and log1p keeps x accurate
 // relative to itself; log(F/K) would carry one ulp of 1 in absolute error.
+// K/2 <= SF <= 2K for positive finite SF, K, on the bit patterns where K's
+// exponent field is neither the lowest two nor the highest: there the integer
+// order of positive doubles is their numeric order and K/2, 2K differ from K
+// by one in the exponent field.
+__device__ __forceinline__ bool within_factor_two(double SF, double K) {
+  const long long bs = __double_as_longlong(SF), bk = __double_as_longlong(K);
+  const long long one = 1LL << 52;
+  if (bk >= 2 * one && bk < 0x7fe0000000000000LL) return bs >= bk - one && bs <= bk + one;
+  return SF >= 0.5 * K && SF <= 2.0 * K;
+}
+
 __device__ __forceinline__ double log_moneyness(double SF, double K) {
-  return (SF >= 0.5 * K && SF <= 2.0 * K) ? log1p(__ddiv_rn(__dsub_rn(SF, K), K))
-                                          : log64(__ddiv_rn(SF, K));
+  return within_factor_two(SF, K) ? log1p(__ddiv_rn(__dsub_rn(SF, K), K))
+                                  : log64(__ddiv_rn(SF, K));
 }
 
 // finiteness tests on the bit pattern (integer unit, not the FP64 pipe)

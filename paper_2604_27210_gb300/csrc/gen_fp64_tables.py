@@ -24,13 +24,13 @@ Beyond z = 128 the kernels use the asymptotic series (Abramowitz & Stegun
 7.1.23) instead.
 
 log: the table-driven method of P. T. P. Tang (ACM TOMS 16(4), 1990).  With
-y = 2^m f, f in [1/sqrt2, sqrt2), and F_j = 1 + j/128 the grid point nearest
-f (j = -37..53), the kernels form r = f c_j - 1 with one fused multiply-add,
+y = 2^m f, f in [1/sqrt2, sqrt2), and F_j = 1 + j/256 the grid point nearest
+f (j = -75..106), the kernels form r = f c_j - 1 with one fused multiply-add,
 c_j = 1/F_j rounded to FP64, and return
     (m ln2_hi + L_hi[j]) + (m ln2_lo + L_lo[j] + log1p(r)),
 where L_j = -ln(c_j) for the rounded c_j (so the rounding of c_j costs
 nothing), split so that m ln2_hi + L_hi[j] is exact (both on a 2^-42 grid),
-and log1p(r), |r| <= 0.0056, is its Taylor polynomial to r^8.  c_0 = 1, so
+and log1p(r), |r| <= 0.0028, is its Taylor polynomial to r^6.  c_0 = 1, so
 next to y = 1 the result is log1p(y - 1) with y - 1 exact.
 
 exp: the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989).  With
@@ -60,7 +60,7 @@ SUB = 16            # pieces per binade on [1/2, 128)
 BINADES = range(-1, 7)
 Z_TABLE_END = 128.0
 
-LOG_J = range(-37, 54)   # F_j = 1 + j/128 covers [1/sqrt2, sqrt2)
+LOG_J = range(-75, 107)  # F_j = 1 + j/256 covers [1/sqrt2, sqrt2)
 EXP_N = 64
 LOG_GRID = 2.0 ** -42    # m ln2_hi and L_hi are multiples of this
 
@@ -132,7 +132,7 @@ def log_table():
     ln2_lo = float(ln2 - ln2_hi)
     rows = []
     for j in LOG_J:
-        c = 1.0 if j == 0 else float(1 / (1 + mp.mpf(j) / 128))
+        c = 1.0 if j == 0 else float(1 / (1 + mp.mpf(j) / 256))
         L = -mp.log(mp.mpf(c))
         L_hi = on_grid(L)
         rows.append((c, L_hi, float(L - L_hi)))
@@ -175,7 +175,7 @@ def write(table, out=OUT):
     lines += [
         "};",
         "",
-        "// log: row j + %d holds c_j = 1/(1 + j/128) (rounded; c_0 = 1), L_hi[j] and" % -LOG_J[0],
+        "// log: row j + %d holds c_j = 1/(1 + j/256) (rounded; c_0 = 1), L_hi[j] and" % -LOG_J[0],
         "// L_lo[j] with L_hi + L_lo = -ln(c_j), L_hi and ln2_hi on a 2^-42 grid, and a pad.",
         "#define FV_LOG_J0 %d" % LOG_J[0],
         "#define FV_LOG_ROWS %d" % len(lrows),

@@ -59,16 +59,16 @@ def _log64(y, tab):
     m = (hi >> 20) - 1023
     if mant >= 0x6a09e:
         m += 1
-        j = ((mant + (1 << 13)) >> 14) - 64
+        j = ((mant + (1 << 12)) >> 13) - 128
         ehi = 0x3fe00000
     else:
-        j = (mant + (1 << 12)) >> 13
+        j = (mant + (1 << 11)) >> 12
         ehi = 0x3ff00000
     f = struct.unpack("<d", struct.pack("<q", ((ehi | mant) << 32) | lo))[0]
     c, L_hi, L_lo, _ = rows[j - j0]
     r = _fma(f, c, -1.0)
-    q = _fma(r, -0.125, 1.0 / 7.0)
-    for k in (-1.0 / 6.0, 0.2, -0.25, 1.0 / 3.0, -0.5):
+    q = _fma(r, -1.0 / 6.0, 0.2)
+    for k in (-0.25, 1.0 / 3.0, -0.5):
         q = _fma(q, r, k)
     p = _fma(r * r, q, r)
     md = float(m)
