@@ -81,26 +81,25 @@ struct Prec<float> {
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
 // FP64 exponential, the table-driven method of P. T. P. Tang (ACM TOMS
-// 15(2), 1989): k = round(v 64/ln2), r = v - k ln2/64 (36-bit head, exact
-// product), j = k mod 64, m = floor(k/64),
+// 15(2), 1989): k = round(v 128/ln2), r = v - k ln2/128 (35-bit head, exact
+// product), j = k mod 128, m = floor(k/128),
 //   exp(v) = 2^m (T_hi[j] + (T_hi[j] expm1(r) + T_lo[j])),
-// T_hi + T_lo = 2^(j/64), expm1(r) to r^6 for |r| <= ln2/128.  Arguments whose
+// T_hi + T_lo = 2^(j/128), expm1(r) to r^5 for |r| <= ln2/256.  Arguments whose
 // result is subnormal, infinite or NaN take the library routine; below
 // -745.2 the result is 0.
 __device__ __forceinline__ double exp64(double v) {
   if (!(v > -708.3 && v < 709.7)) return v < -745.2 ? 0.0 : exp(v);
-  const double t = fma(v, FV_EXP_INV_LN2_64, 6755399441055744.0);  // 1.5 * 2^52: round to integer
+  const double t = fma(v, FV_EXP_INV_LN2_N, 6755399441055744.0);  // 1.5 * 2^52: round to integer
   const int k = __double2loint(t);
   const double kd = t - 6755399441055744.0;
-  double r = fma(kd, -FV_EXP_LN2_64_HI, v);
-  r = fma(kd, -FV_EXP_LN2_64_LO, r);
-  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  q = fma(q, r, 1.0 / 24.0);
+  double r = fma(kd, -FV_EXP_LN2_N_HI, v);
+  r = fma(kd, -FV_EXP_LN2_N_LO, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
   q = fma(q, r, 1.0 / 6.0);
   q = fma(q, r, 0.5);
   const double p = fma(r * r, q, r);  // expm1(r)
-  const double2 tj = __ldg(reinterpret_cast<const double2*>(kExpTable) + (k & 63));
-  return (tj.x + fma(tj.x, p, tj.y)) * __hiloint2double(((k >> 6) + 1023) << 20, 0);
+  const double2 tj = __ldg(reinterpret_cast<const double2*>(kExpTable) + (k & (FV_EXP_N - 1)));
+  return (tj.x + fma(tj.x, p, tj.y)) * __hiloint2double(((k >> 7) + 1023) << 20, 0);
 }
 
 // FP64 erfcx(z) = exp(z^2) erfc(z).  FP64 is the scarce unit of this GPU, and
@@ -280,13 +279,18 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   beta = __ddiv_rn(__dmul_rn(P, exp64(rate)), sqrt(__dmul_rn(SF, K)));
   // beta of a price near the bottom of the FP64 range has lost digits to
   // subnormal rounding; its logarithm is taken from P directly
-  o.ln_beta = (beta < 1e-280 && P > 0.0) ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K)) : 0.0;
+  // (beta < 1e-280 and P > 0 on the bit patterns: beta and P are finite here)
+  o.ln_beta = (__double_as_longlong(beta) < __double_as_longlong(1e-280) && __double_as_longlong(P) > 0)
+                  ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K))
+                  : 0.0;
   if (!bits_finite(x) || !bits_finite(beta)) return o;
   // Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 (from expm1,
   // accurate near the money) an in-the-money quote's intrinsic value is
   // e^{|x|/2} - e^{-|x|/2} = -E (1 + Em) / Em, accurate for every x
   const double Em = exp64(-0.5 * fabs(x));
-  const bool itm = flag > 0 ? x > 0.0 : x < 0.0;
+  // in the money: x > 0 for a call, x < 0 for a put (sign tests on the bits)
+  const long long bx = __double_as_longlong(x);
+  const bool itm = flag > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL);
   double iota = 0.0;
   if (itm) {
     const double E = expm1(-0.5 * fabs(x));

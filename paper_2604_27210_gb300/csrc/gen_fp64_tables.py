@@ -34,11 +34,11 @@ and log1p(r), |r| <= 0.0028, is its Taylor polynomial to r^6.  c_0 = 1, so
 next to y = 1 the result is log1p(y - 1) with y - 1 exact.
 
 exp: the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989).  With
-k = round(v 64/ln2), r = v - k ln2/64 (ln2/64 split into a 36-bit head, so
-k ln2_64_hi is exact, and a tail) and j = k mod 64, m = floor(k/64):
+k = round(v 128/ln2), r = v - k ln2/128 (ln2/128 split into a 35-bit head, so
+k ln2_128_hi is exact, and a tail) and j = k mod 128, m = floor(k/128):
     exp(v) = 2^m (T_hi[j] + (T_hi[j] expm1(r) + T_lo[j])),
-T_hi + T_lo = 2^(j/64) to 2^-106 and expm1(r), |r| <= ln2/128, its Taylor
-polynomial to r^6.
+T_hi + T_lo = 2^(j/128) to 2^-106 and expm1(r), |r| <= ln2/256, its Taylor
+polynomial to r^5.
 
 Run:  python gen_fp64_tables.py [samples per piece]
 (needs mpmath; prints the worst error of the FP64 erfcx Horner evaluation,
@@ -61,7 +61,7 @@ BINADES = range(-1, 7)
 Z_TABLE_END = 128.0
 
 LOG_J = range(-75, 107)  # F_j = 1 + j/256 covers [1/sqrt2, sqrt2)
-EXP_N = 64
+EXP_N = 128
 LOG_GRID = 2.0 ** -42    # m ln2_hi and L_hi are multiples of this
 
 mp.mp.dps = 50
@@ -142,7 +142,7 @@ def log_table():
 def exp_table():
     ln2_64 = mp.log(2) / EXP_N
     e = int(mp.floor(mp.log(ln2_64, 2)))
-    q = mp.mpf(2) ** (e - 35)               # 36 significant bits
+    q = mp.mpf(2) ** (e - 34)               # 35 significant bits
     hi = float(mp.nint(ln2_64 / q) * q)
     lo = float(ln2_64 - hi)
     rows = []
@@ -188,11 +188,12 @@ def write(table, out=OUT):
     lines += [
         "};",
         "",
-        "// exp: row j holds T_hi[j], T_lo[j] with T_hi + T_lo = 2^(j/64); ln2/64 = LN2_64_HI +",
-        "// LN2_64_LO with a 36-bit head.",
-        "#define FV_EXP_INV_LN2_64 %r" % inv,
-        "#define FV_EXP_LN2_64_HI %r" % e_hi,
-        "#define FV_EXP_LN2_64_LO %r" % e_lo,
+        "// exp: row j holds T_hi[j], T_lo[j] with T_hi + T_lo = 2^(j/128); ln2/128 = LN2_N_HI +",
+        "// LN2_N_LO with a 35-bit head.",
+        "#define FV_EXP_N %d" % EXP_N,
+        "#define FV_EXP_INV_LN2_N %r" % inv,
+        "#define FV_EXP_LN2_N_HI %r" % e_hi,
+        "#define FV_EXP_LN2_N_LO %r" % e_lo,
         "static __device__ __align__(16) const double kExpTable[%d * 2] = {" % EXP_N,
     ]
     for hi, lo in erows:

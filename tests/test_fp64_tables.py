@@ -77,9 +77,9 @@ def _log64(y, tab):
 
 def _exp_table():
     src = open(HEADER).read()
-    inv = float(re.search(r"#define FV_EXP_INV_LN2_64 (\S+)", src).group(1))
-    hi = float(re.search(r"#define FV_EXP_LN2_64_HI (\S+)", src).group(1))
-    lo = float(re.search(r"#define FV_EXP_LN2_64_LO (\S+)", src).group(1))
+    inv = float(re.search(r"#define FV_EXP_INV_LN2_N (\S+)", src).group(1))
+    hi = float(re.search(r"#define FV_EXP_LN2_N_HI (\S+)", src).group(1))
+    lo = float(re.search(r"#define FV_EXP_LN2_N_LO (\S+)", src).group(1))
     body = src[src.index("kExpTable"):]
     body = body[body.index("{") + 1:body.index("};")]
     vals = [float(v) for v in body.replace("\n", " ").split(",") if v.strip()]
@@ -95,12 +95,12 @@ def _exp64(v, tab):
     kd = t - big
     r = _fma(kd, -hi, v)
     r = _fma(kd, -lo, r)
-    q = _fma(r, 1.0 / 720.0, 1.0 / 120.0)
-    for c in (1.0 / 24.0, 1.0 / 6.0, 0.5):
+    q = _fma(r, 1.0 / 120.0, 1.0 / 24.0)
+    for c in (1.0 / 6.0, 0.5):
         q = _fma(q, r, c)
     p = _fma(r * r, q, r)
-    t_hi, t_lo = rows[k & 63]
-    return (t_hi + _fma(t_hi, p, t_lo)) * 2.0 ** (k >> 6)
+    t_hi, t_lo = rows[k & 127]
+    return (t_hi + _fma(t_hi, p, t_lo)) * 2.0 ** (k >> 7)
 
 
 def _piece(z):
@@ -170,9 +170,9 @@ def test_log_within_one_and_a_half_ulp():
 def test_exp_within_one_ulp():
     mp.mp.dps = 40
     tab = _exp_table()
-    # the split head of ln2/64 has 36 significant bits: k ln2_64_hi is exact for |k| < 2^17
+    # the split head of ln2/128 has 35 significant bits: k ln2_128_hi is exact for |k| < 2^18
     hi = tab[1]
-    assert (int(hi * 2 ** 42) == hi * 2 ** 42) and abs(int(hi * 2 ** 42)) < 2 ** 36
+    assert (int(hi * 2 ** 42) == hi * 2 ** 42) and abs(int(hi * 2 ** 42)) < 2 ** 35
     g = np.random.default_rng(7)
     v = np.concatenate([g.uniform(-708.3, 709.7, 2000), g.uniform(-1e-3, 1e-3, 500),
                         g.uniform(-1, 1, 500), [0.0, 1.0, -1.0, 709.69, -708.29]])
