@@ -44,20 +44,38 @@ def _np(t):
     return t.cpu().numpy()
 
 
+class _Conditioning(np.ndarray):
+    """kappa per quote, carrying `amb`: the quotes whose status quantities lie
+    within 16 ulp of a threshold of the FP64 status rule."""
+
+
 def _iv_ref(w, model=None):
     model = w["model"] if model is None else model
     f = lambda k: None if w.get(k) is None else np.asarray(w[k], dtype=np.float64)
     sig, st = orc.iv(model, f("P"), f("S_or_F"), f("K"), f("T"), f("r"), f("q"), w["flag"])
     v, kap = orc.conditioning(model, f("P"), f("S_or_F"), f("K"), f("T"), f("r"), f("q"),
                               w["flag"], sig)
+    margin = orc.status(model, f("P"), f("S_or_F"), f("K"), f("T"), f("r"), f("q"), w["flag"])[3]
+    kap = kap.view(_Conditioning)
+    kap.amb = margin <= 16.0
     return sig, st, v, kap
 
 
 def _check_sigma(got, ref, st, v, kap, tol_gate=1e-12, tol_rest=None, name=""):
+    # A quote whose price exceeds its intrinsic value by 64 ulp of it (the
+    # status rule's at-intrinsic threshold) to within a few ulp may take
+    # sigma = 0 on one side and a positive sigma on the other: the kernels' and
+    # the oracle's libm differ in the last place.  Those quotes (and any other
+    # within 16 ulp of a threshold) need only a finite sigma >= 0.
+    amb = getattr(kap, "amb", np.zeros(got.shape, bool))
+    assert amb.mean() <= 1e-3, "%s: %d ambiguous quotes" % (name, amb.sum())
+    okq = st == orc.OK
+    assert np.all(np.isfinite(got[okq & amb]) & (got[okq & amb] >= 0)), name
+    st = np.where(amb & okq, 255, st)  # leave them out below
     solved = (st == orc.OK) & (ref > 0)
     # quotes at intrinsic and failures: exact values
     assert np.all(got[(st == orc.OK) & (ref == 0)] == 0.0), name
-    assert np.all(np.isnan(got[st != orc.OK])), name
+    assert np.all(np.isnan(got[(st != orc.OK) & (st != 255)])), name
     assert np.all(np.isfinite(got[solved]) & (got[solved] > 0)), name
     rel = np.abs(got[solved] - ref[solved]) / ref[solved]
     gate = (v[solved] > 1e-8) & (kap[solved] <= 1e3)
@@ -142,6 +160,22 @@ def test_exp_against_extended_precision(fv, torch_dev):
                                                       dtype=torch.float64, device=dev)))
     assert sp[0] == 0 and sp[1] == pytest.approx(np.exp(-740.0), rel=1e-12) and sp[2] == np.inf
     assert sp[3] == np.inf and sp[4] == 0 and np.isnan(sp[5])
+
+
+def test_log1p_against_extended_precision(fv, torch_dev):
+    # log1p over its domain in the kernels, [-1/2, 1], against long double
+    torch, dev = torch_dev
+    g = np.random.default_rng(12)
+    u = np.concatenate([g.uniform(-0.5, 1.0, 100000), g.uniform(-1e-3, 1e-3, 20000),
+                        np.exp(g.uniform(-700, -7, 10000)), -np.exp(g.uniform(-700, -7, 10000)),
+                        [-0.5, 1.0, 0.0, 5e-324]])
+    got = _np(fv.fv_math(fv.FV_MATH_LOG1P, torch.tensor(u, device=dev)))
+    ref = np.log1p(u.astype(np.longdouble))
+    nz = ref != 0
+    rel = np.abs((got[nz] - ref[nz]) / ref[nz]).astype(np.float64)
+    # the table log (1.5 ulp) plus the c (2 - y) term (under one ulp at the ends)
+    assert rel.max() <= 2.5 * 2.0 ** -52, rel.max()
+    assert np.all(got[~nz] == 0)
 
 
 def test_normalised_black_against_binary128(fv, torch_dev):
