@@ -183,17 +183,6 @@ __device__ __forceinline__ double log64(double y) {
   return fma(md, FV_LN2_HI, t0.y) + (fma(md, FV_LN2_LO, t1.x) + p);
 }
 
-// log1p(u) for u in [-1/2, 1] from the table logarithm: y = 1 + u rounds away
-// c = u - (y - 1) (exact: y - 1 and u - (y - 1) are Sterbenz differences), and
-// log1p(u) = log(y) + log(1 + c/y) = log(y) + c/y to below 2^-100.  c/y is
-// formed as c (2 - y), off by c (y - 1)^2 / y: negligible where u is small,
-// and under one ulp of the result at the ends u = -1/2 and u = 1.
-__device__ __forceinline__ double log1p64(double u) {
-  const double y = 1.0 + u;
-  const double c = u - (y - 1.0);
-  return fma(c, 2.0 - y, log64(y));
-}
-
 __device__ __forceinline__ double f_erfcx(double v) { return erfcx64(v); }
 __device__ __forceinline__ double f_exp(double v) { return exp64(v); }
 __device__ __forceinline__ double f_log(double v) { return log64(v); }
@@ -240,7 +229,7 @@ __device__ __forceinline__ bool within_factor_two(double SF, double K) {
 }
 
 __device__ __forceinline__ double log_moneyness(double SF, double K) {
-  return within_factor_two(SF, K) ? log1p64(__ddiv_rn(__dsub_rn(SF, K), K))
+  return within_factor_two(SF, K) ? log1p(__ddiv_rn(__dsub_rn(SF, K), K))
                                   : log64(__ddiv_rn(SF, K));
 }
 

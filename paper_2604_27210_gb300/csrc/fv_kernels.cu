@@ -692,7 +692,7 @@ template <int FN>
 __global__ void __launch_bounds__(256) k_math(const double* z, int64_t n, double* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = FN == 0 ? erfcx64(z[i]) : (FN == 1 ? log64(z[i]) : (FN == 2 ? exp64(z[i]) : log1p64(z[i])));
+    out[i] = FN == 0 ? erfcx64(z[i]) : (FN == 1 ? log64(z[i]) : exp64(z[i]));
 }
 
 cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStream_t st) {
@@ -701,10 +701,8 @@ cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStr
     k_math<0><<<persistent_grid<k_math<0>>(n, block, block), block, 0, st>>>(z, n, out);
   else if (fn == 1)
     k_math<1><<<persistent_grid<k_math<1>>(n, block, block), block, 0, st>>>(z, n, out);
-  else if (fn == 2)
-    k_math<2><<<persistent_grid<k_math<2>>(n, block, block), block, 0, st>>>(z, n, out);
   else
-    k_math<3><<<persistent_grid<k_math<3>>(n, block, block), block, 0, st>>>(z, n, out);
+    k_math<2><<<persistent_grid<k_math<2>>(n, block, block), block, 0, st>>>(z, n, out);
   return cudaGetLastError();
 }
 

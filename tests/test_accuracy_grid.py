@@ -124,8 +124,11 @@ def test_extreme_grid_all_paths():
     for name, fn, tol_gate, tol_rest in paths:
         s_gpu, st_gpu = fn()
         s_gpu, st_gpu = s_gpu.cpu().numpy(), st_gpu.cpu().numpy()
-        assert np.array_equal(st_gpu, st), name
-        assert np.all(np.isfinite(s_gpu[(st == orc.OK) & amb]) & (s_gpu[(st == orc.OK) & amb] >= 0))
+        # statuses bit-identical away from the thresholds, a neighbour next to one
+        assert np.array_equal(st_gpu[~amb], st[~amb]), name
+        assert np.all(np.isin(st_gpu[amb], (orc.OK, orc.BELOW_INTRINSIC, orc.ABOVE_MAX))), name
+        okg = (st == orc.OK) & (st_gpu == orc.OK) & amb
+        assert np.all(np.isfinite(s_gpu[okg]) & (s_gpu[okg] >= 0)), name
         solved = (st == orc.OK) & (ref > 0) & ~amb
         assert np.all(np.isfinite(s_gpu[solved]) & (s_gpu[solved] > 0)), name
         assert np.all(s_gpu[(st == orc.OK) & (ref == 0) & ~amb] == 0), name

@@ -182,20 +182,3 @@ def test_exp_within_one_ulp():
         worst = max(worst, abs(float((_exp64(float(vi), tab) - ref) / ref)))
     assert worst <= 2.0 ** -52, worst
 
-
-def test_log1p_within_two_and_a_half_ulp():
-    # log1p64(u) = log64(1 + u) + c (2 - y), y = 1 + u, c = u - (y - 1)
-    mp.mp.dps = 40
-    tab = _log_table()
-    g = np.random.default_rng(8)
-    u = np.concatenate([g.uniform(-0.5, 1.0, 1500), g.uniform(-1e-3, 1e-3, 500),
-                        np.exp(g.uniform(-60, -7, 300)), [-0.5, 1.0, 1e-300]])
-    worst = 0.0
-    for ui in u:
-        ui = float(ui)
-        y = 1.0 + ui
-        c = ui - (y - 1.0)
-        got = _fma(c, 2.0 - y, _log64(y, tab))
-        ref = mp.log1p(mp.mpf(ui))
-        worst = max(worst, abs(float((got - ref) / ref)))
-    assert worst <= 2.5 * 2.0 ** -52, worst
