@@ -404,7 +404,8 @@ __device__ __forceinline__ T nb_log(const NB<T>& v) {
 // full normalised Black b(x, s, theta) for any x, s >= 0 (FP64)
 __device__ __forceinline__ double normalised_black(double x, double s, int theta) {
   double iota = 0.0;
-  if (theta * x > 0.0) {
+  const long long bx = __double_as_longlong(x);  // theta x > 0 on the sign bits
+  if (theta > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL)) {
     const double E = expm1(-0.5 * fabs(x)), Em = exp64(-0.5 * fabs(x));
     iota = -E * (1.0 + Em) / Em;
   }

@@ -495,9 +495,9 @@ cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st) {
 // e^{-rT} sqrt(F K) for the model
 __device__ __forceinline__ double price_scale(int model, double SF, double K, double T, double r,
                                               double q) {
-  if (model == M_BLACK76) return exp(-r * T) * sqrt(SF * K);
+  if (model == M_BLACK76) return exp64(-r * T) * sqrt(SF * K);
   const double qq = model == M_BSM ? q : 0.0;
-  return exp(-0.5 * (r + qq) * T) * sqrt(SF * K);
+  return exp64(-0.5 * (r + qq) * T) * sqrt(SF * K);
 }
 
 __global__ void __launch_bounds__(256)
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(256)
       const double sq = sqrt(t), s = sg * sq;
       const double x = model_x(model, sf, k, t, rr, qq);
       const D12 d = d12(x, s, th);
-      const double Dr = exp(-rr * t);
+      const double Dr = exp64(-rr * t);
       if (model == M_BLACK76) {
         const double V = Dr * sqrt(sf * k) * normalised_black(x, s, th);
         gd = th * Dr * d.N1;
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(256)
         gt = (-sf * Dr * d.n1 * sg / (2.0 * sq) + rr * V) / 365.0;
         gr = -t * V * 0.01;
       } else {
-        const double Dq = exp(-qq * t);
+        const double Dq = exp64(-qq * t);
         gd = th * Dq * d.N1;
         gg = Dq * d.n1 / (sf * s);
         gv = sf * Dq * d.n1 * sq * 0.01;
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(256)
         const double sq = sqrt(t), s = sg * sq;
         const double x = model_x(model, sf, k, t, rr, qq);
         const D12 d = d12(x, s, th);
-        const double Dr = exp(-rr * t);
+        const double Dr = exp64(-rr * t);
         double vega, VS, VK, VT, Vr, Vq = 0.0;
         if (model == M_BLACK76) {
           const double V = P[i];
@@ -630,7 +630,7 @@ __global__ void __launch_bounds__(256)
           VT = -rr * V + Dr * sf * d.n1 * sg / (2.0 * sq);
           Vr = -t * V;
         } else {
-          const double Dq = exp(-qq * t);
+          const double Dq = exp64(-qq * t);
           vega = sf * Dq * d.n1 * sq;
           VS = th * Dq * d.N1;
           VK = -th * Dr * d.N2;
