@@ -57,6 +57,22 @@ int persistent_grid(int64_t units, int units_per_block, int block) {
   return grid_for(units, units_per_block, resident[dev]);
 }
 
+// Below kSmallBatch quotes a launch is latency-bound (a warp's ~900
+// dependent FP64 instructions): the unbinned kernel with 64-thread blocks
+// spreads the quotes over as many SMs and sub-partitions as possible.
+constexpr int64_t kSmallBatch = 1 << 17;
+
+// Launch of a one-quote-per-thread grid-stride kernel over n quotes: a small
+// batch takes 64-thread blocks, one per 64 quotes, so that it reaches as many
+// SMs as it can fill; a large one a single resident wave of 256-thread blocks.
+template <auto Kernel, typename... Args>
+void launch_shaped(int64_t n, cudaStream_t st, Args... args) {
+  if (n < kSmallBatch)
+    Kernel<<<grid_for(n, 64, 32), 64, 0, st>>>(args...);
+  else
+    Kernel<<<persistent_grid<Kernel>(n, 256, 256), 256, 0, st>>>(args...);
+}
+
 template <typename InT>
 __device__ __forceinline__ double ld(const void* p, int64_t i) {
   return (double)__ldg(static_cast<const InT*>(p) + i);
@@ -263,10 +279,6 @@ static void launch_binned(const IvArgs& a, cudaStream_t st) {
 // iterations in phase 2, where they interleave with the FP64 correction
 // (10.9 ms; 1 or 2 quotes per thread at 3 to 5 blocks per SM within 1.2 %).
 // The FP32 path has no FP64 solve to sort for and stays unbinned.
-// Below kSmallBatch quotes a launch is latency-bound (a warp's ~900
-// dependent FP64 instructions): the unbinned kernel with 64-thread blocks
-// spreads the quotes over as many SMs and sub-partitions as possible.
-constexpr int64_t kSmallBatch = 1 << 17;
 
 template <typename InT, int PREC>
 static void launch_flat_prec(const IvArgs& a, int block, cudaStream_t st) {
@@ -458,16 +470,12 @@ cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st) {
   const HalleyWs w = halley_ws(ws, a.n);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  const int block = 256;
   if (a.f32_inputs) {
-    k_iv_halley32<float><<<persistent_grid<k_iv_halley32<float>>(a.n, block, block), block, 0, st>>>(a, w);
-    k_halley32_fallback<float>
-        <<<persistent_grid<k_halley32_fallback<float>>(a.n, block, block), block, 0, st>>>(a, w);
+    launch_shaped<k_iv_halley32<float>>(a.n, st, a, w);
+    launch_shaped<k_halley32_fallback<float>>(a.n, st, a, w);
   } else {
-    k_iv_halley32<double>
-        <<<persistent_grid<k_iv_halley32<double>>(a.n, block, block), block, 0, st>>>(a, w);
-    k_halley32_fallback<double>
-        <<<persistent_grid<k_halley32_fallback<double>>(a.n, block, block), block, 0, st>>>(a, w);
+    launch_shaped<k_iv_halley32<double>>(a.n, st, a, w);
+    launch_shaped<k_halley32_fallback<double>>(a.n, st, a, w);
   }
   return cudaGetLastError();
 }
@@ -476,15 +484,12 @@ cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st) {
   const HalleyWs w = halley_ws(ws, a.n);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  const int block = 256;
   if (a.f32_inputs) {
-    k_iv_halley<float><<<persistent_grid<k_iv_halley<float>>(a.n, block, block), block, 0, st>>>(a, w);
-    k_halley_fallback<float>
-        <<<persistent_grid<k_halley_fallback<float>>(a.n, block, block), block, 0, st>>>(a, w);
+    launch_shaped<k_iv_halley<float>>(a.n, st, a, w);
+    launch_shaped<k_halley_fallback<float>>(a.n, st, a, w);
   } else {
-    k_iv_halley<double><<<persistent_grid<k_iv_halley<double>>(a.n, block, block), block, 0, st>>>(a, w);
-    k_halley_fallback<double>
-        <<<persistent_grid<k_halley_fallback<double>>(a.n, block, block), block, 0, st>>>(a, w);
+    launch_shaped<k_iv_halley<double>>(a.n, st, a, w);
+    launch_shaped<k_halley_fallback<double>>(a.n, st, a, w);
   }
   return cudaGetLastError();
 }
@@ -520,8 +525,7 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const double* K,
                          const double* T, const double* r, const double* q, const double* sigma,
                          int64_t n, double* out, cudaStream_t st) {
-  const int block = 256;
-  k_price<<<persistent_grid<k_price>(n, block, block), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, out);
+  launch_shaped<k_price>(n, st, model, flag, SF, K, T, r, q, sigma, n, out);
   return cudaGetLastError();
 }
 
@@ -598,8 +602,7 @@ cudaError_t launch_greeks(int model, const int8_t* flag, const double* SF, const
                           const double* T, const double* r, const double* q, const double* sigma,
                           int64_t n, double* delta, double* gamma, double* vega, double* theta,
                           double* rho, cudaStream_t st) {
-  const int block = 256;
-  k_greeks<<<persistent_grid<k_greeks>(n, block, block), block, 0, st>>>(model, flag, SF, K, T, r, q, sigma, n, delta,
+  launch_shaped<k_greeks>(n, st, model, flag, SF, K, T, r, q, sigma, n, delta,
                                                      gamma, vega, theta, rho);
   return cudaGetLastError();
 }
@@ -664,8 +667,7 @@ cudaError_t launch_adjoint(int model, const double* P, const double* SF, const d
                            const double* sigma, const uint8_t* status, const double* gsig,
                            int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
                            double* gq, cudaStream_t st) {
-  const int block = 256;
-  k_adjoint<<<persistent_grid<k_adjoint>(n, block, block), block, 0, st>>>(model, P, SF, K, T, r, q, flag, sigma, status,
+  launch_shaped<k_adjoint>(n, st, model, P, SF, K, T, r, q, flag, sigma, status,
                                                       gsig, n, gP, gS, gK, gT, gr, gq);
   return cudaGetLastError();
 }
@@ -683,8 +685,7 @@ __global__ void __launch_bounds__(256) k_nb(const double* x, const double* s, co
 
 cudaError_t launch_normalised_black(const double* x, const double* s, const int8_t* theta,
                                     int64_t n, double* out, cudaStream_t st) {
-  const int block = 256;
-  k_nb<<<persistent_grid<k_nb>(n, block, block), block, 0, st>>>(x, s, theta, n, out);
+  launch_shaped<k_nb>(n, st, x, s, theta, n, out);
   return cudaGetLastError();
 }
 
@@ -696,13 +697,12 @@ __global__ void __launch_bounds__(256) k_math(const double* z, int64_t n, double
 }
 
 cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStream_t st) {
-  const int block = 256;
   if (fn == 0)
-    k_math<0><<<persistent_grid<k_math<0>>(n, block, block), block, 0, st>>>(z, n, out);
+    launch_shaped<k_math<0>>(n, st, z, n, out);
   else if (fn == 1)
-    k_math<1><<<persistent_grid<k_math<1>>(n, block, block), block, 0, st>>>(z, n, out);
+    launch_shaped<k_math<1>>(n, st, z, n, out);
   else
-    k_math<2><<<persistent_grid<k_math<2>>(n, block, block), block, 0, st>>>(z, n, out);
+    launch_shaped<k_math<2>>(n, st, z, n, out);
   return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@ kernels:   lbr, mixed, fp32, halley, halley32, price, greeks, adjoint, chains
 workloads: grid (BSM strike x maturity grid), b76 (Black-76 quotes),
            b76f32 (the same in FP32), bsm (BSM quotes with an upstream
            gradient), chains (option chains; --n is the number of chains)
-Inputs are priced by the library's own pricing kernel.
+Inputs are priced by the library's own pricing kernel.  --graph captures
+the call once in a CUDA graph and times its replays (launch overhead out).
 """
 import argparse
 import json
@@ -124,10 +125,22 @@ def chains_runner(fv, torch, w, t, mode):
     return (plan.run if mode == "graph" else plan.run_direct), plan, chains
 
 
-def time_it(torch, fn, reps, warmup):
+def time_it(torch, fn, reps, warmup, graph=False):
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        fn = g.replay
+        fn()
+        torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -147,6 +160,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--chains-mode", default="graph", choices=["graph", "direct", "separate", "flat"])
+    ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the call")
     args = ap.parse_args()
     import torch
     from paper_2604_27210_gb300 import fv
@@ -164,12 +178,14 @@ def main():
                     extra["plan"] = plan.info()
         else:
             fn = runner(fv, torch, args.kernel, w, t)
-        ms = time_it(torch, fn, args.reps, args.warmup)
+        ms = time_it(torch, fn, args.reps, args.warmup, graph=args.graph and args.kernel != "chains")
         line = {"kernel": args.kernel, "workload": args.workload, "n": n, "quotes": quotes,
                 "ms": ms, "quotes_per_s": quotes / (ms * 1e-3)}
         line.update(extra)
         if args.kernel == "chains":
             line["chains_mode"] = args.chains_mode
+        if args.graph and args.kernel != "chains":
+            line["graph"] = True
         print(json.dumps(line), flush=True)
         del t, fn
         torch.cuda.empty_cache()
