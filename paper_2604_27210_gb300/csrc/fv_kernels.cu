@@ -57,9 +57,10 @@ int persistent_grid(int64_t units, int units_per_block, int block) {
   return grid_for(units, units_per_block, resident[dev]);
 }
 
-// Below kSmallBatch quotes a launch is latency-bound (a warp's ~900
-// dependent FP64 instructions): the unbinned kernel with 64-thread blocks
-// spreads the quotes over as many SMs and sub-partitions as possible.
+// Below kSmallBatch quotes a launch is latency-bound (each warp runs one long
+// chain of dependent FP64 instructions): 64-thread blocks spread the quotes
+// over as many SMs and sub-partitions as possible, and the LBR solvers skip
+// the binning.
 constexpr int64_t kSmallBatch = 1 << 17;
 
 // Launch of a one-quote-per-thread grid-stride kernel over n quotes: a small
