@@ -75,12 +75,16 @@ fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const 
 
 /* Implied volatility (Section 3 "Implied volatility": fast_implied_volatility
  * for BSM quotes, fast_implied_volatility_black for discounted Black-76 mids;
- * Section 2.2 for the solvers).  FP64 inputs, FP64 arithmetic.
- *   FV_LBR:    normalised coordinates, four-region initial guess,
+ * Section 2.2 for the solvers).  FP64 inputs; the status decision, every
+ * residual and every Newton step in FP64.
+ *   FV_LBR:    normalised coordinates, four-region initial guess (built in
+ *              FP32: it is ~1e-2 off and only seeds the iteration),
  *              three-branch objective, Householder(3) iteration (two steps,
- *              plus a third wherever the second still moved sigma).
+ *              plus a third wherever the second still moved sigma; the
+ *              step's second-order correction factor in FP32).
  *   FV_HALLEY: Brenner-Subrahmanyam guess, eight Halley sweeps on the
- *              residual, bisection fallback on the quotes that fail the
+ *              residual, bisection with Newton steps on the LBR's
+ *              transformed residual for the quotes that fail the
  *              convergence test.  Uses a library-owned device workspace,
  *              allocated on the first call for a given size (make that first
  *              call before capturing the stream into a CUDA graph); use
