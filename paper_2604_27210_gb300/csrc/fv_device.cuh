@@ -744,10 +744,15 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
       break;
     }
     const double bp = v.e * kInvSqrt2Pi;
-    const double u = v.h * v.h * v.inv_s - 0.25 * s;
-    // Newton distance to the root relative to s: the convergence test
-    nerr = fabs(g / bp) / s;
-    const double step = -2.0 * g / (2.0 * bp - g * u);
+    // Newton step nu = g/b' and its distance to the root relative to s (the
+    // convergence test)
+    const double nu = g / bp;
+    nerr = fabs(nu) * v.inv_s;
+    // Halley: ds = -2 g g' / (2 g'^2 - g g'') = -nu / (1 - nu u / 2), u = b''/b';
+    // the factor 1 / (1 - nu u / 2) only shapes the step (its rounding enters at
+    // order nu^2), so it is formed in FP32
+    const float u = (float)(v.h * v.h) * (float)v.inv_s - 0.25f * (float)s;
+    const double step = -nu * (double)(1.0f / (1.0f - 0.5f * (float)nu * u));
     double sn = s + step;
     if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
     s = sn;
@@ -782,15 +787,15 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
     NB<double> v;
     nb_eval<double>(x, s, upper, v, false);
     const double L = nb_log(v);
-    const double qw = kInvSqrt2Pi / v.B;  // b'/b (lower) or b'/(b_max - b) (upper)
-    double f, fp;
+    // 1/f' = b/b' (lower: times ln^2 b) or (b_max - b)/b' = B sqrt(2 pi): no division
+    const double bq = v.B * kSqrt2Pi;
+    double f, inv_fp;
     if (upper) {
       f = ln_c_beta - L;
-      fp = qw;
+      inv_fp = bq;
     } else {
-      const double iL = 1.0 / L;
-      f = inv_ln_beta - iL;
-      fp = qw * iL * iL;
+      f = inv_ln_beta - 1.0 / L;
+      inv_fp = bq * L * L;
     }
     // a NaN residual comes from b underflowing at s far below the root
     if (f > 0.0)
@@ -799,7 +804,7 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
       lo = s;
     else
       break;
-    double sn = s - f / fp;
+    double sn = s - f * inv_fp;
     if (!isfinite(hi))
       sn = (isfinite(sn) && sn > s) ? fmin(sn, 16.0 * s) : 2.0 * s;
     else if (!(lo > 0.0))
