@@ -86,9 +86,11 @@ fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const 
  *              residual, bisection with Newton steps on the LBR's
  *              transformed residual for the quotes that fail the
  *              convergence test.  Uses a library-owned device workspace,
- *              allocated on the first call for a given size (make that first
- *              call before capturing the stream into a CUDA graph); use
- *              fv_implied_vol_ws to supply the workspace instead.
+ *              one per device, allocated on the first call for a given size
+ *              (make that first call before capturing the stream into a CUDA
+ *              graph).  Halley calls whose GPU work may overlap (on different
+ *              streams) must not share it: give each its own workspace
+ *              through fv_implied_vol_ws.
  * out_sigma: FP64, NaN where status != FV_Q_OK.  status: uint8 per quote. */
 fv_err fv_implied_vol(fv_model model, fv_solver solver, const double* price, const double* S_or_F,
                       const double* K, const double* T, const double* r, const double* q,
