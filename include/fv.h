@@ -185,12 +185,24 @@ fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta
  *   FV_MATH_LOG    ln z, the logarithm of the wing objectives (Section 2.2);
  *                  ln 0 = -inf, negative z gives NaN;
  *   FV_MATH_EXP    e^z, the exponential of every normalised-Black evaluation;
- *                  0 below z = -745.2, +inf above 709.78.
+ *                  0 below z = -745.2, +inf above 709.78;
+ *   FV_MATH_EXPM1  e^z - 1 from the same reduction as e^z (the status rule
+ *                  takes both for z = -|x|/2: bound and intrinsic value);
+ *                  -1 below z = -708.3, +inf above 709.78;
+ *   FV_MATH_LOG1P  ln(1 + z) as the logarithm of the exact sum 1 + z, the
+ *                  form the status rule gives x = ln(F/K) near the money;
+ *                  -inf at z = -1, NaN below.
  * The paper has no counterpart entry point: this exposes what the kernels
  * compute so that it can be checked on its own.  z, out: device arrays of n
  * doubles (caller-owned); NaN gives NaN.  Errors: unknown function, n < 0 or
  * a NULL pointer with n > 0 -> FV_ERR_ARG before any launch. */
-typedef enum { FV_MATH_ERFCX = 0, FV_MATH_LOG = 1, FV_MATH_EXP = 2 } fv_math_fn;
+typedef enum {
+  FV_MATH_ERFCX = 0,
+  FV_MATH_LOG = 1,
+  FV_MATH_EXP = 2,
+  FV_MATH_EXPM1 = 3,
+  FV_MATH_LOG1P = 4
+} fv_math_fn;
 fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* stream);
 
 /* ---- batches of option chains (one persistent launch) ------------------ */

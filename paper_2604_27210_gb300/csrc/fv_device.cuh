@@ -22,7 +22,9 @@
 // whose derivatives satisfy R' = 1 + h R, so R^{(n)} = P_n(h) + Q_n(h) R with
 // integer polynomials (P_{n+1} = P_n' + Q_n, Q_{n+1} = Q_n' + h Q_n).  The
 // series is the odd part of R(h+t) - R(h-t), i.e. the cancellation-free form
-// of the erfcx difference when t is small.
+// of the erfcx difference when t is small.  Past the inflection point
+// (h + t > 0) the value itself is b_max - e (b_max - b)/e: the complement
+// needs no reflected erfcx, hence no second exponential.
 //
 // Every lane of a warp calls the same special functions with lane-selected
 // arguments (region-selected coefficients instead of region branches), so the
@@ -102,6 +104,39 @@ __device__ __forceinline__ double exp64(double v) {
   return (tj.x + fma(tj.x, p, tj.y)) * __hiloint2double(((k >> 7) + 1023) << 20, 0);
 }
 
+// exp(v) and expm1(v) from one reduction of the method above (the polynomial
+// taken to r^6, so that expm1(r) = p holds to 2^-60 relative):
+//   expm1(v) = (2^m T_hi[j] - 1) + 2^m (T_hi[j] p + T_lo[j]).
+// 2^m T_hi - 1 is exact for m = 0, -1 (Sterbenz: 2^m T_hi in [1/2, 2)) and
+// otherwise below half an ulp of a result beyond 1/2 in magnitude; the second
+// term is at most 2^m T_hi ln2/256.  Below |v| = 1/200 the reduction is
+// skipped (k = 0, expm1 = p; the polynomial's truncation stays below 2^-60
+// there), so that the two terms never cancel by more than a factor ~1.3.
+// Within ~1 ulp for both.
+__device__ __forceinline__ double exp_expm1_64(double v, double& em1) {
+  if (!(v > -708.3 && v < 709.7)) {
+    em1 = v < 0.0 ? -1.0 : expm1(v);  // +inf, or NaN
+    return v < -745.2 ? 0.0 : exp(v);
+  }
+  const double t = fma(v, FV_EXP_INV_LN2_N, 6755399441055744.0);
+  const bool tiny = fabs(v) < 0.005;
+  const int k = tiny ? 0 : __double2loint(t);
+  const double kd = tiny ? 0.0 : t - 6755399441055744.0;
+  double r = fma(kd, -FV_EXP_LN2_N_HI, v);
+  r = fma(kd, -FV_EXP_LN2_N_LO, r);
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(r * r, q, r);
+  const double2 tj = __ldg(reinterpret_cast<const double2*>(kExpTable) + (k & (FV_EXP_N - 1)));
+  const double sc = __hiloint2double(((k >> 7) + 1023) << 20, 0);
+  const double th = tj.x * sc;  // exact: a power-of-two scaling of a normal number
+  const double tl = tj.y * sc;
+  em1 = (th - 1.0) + fma(th, p, tl);
+  return th + fma(th, p, tl);
+}
+
 // FP64 erfcx(z) = exp(z^2) erfc(z).  FP64 is the scarce unit of this GPU, and
 // the solvers evaluate erfcx more often than any other FP64 function, so it
 // is not the general library routine: for 0 <= z < 128 a degree-8 piecewise
@@ -156,8 +191,11 @@ __device__ __forceinline__ double erfcx64(double z) {
 // with L_hi + L_lo = -ln(c_j) for the rounded c_j, the first sum exact (both
 // terms on a 2^-42 grid) and log1p(r), |r| <= 0.0028, its Taylor polynomial to
 // r^6 (truncation below 2^-58 relative).  Zero, negative, subnormal, infinite
-// and NaN arguments take the library routine.
-__device__ __forceinline__ double log64(double y) {
+// and NaN arguments take the library routine.  With c (|c| below half an ulp
+// of y) the result is ln(y + c): c/y = 2^-m c / f enters r as 2^-m c c_j (its
+// relative error, |r| <= 0.0028, does not show).
+template <bool kWithC>
+__device__ __forceinline__ double log64_core(double y, double c) {
   if (!(y >= 2.2250738585072014e-308 && y <= 1.7976931348623157e308)) return log(y);
   const int hi = __double2hiint(y), lo = __double2loint(y);
   const int mant = hi & 0xfffff;
@@ -173,7 +211,8 @@ __device__ __forceinline__ double log64(double y) {
   const double f = __hiloint2double(ehi | mant, lo);
   const double2* t = reinterpret_cast<const double2*>(kLogTable + (j - FV_LOG_J0) * 4);
   const double2 t0 = __ldg(t), t1 = __ldg(t + 1);  // (c_j, L_hi), (L_lo, pad)
-  const double r = fma(f, t0.x, -1.0);
+  double r = fma(f, t0.x, -1.0);
+  if (kWithC) r = fma(__dmul_rn(c, __hiloint2double((1023 - m) << 20, 0)), t0.x, r);
   double q = fma(r, -1.0 / 6.0, 0.2);
   q = fma(q, r, -0.25);
   q = fma(q, r, 1.0 / 3.0);
@@ -181,6 +220,15 @@ __device__ __forceinline__ double log64(double y) {
   const double p = fma(r * r, q, r);  // log1p(r)
   const double md = (double)m;
   return fma(md, FV_LN2_HI, t0.y) + (fma(md, FV_LN2_LO, t1.x) + p);
+}
+__device__ __forceinline__ double log64(double y) { return log64_core<false>(y, 0.0); }
+__device__ __forceinline__ double log64(double y, double c) { return log64_core<true>(y, c); }
+
+// ln(1 + u) = ln(y + c), (y, c) the exact sum 1 + u (Knuth's TwoSum)
+__device__ __forceinline__ double log1p64(double u) {
+  const double y = 1.0 + u, bu = y - 1.0;
+  const double c = (1.0 - (y - bu)) + (u - bu);
+  return log64(y, c);
 }
 
 __device__ __forceinline__ double f_erfcx(double v) { return erfcx64(v); }
@@ -228,9 +276,14 @@ __device__ __forceinline__ bool within_factor_two(double SF, double K) {
   return SF >= 0.5 * K && SF <= 2.0 * K;
 }
 
+// One division and one logarithm for both cases: near the money
+// log1p(u) = ln(y + c) with y = 1 + u rounded and c = u - (y - 1) its exact
+// rounding error (|u| <= 1).
 __device__ __forceinline__ double log_moneyness(double SF, double K) {
-  return within_factor_two(SF, K) ? log1p(__ddiv_rn(__dsub_rn(SF, K), K))
-                                  : log64(__ddiv_rn(SF, K));
+  const bool near = within_factor_two(SF, K);
+  const double u = __ddiv_rn(near ? __dsub_rn(SF, K) : SF, K);
+  const double y = near ? __dadd_rn(1.0, u) : u;
+  return log64(y, near ? __dsub_rn(u, __dsub_rn(y, 1.0)) : 0.0);
 }
 
 // finiteness tests on the bit pattern (integer unit, not the FP64 pipe)
@@ -289,15 +342,13 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   // Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 (from expm1,
   // accurate near the money) an in-the-money quote's intrinsic value is
   // e^{|x|/2} - e^{-|x|/2} = -E (1 + Em) / Em, accurate for every x
-  const double Em = exp64(-0.5 * fabs(x));
+  double E;
+  const double Em = exp_expm1_64(-0.5 * fabs(x), E);
   // in the money: x > 0 for a call, x < 0 for a put (sign tests on the bits)
   const long long bx = __double_as_longlong(x);
   const bool itm = flag > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL);
   double iota = 0.0;
-  if (itm) {
-    const double E = expm1(-0.5 * fabs(x));
-    iota = __ddiv_rn(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em);
-  }
+  if (itm) iota = __ddiv_rn(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em);
   o.x = x;
   o.beta = beta;
   o.iota = iota;
@@ -326,6 +377,7 @@ template <typename T>
 struct NB {
   T e;      // exp(-(h^2+t^2)/2)
   T B;      // b/e (or (b_max - b)/e for the complement)
+  T b;      // b itself (value mode of nb_eval only)
   T h, t, inv_s;
 };
 
@@ -370,15 +422,26 @@ __device__ __forceinline__ T small_t_series(T h, T t, T R) {
 
 // b(x, s) for x <= 0 (or its complement b_max - b when comp), scaled by e.
 // with_e = false leaves o.e unset: the wing objectives use only B and ln b.
+//
+// Value mode (with_e, a bound bmax = e^{x/2} >= 0 passed in, not comp): o.b
+// is b itself.  Past the inflection point (h + t > 0) the erfcx form would
+// reflect a negative argument, erfcx(-a) = 2 exp(a^2) - erfcx(a), at the cost
+// of one more exponential; but e exp((h+t)^2/2) = e^{ht} = e^{x/2} = b_max, so
+// there b = b_max - e [erfcx((h+t)/sqrt2) + erfcx((t-h)/sqrt2)]/2 instead,
+// with the same error relative to b_max and no exponential (o.B then holds
+// the complement, (b_max - b)/e).
 template <typename T>
-__device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e) {
+__device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e,
+                                        T bmax = T(-1)) {
   o.inv_s = T(1) / s;
   o.h = x * o.inv_s;
   o.t = T(0.5) * s;
   const T h = o.h, t = o.t;
   o.e = with_e ? f_exp(T(-0.5) * (h * h + t * t)) : T(0);
   const bool small = (t < Prec<T>::t_small) && !comp;
-  const T a1 = small ? -h * T(kInvSqrt2) : (comp ? (h + t) : -(h + t)) * T(kInvSqrt2);
+  const bool via_comp = with_e && !comp && !small && bmax >= T(0) && h + t > T(0);
+  const T a1 = small ? -h * T(kInvSqrt2)
+                     : ((comp || via_comp) ? (h + t) : -(h + t)) * T(kInvSqrt2);
   const T Y1 = f_erfcx(a1);
   if (small) {
     if (f_abs(h) < Prec<T>::h_asym) {
@@ -391,8 +454,9 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
     }
   } else {
     const T Y2 = f_erfcx((t - h) * T(kInvSqrt2));
-    o.B = comp ? T(0.5) * (Y1 + Y2) : T(0.5) * (Y1 - Y2);
+    o.B = (comp || via_comp) ? T(0.5) * (Y1 + Y2) : T(0.5) * (Y1 - Y2);
   }
+  o.b = via_comp ? bmax - o.e * o.B : o.e * o.B;
 }
 
 // ln of the value nb_eval describes
@@ -403,16 +467,16 @@ __device__ __forceinline__ T nb_log(const NB<T>& v) {
 
 // full normalised Black b(x, s, theta) for any x, s >= 0 (FP64)
 __device__ __forceinline__ double normalised_black(double x, double s, int theta) {
+  double E;
+  const double Em = exp_expm1_64(-0.5 * fabs(x), E);  // e^{-|x|/2}, its expm1
   double iota = 0.0;
   const long long bx = __double_as_longlong(x);  // theta x > 0 on the sign bits
-  if (theta > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL)) {
-    const double E = expm1(-0.5 * fabs(x)), Em = exp64(-0.5 * fabs(x));
+  if (theta > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL))
     iota = -E * (1.0 + Em) / Em;
-  }
   if (!(s > 0.0)) return iota;
   NB<double> v;
-  nb_eval<double>(-fabs(x), s, false, v, true);
-  return iota + v.e * v.B;
+  nb_eval<double>(-fabs(x), s, false, v, true, Em);
+  return iota + v.b;
 }
 
 // ---------------------------------------------------------------------------
@@ -471,14 +535,14 @@ struct Objective {
 template <typename T>
 __device__ __forceinline__ Objective<T> objective(const Reduced<T>& q, T s, int reg) {
   NB<T> v;
-  nb_eval<T>(q.x, s, reg == 3, v, reg == 1 || reg == 2);
+  nb_eval<T>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax);
   const T hh = v.h * v.h;
   const T u = hh * v.inv_s - T(0.25) * s;                    // b''/b'
   const T du = T(-3) * hh * v.inv_s * v.inv_s - T(0.25);     // d(b''/b')/ds
   Objective<T> o;
   if (reg == 1 || reg == 2) {
-    const T b = v.e * v.B, bp = v.e * T(kInvSqrt2Pi);
-    o.nu = (q.beta - b) / bp;
+    const T bp = v.e * T(kInvSqrt2Pi);
+    o.nu = (q.beta - v.b) / bp;
     o.h2 = u;
     o.h3 = u * u + du;
   } else {
@@ -520,14 +584,24 @@ __device__ __forceinline__ T guarded(T s, T ds) {
 // once after its FP32 iterations.
 __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg) {
   NB<double> v;
-  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2);
+  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax);
   const float hh = (float)(v.h * v.h), is = (float)v.inv_s, sf = (float)s;
   const float u = hh * is - 0.25f * sf;
   const float du = -3.0f * hh * is * is - 0.25f;
   double nu;
   float h2, h3;
   if (reg == 1 || reg == 2) {
-    nu = (q.beta - v.e * v.B) / (v.e * kInvSqrt2Pi);
+    // nu = (beta - b) sqrt(2 pi) / e with 1/e from the FP32 reciprocal and one
+    // Newton step (relative error ~1e-14 in the step, which the next
+    // iteration or the convergence of nu to 0 makes invisible)
+    double ie;
+    if (v.e > 1e-30) {
+      ie = (double)__frcp_rn((float)v.e);
+      ie = fma(ie, fma(-v.e, ie, 1.0), ie);
+    } else {
+      ie = 1.0 / v.e;
+    }
+    nu = (q.beta - v.b) * (kSqrt2Pi * ie);
     h2 = u;
     h3 = u * u + du;
   } else {
@@ -536,9 +610,10 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
     const double bq = v.B * kSqrt2Pi;
     const float qf = 1.0f / (float)bq;
     if (reg == 0) {
-      const double iL = 1.0 / lnX;
-      nu = (iL - q.inv_ln_beta) * lnX * lnX * bq;
-      const float iLf = (float)iL, k1 = 1.0f + 2.0f * iLf;
+      // g = 1/ln b - 1/ln beta = (ln beta - ln b) / (ln b ln beta): the
+      // residual as a difference of logarithms, no FP64 division
+      nu = (q.ln_beta - lnX) * lnX * q.inv_ln_beta * bq;
+      const float iLf = 1.0f / (float)lnX, k1 = 1.0f + 2.0f * iLf;
       h2 = u - qf * k1;
       h3 = h2 * h2 + du - (qf * u - qf * qf) * k1 + 2.0f * qf * qf * iLf * iLf;
     } else {
@@ -586,8 +661,8 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
   const bool degenerate = !(so > T(0));  // s_l lost to rounding next to x = 0
   if (degenerate) so = sc > T(0) ? sc : T(1);
   NB<T> vo_;
-  nb_eval<T>(x, so, false, vo_, true);
-  const T bo = degenerate ? T(0) : vo_.e * vo_.B;
+  nb_eval<T>(x, so, false, vo_, true, bmax);
+  const T bo = degenerate ? T(0) : vo_.b;
   const T vo = vo_.e * T(kInvSqrt2Pi);
   // ln b_l, for the region test where b_l underflows the type and for the
   // lowest-region guess: an FP32 value is enough for both (a wrong side next
@@ -732,8 +807,8 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
   double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
   for (int k = 0; k < kHalleySteps; k++) {
     NB<double> v;
-    nb_eval<double>(x, s, upper, v, true);
-    const double g = upper ? c_beta - v.e * v.B : v.e * v.B - beta;
+    nb_eval<double>(x, s, upper, v, true, bmax);
+    const double g = upper ? c_beta - v.e * v.B : v.b - beta;
     if (g < 0.0) {
       lo = s;
     } else if (g > 0.0) {

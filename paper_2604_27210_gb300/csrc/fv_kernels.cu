@@ -693,17 +693,25 @@ cudaError_t launch_normalised_black(const double* x, const double* s, const int8
 template <int FN>
 __global__ void __launch_bounds__(256) k_math(const double* z, int64_t n, double* out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    out[i] = FN == 0 ? erfcx64(z[i]) : (FN == 1 ? log64(z[i]) : exp64(z[i]));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double em1;
+    const double v = z[i];
+    out[i] = FN == 0   ? erfcx64(v)
+             : FN == 1 ? log64(v)
+             : FN == 2 ? exp64(v)
+             : FN == 3 ? (exp_expm1_64(v, em1), em1)
+                       : log1p64(v);
+  }
 }
 
 cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStream_t st) {
-  if (fn == 0)
-    launch_shaped<k_math<0>>(n, st, z, n, out);
-  else if (fn == 1)
-    launch_shaped<k_math<1>>(n, st, z, n, out);
-  else
-    launch_shaped<k_math<2>>(n, st, z, n, out);
+  switch (fn) {
+    case 0: launch_shaped<k_math<0>>(n, st, z, n, out); break;
+    case 1: launch_shaped<k_math<1>>(n, st, z, n, out); break;
+    case 2: launch_shaped<k_math<2>>(n, st, z, n, out); break;
+    case 3: launch_shaped<k_math<3>>(n, st, z, n, out); break;
+    default: launch_shaped<k_math<4>>(n, st, z, n, out); break;
+  }
   return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
-"""The FP64 erfcx and log tables of the CUDA kernels, checked on the CPU.
+"""The FP64 erfcx, log and exp tables of the CUDA kernels, checked on the CPU.
 
 The kernels evaluate erfcx(z) = exp(z^2) erfc(z) on 0 <= z < 128 from
-piecewise Chebyshev interpolants and ln y by Tang's table-driven method
-(csrc/fv_fp64_tables.h, written by csrc/gen_fp64_tables.py).  Here the
+piecewise Chebyshev interpolants, and ln y, log1p, exp and expm1 by Tang's
+table-driven methods (csrc/fv_fp64_tables.h, written by
+csrc/gen_fp64_tables.py).  Here the
 committed header is what the generator writes, and each function, evaluated
 step by step the way the kernel does (table rows located from the bits of the
 argument, exactly rounded fused multiply-adds), is within its error bound of
@@ -50,8 +51,9 @@ def _log_table():
     return j0, ln2_hi, ln2_lo, np.array(vals).reshape(-1, 4)
 
 
-def _log64(y, tab):
-    """The kernel's log64 for a positive normal y, operation by operation."""
+def _log64(y, tab, corr=None):
+    """The kernel's log64 for a positive normal y, operation by operation;
+    with corr, ln(y + corr) (the correction enters r)."""
     j0, ln2_hi, ln2_lo, rows = tab
     bits = struct.unpack("<q", struct.pack("<d", y))[0]
     hi, lo = bits >> 32, bits & 0xffffffff
@@ -67,6 +69,8 @@ def _log64(y, tab):
     f = struct.unpack("<d", struct.pack("<q", ((ehi | mant) << 32) | lo))[0]
     c, L_hi, L_lo, _ = rows[j - j0]
     r = _fma(f, c, -1.0)
+    if corr is not None:
+        r = _fma(corr * 2.0 ** -m, c, r)
     q = _fma(r, -1.0 / 6.0, 0.2)
     for k in (-0.25, 1.0 / 3.0, -0.5):
         q = _fma(q, r, k)
@@ -101,6 +105,35 @@ def _exp64(v, tab):
     p = _fma(r * r, q, r)
     t_hi, t_lo = rows[k & 127]
     return (t_hi + _fma(t_hi, p, t_lo)) * 2.0 ** (k >> 7)
+
+
+def _exp_expm1(v, tab):
+    """The kernel's exp_expm1_64 for -708.3 < v < 709.7: (exp v, expm1 v)."""
+    inv, hi, lo, rows = tab
+    big = 6755399441055744.0
+    t = _fma(v, inv, big)
+    k = int(t - big)
+    kd = t - big
+    if abs(v) < 0.005:
+        k, kd = 0, 0.0
+    r = _fma(kd, -hi, v)
+    r = _fma(kd, -lo, r)
+    q = _fma(r, 1.0 / 720.0, 1.0 / 120.0)
+    for c in (1.0 / 24.0, 1.0 / 6.0, 0.5):
+        q = _fma(q, r, c)
+    p = _fma(r * r, q, r)
+    t_hi, t_lo = rows[k & 127]
+    sc = 2.0 ** (k >> 7)
+    th, tl = t_hi * sc, t_lo * sc
+    return th + _fma(th, p, tl), (th - 1.0) + _fma(th, p, tl)
+
+
+def _log1p_near(u, tab):
+    """x = ln(1 + u) as the status rule forms it near the money (|u| <= 1):
+    y = 1 + u rounded, its exact error c (Fast2Sum), then ln(y + c)."""
+    y = 1.0 + u
+    c = u - (y - 1.0)
+    return _log64(y, tab, corr=c)
 
 
 def _piece(z):
@@ -182,3 +215,47 @@ def test_exp_within_one_ulp():
         worst = max(worst, abs(float((_exp64(float(vi), tab) - ref) / ref)))
     assert worst <= 2.0 ** -52, worst
 
+
+
+def test_expm1_and_exp_from_one_reduction_within_one_ulp():
+    mp.mp.dps = 40
+    tab = _exp_table()
+    g = np.random.default_rng(8)
+    ln2_256 = float(np.log(2) / 256)
+    # the status rule's range (v = -|x|/2 <= 0) densely, the reduction's
+    # boundaries k = 0, +-1 and the binades m = -1, -2, and positive v
+    v = np.concatenate([-np.exp(g.uniform(np.log(1e-300), np.log(708), 2500)),
+                        g.uniform(-3 * ln2_256, 3 * ln2_256, 2000), g.uniform(-1.5, 1.5, 800),
+                        g.uniform(0.0, 709.6, 500), np.exp(g.uniform(-30, 0, 300)),
+                        [0.0, -0.0, ln2_256, -ln2_256, -np.log(2.0), -2 * np.log(2.0), -708.29]])
+    worst_e = worst_m = 0.0
+    for vi in v:
+        e, m1 = _exp_expm1(float(vi), tab)
+        x = mp.mpf(float(vi))
+        worst_e = max(worst_e, abs(float((e - mp.exp(x)) / mp.exp(x))))
+        if vi == 0:
+            assert m1 == 0.0
+            continue
+        worst_m = max(worst_m, abs(float((m1 - mp.expm1(x)) / mp.expm1(x))))
+    assert worst_e <= 2.0 ** -52, worst_e
+    # the first sum exact (m = 0, -1) or half an ulp of a result beyond 1/2,
+    # the second one small: about one ulp
+    assert worst_m <= 1.2 * 2.0 ** -52, worst_m
+
+
+def test_log1p_near_the_money_within_one_and_a_half_ulp():
+    mp.mp.dps = 40
+    tab = _log_table()
+    g = np.random.default_rng(9)
+    u = np.concatenate([g.uniform(-0.5, 1.0, 1500), np.exp(g.uniform(np.log(1e-300), 0, 800)),
+                        -np.exp(g.uniform(np.log(1e-300), np.log(0.5), 800)),
+                        g.uniform(-4.0 / 256, 4.0 / 256, 800), [0.0, -0.5, 1.0, 1.0 / 512, -1.0 / 512]])
+    worst = 0.0
+    for ui in u:
+        got = _log1p_near(float(ui), tab)
+        ref = mp.log1p(mp.mpf(float(ui)))
+        if ref == 0:
+            assert got == 0.0
+            continue
+        worst = max(worst, abs(float((got - ref) / ref)))
+    assert worst <= 1.5 * 2.0 ** -52, worst

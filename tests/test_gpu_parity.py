@@ -162,6 +162,39 @@ def test_exp_against_extended_precision(fv, torch_dev):
     assert sp[3] == np.inf and sp[4] == 0 and np.isnan(sp[5])
 
 
+def test_expm1_and_log1p_against_extended_precision(fv, torch_dev):
+    # expm1 from the exponential's reduction, log1p as the logarithm of the
+    # exact sum 1 + z: the status rule's intrinsic value and x near the money
+    torch, dev = torch_dev
+    g = np.random.default_rng(12)
+    v = np.concatenate([-np.exp(g.uniform(np.log(1e-300), np.log(708), 50000)),
+                        g.uniform(-0.01, 0.01, 20000), g.uniform(-1.5, 1.5, 20000),
+                        g.uniform(0, 709.6, 10000), [0.0, -0.0, -708.29, 709.69]])
+    got = _np(fv.fv_math(fv.FV_MATH_EXPM1, torch.tensor(v, device=dev)))
+    ref = np.expm1(v.astype(np.longdouble))
+    nz = ref != 0
+    rel = np.abs((got[nz] - ref[nz]) / ref[nz]).astype(np.float64)
+    assert rel.max() <= 1.25 * 2.0 ** -52, rel.max()
+    assert np.all(got[~nz] == 0)
+    sp = _np(fv.fv_math(fv.FV_MATH_EXPM1, torch.tensor([-708.4, -1e300, 710.0, np.inf, -np.inf, np.nan],
+                                                        dtype=torch.float64, device=dev)))
+    assert sp[0] == -1 and sp[1] == -1 and sp[2] == np.inf and sp[3] == np.inf and sp[4] == -1
+    assert np.isnan(sp[5])
+    u = np.concatenate([g.uniform(-0.5, 1.0, 50000), np.exp(g.uniform(np.log(1e-300), 0, 20000)),
+                        -np.exp(g.uniform(np.log(1e-300), np.log(0.9999), 20000)),
+                        np.exp(g.uniform(0, 700, 10000)), [0.0, -0.5, 1.0, 1.0 / 512, -1.0 / 512]])
+    got = _np(fv.fv_math(fv.FV_MATH_LOG1P, torch.tensor(u, device=dev)))
+    ref = np.log1p(u.astype(np.longdouble))
+    nz = ref != 0
+    rel = np.abs((got[nz] - ref[nz]) / ref[nz]).astype(np.float64)
+    assert rel.max() <= 1.5 * 2.0 ** -52, rel.max()
+    assert np.all(got[~nz] == 0)
+    sp = _np(fv.fv_math(fv.FV_MATH_LOG1P, torch.tensor([-1.0, -2.0, np.inf, np.nan, 5e-324],
+                                                        dtype=torch.float64, device=dev)))
+    assert sp[0] == -np.inf and np.isnan(sp[1]) and sp[2] == np.inf and np.isnan(sp[3])
+    assert sp[4] == 5e-324
+
+
 def test_normalised_black_against_binary128(fv, torch_dev):
     xs = np.concatenate([-np.logspace(-8, np.log10(40), 60), [0.0], np.logspace(-8, np.log10(40), 60)])
     ss = np.logspace(-4, np.log10(50), 90)
