@@ -89,8 +89,15 @@ __device__ __forceinline__ float f_log(float v) { return logf(v); }
 // T_hi + T_lo = 2^(j/128), expm1(r) to r^5 for |r| <= ln2/256.  Arguments whose
 // result is subnormal, infinite or NaN take the library routine; below
 // -745.2 the result is 0.
+// -708.3 < v < 709.7 (the table's range) on the high word, an integer test
+// that keeps the FP64 pipe free; NaN fails it
+__device__ __forceinline__ bool exp_table_range(double v) {
+  const int hv = __double2hiint(v), ah = hv & 0x7fffffff;
+  return ah < (hv >= 0 ? 0x40862d99 : 0x40862266);
+}
+
 __device__ __forceinline__ double exp64(double v) {
-  if (!(v > -708.3 && v < 709.7)) return v < -745.2 ? 0.0 : exp(v);
+  if (!exp_table_range(v)) return v < -745.2 ? 0.0 : exp(v);
   const double t = fma(v, FV_EXP_INV_LN2_N, 6755399441055744.0);  // 1.5 * 2^52: round to integer
   const int k = __double2loint(t);
   const double kd = t - 6755399441055744.0;
@@ -114,7 +121,7 @@ __device__ __forceinline__ double exp64(double v) {
 // there), so that the two terms never cancel by more than a factor ~1.3.
 // Within ~1 ulp for both.
 __device__ __forceinline__ double exp_expm1_64(double v, double& em1) {
-  if (!(v > -708.3 && v < 709.7)) {
+  if (!exp_table_range(v)) {
     em1 = v < 0.0 ? -1.0 : expm1(v);  // +inf, or NaN
     return v < -745.2 ? 0.0 : exp(v);
   }
@@ -143,15 +150,21 @@ __device__ __forceinline__ double exp_expm1_64(double v, double& em1) {
 // Chebyshev interpolant (fv_fp64_tables.h, 136 pieces located from the bits of
 // z, within 1.2 ulp); beyond, the asymptotic series (Abramowitz & Stegun
 // 7.1.23) to the term in z^-8, whose first omitted term is below 2^-55 there.
+//
+// The piece index comes from the high word of z alone (integer operations,
+// which leave the FP64 pipe to the arithmetic): for z >= 0 the integer order
+// of the high words is the numeric order.
 __device__ __forceinline__ double erfcx_nonneg(double z) {
-  if (z < FV_ERFCX_TABLE_END) {
+  const int hi = __double2hiint(z);
+  if (hi < 0x40600000) {  // z < 128 (FV_ERFCX_TABLE_END)
+    const int e = (hi >> 20) - 1023;  // binade 2^e
     int k;
-    if (z < 0.5) {
-      k = __double2int_rz(z * 16.0);  // exact scaling: k in 0..7
+    if (e >= -1) {
+      // e = -1..6 and the top four fraction bits: k in 8..135
+      k = 8 + ((e + 1) << 4) + ((hi >> 16) & 15);
     } else {
-      // binade 2^e, e = -1..6, and the top four fraction bits: k in 8..135
-      const int hi = __double2hiint(z);
-      k = 8 + (((hi >> 20) - 1022) << 4) + ((hi >> 16) & 15);
+      // floor(16 z) = (1.f x 2^20) >> (16 - e) for e = -4..-2, else 0: k in 0..7
+      k = e >= -4 ? ((hi & 0xfffff) | 0x100000) >> (16 - e) : 0;
     }
     // row k: centre, then the coefficients of v^0 .. v^8
     const double2* c = reinterpret_cast<const double2*>(kErfcxTable + k * FV_ERFCX_STRIDE);
@@ -178,7 +191,7 @@ __device__ __forceinline__ double erfcx_nonneg(double z) {
 // keeps its relative accuracy up to the overflow at z^2 ~ 709.8.
 __device__ __forceinline__ double erfcx64(double z) {
   const double p = erfcx_nonneg(fabs(z));
-  if (!(z < 0.0)) return p;
+  if (__double2hiint(z) >= 0) return p;  // sign bit clear
   const double zz = z * z, zl = fma(z, z, -zz);
   const double e2 = 2.0 * exp64(zz);
   return isinf(e2) ? e2 : fma(e2, zl, e2) - p;
@@ -196,8 +209,9 @@ __device__ __forceinline__ double erfcx64(double z) {
 // relative error, |r| <= 0.0028, does not show).
 template <bool kWithC>
 __device__ __forceinline__ double log64_core(double y, double c) {
-  if (!(y >= 2.2250738585072014e-308 && y <= 1.7976931348623157e308)) return log(y);
   const int hi = __double2hiint(y), lo = __double2loint(y);
+  // positive, normal and finite: exponent field 1..2046 with the sign clear
+  if ((unsigned)hi - 0x00100000u >= 0x7fe00000u) return log(y);
   const int mant = hi & 0xfffff;
   int m = (hi >> 20) - 1023, j, ehi;
   if (mant >= 0x6a09e) {  // f >= sqrt2: take f/2 in [1/sqrt2, 1), j in -75..0
@@ -430,15 +444,27 @@ __device__ __forceinline__ T small_t_series(T h, T t, T R) {
 // there b = b_max - e [erfcx((h+t)/sqrt2) + erfcx((t-h)/sqrt2)]/2 instead,
 // with the same error relative to b_max and no exponential (o.B then holds
 // the complement, (b_max - b)/e).
+//
+// log_space: the caller's objective is ln b (the lowest region).  B's
+// relative error is then an absolute error of ln b, which moves s by that
+// error over s (ln b)' ~ h^2.  For small t the erfcx difference loses a factor
+// ~|h|/(2t) = |x|/s^2 to cancellation, so its effect on s is ~eps/|x|: within
+// an ulp for |x| >= 1, where the two erfcx evaluations replace the small-t
+// series (while |x|/s^2 < 1e12 leaves the difference four digits or more).
+template <typename T>
+__device__ __forceinline__ bool series_in_log_space(T x, T s) {
+  return !(x <= T(-1) && -x < T(1e12) * s * s);
+}
+
 template <typename T>
 __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e,
-                                        T bmax = T(-1)) {
+                                        T bmax = T(-1), bool log_space = false) {
   o.inv_s = T(1) / s;
   o.h = x * o.inv_s;
   o.t = T(0.5) * s;
   const T h = o.h, t = o.t;
   o.e = with_e ? f_exp(T(-0.5) * (h * h + t * t)) : T(0);
-  const bool small = (t < Prec<T>::t_small) && !comp;
+  const bool small = (t < Prec<T>::t_small) && !comp && (!log_space || series_in_log_space(x, s));
   const bool via_comp = with_e && !comp && !small && bmax >= T(0) && h + t > T(0);
   const T a1 = small ? -h * T(kInvSqrt2)
                      : ((comp || via_comp) ? (h + t) : -(h + t)) * T(kInvSqrt2);
@@ -584,8 +610,9 @@ __device__ __forceinline__ T guarded(T s, T ds) {
 // once after its FP32 iterations.
 __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg) {
   NB<double> v;
-  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax);
-  const float hh = (float)(v.h * v.h), is = (float)v.inv_s, sf = (float)s;
+  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax, reg == 0);
+  const float hf = (float)v.h, sf = (float)s;
+  const float hh = hf * hf, is = __frcp_rn(sf);
   const float u = hh * is - 0.25f * sf;
   const float du = -3.0f * hh * is * is - 0.25f;
   double nu;

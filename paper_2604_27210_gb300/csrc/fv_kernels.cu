@@ -198,7 +198,10 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<Q>& sm, int model, const
         }
         sm.s32[li] = sg;
         sm.reg[li] = (unsigned char)reg;
-        key[k] = (unsigned char)(reg * 2 + ((0.5f * sg < (float)fvd::Prec<double>::t_small) ? 1 : 0));
+        // small-t class: the FP64 objective of this region takes the series
+        const bool series = 0.5f * sg < (float)fvd::Prec<double>::t_small &&
+                            (reg != 0 || series_in_log_space<float>(q32.x, sg));
+        key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
         rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
       } else {
         sigma[out0 + li] = nq.status == Q_OK ? 0.0 : qnan();

@@ -137,10 +137,26 @@ def _log1p_near(u, tab):
 
 
 def _piece(z):
-    if z < 0.5:
-        return int(z * 16.0)
+    """The kernel's piece index, from the high word of z >= 0 alone."""
     hi = struct.unpack("<q", struct.pack("<d", z))[0] >> 32
-    return 8 + (((hi >> 20) - 1022) << 4) + ((hi >> 16) & 15)
+    e = (hi >> 20) - 1023
+    if e >= -1:
+        return 8 + ((e + 1) << 4) + ((hi >> 16) & 15)
+    return ((hi & 0xfffff) | 0x100000) >> (16 - e) if e >= -4 else 0
+
+
+def test_piece_index_from_the_high_word():
+    # the bit formula gives the piece whose interval holds z: floor(16 z) below
+    # 1/2, binade and top four fraction bits above
+    g = np.random.default_rng(4)
+    edges = [k / 16 for k in range(9)] + [2.0 ** e * (1 + j / 16) for e in range(-1, 7) for j in range(16)]
+    z = np.concatenate([g.uniform(0, 0.5, 20000), np.exp(g.uniform(np.log(1e-300), np.log(128), 20000)),
+                        edges, np.nextafter(edges, 0), np.nextafter(edges, 200), [0.0, 5e-324, 127.99999]])
+    z = z[(z >= 0) & (z < 128)]
+    bounds = [k / 16 for k in range(9)] + [2.0 ** e * (1 + j / 16) for e in range(-1, 7) for j in range(1, 17)]
+    for zi in z:
+        k = _piece(float(zi))
+        assert bounds[k] <= zi < bounds[k + 1], (zi, k)
 
 
 def _fma(x, y, z):
