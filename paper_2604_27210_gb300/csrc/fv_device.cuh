@@ -80,6 +80,40 @@ struct Prec<float> {
   static constexpr float ln_p_floor = -80.0f;
 };
 
+// ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversions and FP64 sign / range tests on the integer unit.
+// On this GPU a conversion between FP64 and FP32 and an FP64 comparison issue
+// on the FP64 pipe like an FMA; the hot loops take them from the bit
+// patterns instead, where the integer pipe has room to spare.
+// ---------------------------------------------------------------------------
+// FP64 -> FP32 with the fraction truncated (relative error below 2^-23).
+// Magnitudes below FP32's normal range give a signed zero; beyond it, and
+// infinities and NaN, a signed infinity.
+__device__ __forceinline__ float f32_trunc(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // FP32 exponent field
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned bits =
+      e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : (sign | ((unsigned)e << 23) | frac));
+  return __uint_as_float(bits);
+}
+
+// FP32 -> FP64, exact for normal numbers, zeros and infinities (FP32
+// subnormals give zero, NaN an infinity).
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned sign = b & 0x80000000u;
+  const bool normal = e != 0u && e != 255u;
+  const unsigned e64 = e == 0u ? 0u : (e == 255u ? 0x7ffu : e + 896u);
+  const unsigned frac = normal ? (b & 0x7fffffu) : 0u;
+  return __hiloint2double((int)(sign | (e64 << 20) | (frac >> 3)), (int)(frac << 29));
+}
+
+// v > 0 (or +NaN): positive doubles are exactly the positive 64-bit patterns
+__device__ __forceinline__ bool positive64(double v) { return __double_as_longlong(v) > 0; }
+
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
 // FP64 exponential, the table-driven method of P. T. P. Tang (ACM TOMS
@@ -451,6 +485,15 @@ __device__ __forceinline__ T small_t_series(T h, T t, T R) {
 // ~|h|/(2t) = |x|/s^2 to cancellation, so its effect on s is ~eps/|x|: within
 // an ulp for |x| >= 1, where the two erfcx evaluations replace the small-t
 // series (while |x|/s^2 < 1e12 leaves the difference four digits or more).
+// t < t_small and b_max >= 0 (b_max < 0 means no bound was passed), for
+// t, b_max of either type; the FP64 forms test the bits
+__device__ __forceinline__ bool small_t(double t) { return __double2hiint(t) < 0x3fb9999a; }  // 0.1
+__device__ __forceinline__ bool small_t(float t) { return t < Prec<float>::t_small; }
+__device__ __forceinline__ bool has_bound(double b) { return __double2hiint(b) >= 0; }
+__device__ __forceinline__ bool has_bound(float b) { return b >= 0.0f; }
+__device__ __forceinline__ bool positive(double v) { return positive64(v); }
+__device__ __forceinline__ bool positive(float v) { return v > 0.0f; }
+
 template <typename T>
 __device__ __forceinline__ bool series_in_log_space(T x, T s) {
   return !(x <= T(-1) && -x < T(1e12) * s * s);
@@ -464,8 +507,8 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
   o.t = T(0.5) * s;
   const T h = o.h, t = o.t;
   o.e = with_e ? f_exp(T(-0.5) * (h * h + t * t)) : T(0);
-  const bool small = (t < Prec<T>::t_small) && !comp && (!log_space || series_in_log_space(x, s));
-  const bool via_comp = with_e && !comp && !small && bmax >= T(0) && h + t > T(0);
+  const bool small = small_t(t) && !comp && (!log_space || series_in_log_space(x, s));
+  const bool via_comp = with_e && !comp && !small && has_bound(bmax) && positive(h + t);
   const T a1 = small ? -h * T(kInvSqrt2)
                      : ((comp || via_comp) ? (h + t) : -(h + t)) * T(kInvSqrt2);
   const T Y1 = f_erfcx(a1);
@@ -600,6 +643,18 @@ template <typename T>
 __device__ __forceinline__ T guarded(T s, T ds) {
   return (s + ds <= T(0.25) * s) ? T(0.25) * s : s + ds;
 }
+// FP64: s > 0, so s/4 is the pattern of s less two in the exponent field
+// (for s >= 2^-1018) and s + ds <= s/4 is the signed order of the patterns
+// (a zero or negative s + ds compares as the FP64 test would; the FP64
+// Householder step is finite)
+template <>
+__device__ __forceinline__ double guarded<double>(double s, double ds) {
+  const long long bs = __double_as_longlong(s);
+  if (bs < (5LL << 52)) return (s + ds <= 0.25 * s) ? 0.25 * s : s + ds;
+  const double sn = s + ds;
+  const long long bq = bs - (2LL << 52);
+  return __double_as_longlong(sn) <= bq ? __longlong_as_double(bq) : sn;
+}
 
 // One Householder(3) step whose residual g and first derivative g' are FP64
 // and whose second-order ratios h2 = g''/g', h3 = g'''/g' are FP32: they only
@@ -611,7 +666,7 @@ __device__ __forceinline__ T guarded(T s, T ds) {
 __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg) {
   NB<double> v;
   nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax, reg == 0);
-  const float hf = (float)v.h, sf = (float)s;
+  const float hf = f32_trunc(v.h), sf = f32_trunc(s);
   const float hh = hf * hf, is = __frcp_rn(sf);
   const float u = hh * is - 0.25f * sf;
   const float du = -3.0f * hh * is * is - 0.25f;
@@ -622,8 +677,8 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
     // Newton step (relative error ~1e-14 in the step, which the next
     // iteration or the convergence of nu to 0 makes invisible)
     double ie;
-    if (v.e > 1e-30) {
-      ie = (double)__frcp_rn((float)v.e);
+    if (__double2hiint(v.e) > 0x39b4484b) {  // e > 1e-30
+      ie = f64_of(__frcp_rn(f32_trunc(v.e)));
       ie = fma(ie, fma(-v.e, ie, 1.0), ie);
     } else {
       ie = 1.0 / v.e;
@@ -635,12 +690,12 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
     const double lnX = nb_log(v);
     // b/b' (region 0) or (b_max - b)/b' (region 3): B sqrt(2 pi), no division
     const double bq = v.B * kSqrt2Pi;
-    const float qf = 1.0f / (float)bq;
+    const float qf = 1.0f / f32_trunc(bq);
     if (reg == 0) {
       // g = 1/ln b - 1/ln beta = (ln beta - ln b) / (ln b ln beta): the
       // residual as a difference of logarithms, no FP64 division
       nu = (q.ln_beta - lnX) * lnX * q.inv_ln_beta * bq;
-      const float iLf = 1.0f / (float)lnX, k1 = 1.0f + 2.0f * iLf;
+      const float iLf = 1.0f / f32_trunc(lnX), k1 = 1.0f + 2.0f * iLf;
       h2 = u - qf * k1;
       h3 = h2 * h2 + du - (qf * u - qf * qf) * k1 + 2.0f * qf * qf * iLf * iLf;
     } else {
@@ -649,10 +704,10 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
       h3 = h2 * h2 + du + qf * h2;
     }
   }
-  const float nf = (float)nu;
+  const float nf = f32_trunc(nu);
   const float phi = nf * (-0.5f * h2 - h3 * nf * (1.0f / 6.0f)) / (1.0f + nf * (h2 + h3 * nf * (1.0f / 6.0f)));
-  const double ds = isfinite(phi) ? nu + nu * (double)phi : nu;
-  return isfinite(ds) ? ds : 0.0;
+  const double ds = isfinite(phi) ? fma(nu, f64_of(phi), nu) : nu;
+  return bits_finite(ds) ? ds : 0.0;
 }
 
 __device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, int reg) {
@@ -786,14 +841,14 @@ __device__ __forceinline__ Reduced<double> reduced64(const Norm& n) {
 
 __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
   Reduced<float> f;
-  f.beta = (float)q.beta;
+  f.beta = f32_trunc(q.beta);
   // below FP32's normal range ln beta comes from FP64 (the FP32 solve works
   // in log space there); above it logf of the FP32 beta is accurate enough
   f.ln_beta = q.ln_beta != 0.0 ? (float)q.ln_beta
                                : (q.beta < 1e-37 ? (float)log(q.beta) : 0.0f);
-  f.c_beta = (float)q.c_beta;
-  f.x = (float)q.x;
-  f.bmax = (float)q.bmax;
+  f.c_beta = f32_trunc(q.c_beta);
+  f.x = f32_trunc(q.x);
+  f.bmax = f32_trunc(q.bmax);
   f.inv_ln_beta = 0.0f;
   f.ln_c_beta = 0.0f;
   return f;
@@ -807,7 +862,7 @@ __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
 // the FP64 guess is taken instead.
 __device__ __forceinline__ double lbr_solve64(const Reduced<double>& q, float g, int reg) {
   if (q.bmax > 1e-20 && g > 1e-30f && g < 1e30f)
-    return lbr_iterate<double>(q, (double)g, reg, 2, 3, 0x1p-17);
+    return lbr_iterate<double>(q, f64_of(g), reg, 2, 3, 0x1p-17);
   int reg64 = 1;
   return lbr_solve<double>(q, 2, 3, 0x1p-17, reg64);
 }
@@ -853,8 +908,9 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
     // Halley: ds = -2 g g' / (2 g'^2 - g g'') = -nu / (1 - nu u / 2), u = b''/b';
     // the factor 1 / (1 - nu u / 2) only shapes the step (its rounding enters at
     // order nu^2), so it is formed in FP32
-    const float u = (float)(v.h * v.h) * (float)v.inv_s - 0.25f * (float)s;
-    const double step = -nu * (double)(1.0f / (1.0f - 0.5f * (float)nu * u));
+    const float hf = f32_trunc(v.h), sf = f32_trunc(s);
+    const float u = hf * hf * __frcp_rn(sf) - 0.25f * sf;
+    const double step = -nu * f64_of(1.0f / (1.0f - 0.5f * f32_trunc(nu) * u));
     double sn = s + step;
     if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
     s = sn;

@@ -246,7 +246,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<Q>& sm, int model, const
         for (int it = 0; it < 2; it++)
           s32 = guarded<float>(s32, hh3_step<float>(objective<float>(q32, s32, reg)));
       }
-      s = hh3_correction(q, (double)s32, reg);
+      s = hh3_correction(q, f64_of(s32), reg);
     }
     sigma[out0 + li] = s * rsqrt(sm.T[li]);
   }

@@ -1,0 +1,66 @@
+"""The integer-unit FP64 <-> FP32 conversions of the kernels' hot loops
+(f32_trunc, f64_of in csrc/fv_device.cuh), step by step on the CPU, against
+numpy's conversions: truncation within 2^-23 relative, exact widening, and
+the stated handling of zeros, FP32 range limits, infinities and NaN."""
+import struct
+
+import numpy as np
+
+
+def _hi_lo(d):
+    b = struct.unpack("<Q", struct.pack("<d", d))[0]
+    return b >> 32, b & 0xffffffff
+
+
+def f32_trunc(d):
+    hi, lo = _hi_lo(d)
+    e = ((hi >> 20) & 0x7ff) - 896
+    sign = hi & 0x80000000
+    frac = ((hi & 0xfffff) << 3) | (lo >> 29)
+    bits = sign if e <= 0 else (sign | 0x7f800000 if e >= 255 else sign | (e << 23) | frac)
+    return struct.unpack("<f", struct.pack("<I", bits))[0]
+
+
+def f64_of(f):
+    b = struct.unpack("<I", struct.pack("<f", f))[0]
+    e = (b >> 23) & 0xff
+    sign = b & 0x80000000
+    normal = e not in (0, 255)
+    e64 = 0 if e == 0 else (0x7ff if e == 255 else e + 896)
+    frac = b & 0x7fffff if normal else 0
+    hi = sign | (e64 << 20) | (frac >> 3)
+    lo = (frac << 29) & 0xffffffff
+    return struct.unpack("<d", struct.pack("<Q", (hi << 32) | lo))[0]
+
+
+def test_truncation_within_fp32_resolution():
+    g = np.random.default_rng(1)
+    d = np.concatenate([np.exp(g.uniform(np.log(1.2e-38), np.log(3.3e38), 20000)) * g.choice([-1, 1], 20000),
+                        [1.0, -1.0, 0.1, 3.4028234663852886e38, 1.1754943508222875e-38]])
+    for v in d:
+        t = f32_trunc(float(v))
+        assert abs(t) <= abs(v) and np.sign(t) == np.sign(v)
+        assert abs(t - v) <= abs(v) * 2.0 ** -23, v
+        # truncation is one of the two FP32 neighbours of v
+        r = float(np.float32(v))
+        assert t == r or t == float(np.nextafter(np.float32(r), np.float32(0)))
+
+
+def test_truncation_special_values():
+    assert f32_trunc(0.0) == 0.0 and str(f32_trunc(-0.0)) == "-0.0"
+    assert f32_trunc(1e-40) == 0.0 and f32_trunc(-1e-300) == 0.0
+    assert f32_trunc(1e39) == np.inf and f32_trunc(-1e300) == -np.inf
+    assert f32_trunc(np.inf) == np.inf and f32_trunc(-np.inf) == -np.inf
+    assert f32_trunc(np.nan) in (np.inf, -np.inf)
+
+
+def test_widening_is_exact():
+    g = np.random.default_rng(2)
+    f = np.concatenate([np.exp(g.uniform(np.log(1.2e-38), np.log(3.3e38), 20000)).astype(np.float32),
+                        np.float32([1, -1, 0.1, 3.4028235e38, 1.1754944e-38, -2.5])])
+    for v in f:
+        assert f64_of(float(v)) == float(v)
+    assert f64_of(0.0) == 0.0 and str(f64_of(-0.0)) == "-0.0"
+    assert f64_of(float(np.float32(1e-40))) == 0.0  # FP32 subnormal
+    assert f64_of(np.inf) == np.inf and f64_of(-np.inf) == -np.inf
+    assert f64_of(float("nan")) in (np.inf, -np.inf)
