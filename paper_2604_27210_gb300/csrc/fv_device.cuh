@@ -114,6 +114,17 @@ __device__ __forceinline__ double f64_of(float f) {
 // v > 0 (or +NaN): positive doubles are exactly the positive 64-bit patterns
 __device__ __forceinline__ bool positive64(double v) { return __double_as_longlong(v) > 0; }
 
+// 1/s for s in FP32's normal range (else the FP64 division): the FP32
+// reciprocal (relative error ~2^-23 after the truncation) and two Newton
+// steps r += r (1 - s r), the error squaring each time; within an ulp.
+__device__ __forceinline__ double recip64(double s) {
+  const unsigned ah = (unsigned)__double2hiint(s) & 0x7fffffffu;
+  if (ah - 0x38200000u >= 0x0fb00000u) return 1.0 / s;  // |s| outside [2^-125, 2^126)
+  double r = f64_of(__frcp_rn(f32_trunc(s)));
+  r = fma(r, fma(-s, r, 1.0), r);
+  return fma(r, fma(-s, r, 1.0), r);
+}
+
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
 // FP64 exponential, the table-driven method of P. T. P. Tang (ACM TOMS
@@ -493,6 +504,8 @@ __device__ __forceinline__ bool has_bound(double b) { return __double2hiint(b) >
 __device__ __forceinline__ bool has_bound(float b) { return b >= 0.0f; }
 __device__ __forceinline__ bool positive(double v) { return positive64(v); }
 __device__ __forceinline__ bool positive(float v) { return v > 0.0f; }
+__device__ __forceinline__ double recip(double s) { return recip64(s); }
+__device__ __forceinline__ float recip(float s) { return 1.0f / s; }
 
 template <typename T>
 __device__ __forceinline__ bool series_in_log_space(T x, T s) {
@@ -502,7 +515,7 @@ __device__ __forceinline__ bool series_in_log_space(T x, T s) {
 template <typename T>
 __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e,
                                         T bmax = T(-1), bool log_space = false) {
-  o.inv_s = T(1) / s;
+  o.inv_s = recip(s);
   o.h = x * o.inv_s;
   o.t = T(0.5) * s;
   const T h = o.h, t = o.t;
@@ -633,6 +646,16 @@ __device__ __forceinline__ Objective<T> objective(const Reduced<T>& q, T s, int 
   return o;
 }
 
+// 1/e for the Newton step nu = (beta - b) sqrt(2 pi)/e: the FP32 reciprocal
+// and one Newton step, relative error ~1e-14, which only scales the step
+// (the next iteration, or nu -> 0 at the root, makes it invisible); e below
+// 1e-30 takes the division
+__device__ __forceinline__ double inv_e(double e) {
+  if (__double2hiint(e) <= 0x39b4484b) return 1.0 / e;  // e >= 0
+  const double r = f64_of(__frcp_rn(f32_trunc(e)));
+  return fma(r, fma(-e, r, 1.0), r);
+}
+
 template <typename T>
 __device__ __forceinline__ T hh3_step(const Objective<T>& o) {
   const T ds = o.nu * (T(1) + T(0.5) * o.h2 * o.nu) / (T(1) + o.nu * (o.h2 + o.h3 * o.nu / T(6)));
@@ -673,17 +696,7 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
   double nu;
   float h2, h3;
   if (reg == 1 || reg == 2) {
-    // nu = (beta - b) sqrt(2 pi) / e with 1/e from the FP32 reciprocal and one
-    // Newton step (relative error ~1e-14 in the step, which the next
-    // iteration or the convergence of nu to 0 makes invisible)
-    double ie;
-    if (__double2hiint(v.e) > 0x39b4484b) {  // e > 1e-30
-      ie = f64_of(__frcp_rn(f32_trunc(v.e)));
-      ie = fma(ie, fma(-v.e, ie, 1.0), ie);
-    } else {
-      ie = 1.0 / v.e;
-    }
-    nu = (q.beta - v.b) * (kSqrt2Pi * ie);
+    nu = (q.beta - v.b) * (kSqrt2Pi * inv_e(v.e));
     h2 = u;
     h3 = u * u + du;
   } else {
@@ -900,10 +913,9 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
       nerr = (g == 0.0) ? 0.0 : hi;
       break;
     }
-    const double bp = v.e * kInvSqrt2Pi;
-    // Newton step nu = g/b' and its distance to the root relative to s (the
-    // convergence test)
-    const double nu = g / bp;
+    // Newton step nu = g/b' = g sqrt(2 pi)/e (e^-1 as in the Householder step)
+    // and its distance to the root relative to s (the convergence test)
+    const double nu = g * (kSqrt2Pi * inv_e(v.e));
     nerr = fabs(nu) * v.inv_s;
     // Halley: ds = -2 g g' / (2 g'^2 - g g'') = -nu / (1 - nu u / 2), u = b''/b';
     // the factor 1 / (1 - nu u / 2) only shapes the step (its rounding enters at
@@ -912,7 +924,10 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
     const float u = hf * hf * __frcp_rn(sf) - 0.25f * sf;
     const double step = -nu * f64_of(1.0f / (1.0f - 0.5f * f32_trunc(nu) * u));
     double sn = s + step;
-    if (!(sn >= lo && sn <= hi) || !isfinite(sn)) sn = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
+    // lo <= sn <= hi, sn finite: lo, hi >= 0, so on the signed patterns
+    const long long bn = __double_as_longlong(sn);
+    if (!(bn >= __double_as_longlong(lo) && bn <= __double_as_longlong(hi) && bits_finite(sn)))
+      sn = bits_finite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
     s = sn;
   }
   HalleyOut o;
