@@ -125,6 +125,15 @@ __device__ __forceinline__ double recip64(double s) {
   return fma(r, fma(-s, r, 1.0), r);
 }
 
+// a/b from that reciprocal with Markstein's correction q + (a - q b)/b, the
+// remainder a - q b exact by one FMA: the rounded quotient up to a last-place
+// difference in rare cases (a non-finite quotient gives NaN or inf)
+__device__ __forceinline__ double div64(double a, double b) {
+  const double r = recip64(b);
+  const double q = a * r;
+  return fma(fma(-q, b, a), r, q);
+}
+
 __device__ __forceinline__ float f_exp(float v) { return expf(v); }
 __device__ __forceinline__ float f_log(float v) { return logf(v); }
 // FP64 exponential, the table-driven method of P. T. P. Tang (ACM TOMS
@@ -153,7 +162,9 @@ __device__ __forceinline__ double exp64(double v) {
   q = fma(q, r, 0.5);
   const double p = fma(r * r, q, r);  // expm1(r)
   const double2 tj = __ldg(reinterpret_cast<const double2*>(kExpTable) + (k & (FV_EXP_N - 1)));
-  return (tj.x + fma(tj.x, p, tj.y)) * __hiloint2double(((k >> 7) + 1023) << 20, 0);
+  // times 2^m by adding m to the exponent field (the result is normal here)
+  const double r1 = tj.x + fma(tj.x, p, tj.y);
+  return __longlong_as_double(__double_as_longlong(r1) + ((long long)(k >> 7) << 52));
 }
 
 // exp(v) and expm1(v) from one reduction of the method above (the polynomial
@@ -171,7 +182,7 @@ __device__ __forceinline__ double exp_expm1_64(double v, double& em1) {
     return v < -745.2 ? 0.0 : exp(v);
   }
   const double t = fma(v, FV_EXP_INV_LN2_N, 6755399441055744.0);
-  const bool tiny = fabs(v) < 0.005;
+  const bool tiny = (__double2hiint(v) & 0x7fffffff) < 0x3f747ae1;  // |v| < 0.005
   const int k = tiny ? 0 : __double2loint(t);
   const double kd = tiny ? 0.0 : t - 6755399441055744.0;
   double r = fma(kd, -FV_EXP_LN2_N_HI, v);
@@ -277,7 +288,9 @@ __device__ __forceinline__ double log64_core(double y, double c) {
   q = fma(q, r, 1.0 / 3.0);
   q = fma(q, r, -0.5);
   const double p = fma(r * r, q, r);  // log1p(r)
-  const double md = (double)m;
+  // m as a double without an int -> FP64 conversion: 2^52 + 2^31 + m is exact
+  // in the low word of a double with high word 0x43300000
+  const double md = __hiloint2double(0x43300000, m ^ (int)0x80000000) - 4503601774854144.0;
   return fma(md, FV_LN2_HI, t0.y) + (fma(md, FV_LN2_LO, t1.x) + p);
 }
 __device__ __forceinline__ double log64(double y) { return log64_core<false>(y, 0.0); }
@@ -340,7 +353,7 @@ __device__ __forceinline__ bool within_factor_two(double SF, double K) {
 // rounding error (|u| <= 1).
 __device__ __forceinline__ double log_moneyness(double SF, double K) {
   const bool near = within_factor_two(SF, K);
-  const double u = __ddiv_rn(near ? __dsub_rn(SF, K) : SF, K);
+  const double u = div64(near ? __dsub_rn(SF, K) : SF, K);
   const double y = near ? __dadd_rn(1.0, u) : u;
   return log64(y, near ? __dsub_rn(u, __dsub_rn(y, 1.0)) : 0.0);
 }
@@ -373,8 +386,9 @@ __device__ __forceinline__ double model_x(int model, double SF, double K, double
 
 // The status rule: every product and sum rounded as written (no contraction),
 // so the decision matches an FP64 evaluation of the same expressions up to the
-// last-place differences of exp / expm1 / log1p / log implementations, which
-// the 64-ulp band of the bound tests absorbs.
+// last-place differences of exp / expm1 / log1p / log implementations and of
+// the divisions' rare last-place misses, which the 64-ulp band of the bound
+// tests absorbs.
 __device__ __forceinline__ Norm decide(int model, double P, double SF, double K, double T,
                                        double r, double q, int flag) {
   Norm o;
@@ -407,7 +421,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   const long long bx = __double_as_longlong(x);
   const bool itm = flag > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL);
   double iota = 0.0;
-  if (itm) iota = __ddiv_rn(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em);
+  if (itm) iota = div64(__dmul_rn(-E, __dadd_rn(1.0, Em)), Em);
   o.x = x;
   o.beta = beta;
   o.iota = iota;
@@ -858,7 +872,7 @@ __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
   // below FP32's normal range ln beta comes from FP64 (the FP32 solve works
   // in log space there); above it logf of the FP32 beta is accurate enough
   f.ln_beta = q.ln_beta != 0.0 ? (float)q.ln_beta
-                               : (q.beta < 1e-37 ? (float)log(q.beta) : 0.0f);
+                               : (__double2hiint(q.beta) < 0x3841039d ? (float)log(q.beta) : 0.0f);  // beta < 1e-37
   f.c_beta = f32_trunc(q.c_beta);
   f.x = f32_trunc(q.x);
   f.bmax = f32_trunc(q.bmax);

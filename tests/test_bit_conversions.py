@@ -64,3 +64,42 @@ def test_widening_is_exact():
     assert f64_of(float(np.float32(1e-40))) == 0.0  # FP32 subnormal
     assert f64_of(np.inf) == np.inf and f64_of(-np.inf) == -np.inf
     assert f64_of(float("nan")) in (np.inf, -np.inf)
+
+
+
+def _fma(x, y, z):
+    """x*y + z rounded once (what the GPU's FMA does)."""
+    from fractions import Fraction
+    return float(Fraction(x) * Fraction(y) + Fraction(z))
+
+
+def _recip64(s):
+    """The kernels' recip64 for s in FP32's normal range: the FP32 reciprocal of
+    the truncated s (correctly rounded, as __frcp_rn), then two Newton steps."""
+    r = f64_of(float(np.float32(1.0) / np.float32(f32_trunc(s))))
+    r = _fma(r, _fma(-s, r, 1.0), r)
+    return _fma(r, _fma(-s, r, 1.0), r)
+
+
+def _div64(a, b):
+    r = _recip64(b)
+    q = a * r
+    return _fma(_fma(-q, b, a), r, q)
+
+
+def test_reciprocal_and_markstein_division():
+    # the reciprocal within an ulp; the quotient the rounded one but for rare
+    # last-place misses
+    g = np.random.default_rng(3)
+    b = np.exp(g.uniform(np.log(1e-30), np.log(1e30), 5000))
+    a = np.exp(g.uniform(np.log(1e-30), np.log(1e30), 5000)) * g.choice([-1, 1], 5000)
+    miss = 0
+    for ai, bi in zip(a, b):
+        r = _recip64(float(bi))
+        assert abs(r - 1.0 / float(bi)) <= abs(np.spacing(1.0 / float(bi)))
+        q = _div64(float(ai), float(bi))
+        exact = float(ai) / float(bi)
+        if q != exact:
+            miss += 1
+            assert abs(q - exact) <= abs(np.spacing(exact)), (ai, bi)
+    assert miss <= len(a) * 2e-3, miss
