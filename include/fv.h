@@ -191,7 +191,11 @@ fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta
  *                  -1 below z = -708.3, +inf above 709.78;
  *   FV_MATH_LOG1P  ln(1 + z) as the logarithm of the exact sum 1 + z, the
  *                  form the status rule gives x = ln(F/K) near the money;
- *                  -inf at z = -1, NaN below.
+ *                  -inf at z = -1, NaN below;
+ *   FV_MATH_ERFCX_SQRT2  erfcx(z/sqrt2), the form the solvers and Greeks call
+ *                  (their arguments are h + t, t - h, h and |d|): the piece
+ *                  index from an FP32 view of z/sqrt2, v = z/sqrt2 - c by one
+ *                  FMA; any z.
  * The paper has no counterpart entry point: this exposes what the kernels
  * compute so that it can be checked on its own.  z, out: device arrays of n
  * doubles (caller-owned); NaN gives NaN.  Errors: unknown function, n < 0 or
@@ -201,7 +205,8 @@ typedef enum {
   FV_MATH_LOG = 1,
   FV_MATH_EXP = 2,
   FV_MATH_EXPM1 = 3,
-  FV_MATH_LOG1P = 4
+  FV_MATH_LOG1P = 4,
+  FV_MATH_ERFCX_SQRT2 = 5
 } fv_math_fn;
 fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* stream);
 

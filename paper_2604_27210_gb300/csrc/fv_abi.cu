@@ -365,7 +365,7 @@ fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta
 fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* stream) {
   const char* fn = "fv_math";
   if (which != FV_MATH_ERFCX && which != FV_MATH_LOG && which != FV_MATH_EXP &&
-      which != FV_MATH_EXPM1 && which != FV_MATH_LOG1P)
+      which != FV_MATH_EXPM1 && which != FV_MATH_LOG1P && which != FV_MATH_ERFCX_SQRT2)
     return fail(FV_ERR_ARG, "%s: unknown function %d", fn, (int)which);
   if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
   if (n == 0) return FV_SUCCESS;

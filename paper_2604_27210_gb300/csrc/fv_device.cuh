@@ -114,6 +114,17 @@ __device__ __forceinline__ double f64_of(float f) {
 // v > 0 (or +NaN): positive doubles are exactly the positive 64-bit patterns
 __device__ __forceinline__ bool positive64(double v) { return __double_as_longlong(v) > 0; }
 
+// v/2 on the pattern: one less in the exponent field for normal numbers from
+// 2^-1021 up, the magnitude bits shifted right below (truncating a subnormal's
+// last bit); zero, infinity and NaN pass through
+__device__ __forceinline__ double half64(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const long long sign = b & (long long)0x8000000000000000ULL;
+  return __longlong_as_double(e >= 2 ? (e == 0x7ff ? b : b - (1LL << 52))
+                                     : (sign | ((b & 0x7fffffffffffffffLL) >> 1)));
+}
+
 // 1/s for s in FP32's normal range (else the FP64 division): the FP32
 // reciprocal (relative error ~2^-23 after the truncation) and two Newton
 // steps r += r (1 - s r), the error squaring each time; within an ulp.
@@ -210,6 +221,32 @@ __device__ __forceinline__ double exp_expm1_64(double v, double& em1) {
 // The piece index comes from the high word of z alone (integer operations,
 // which leave the FP64 pipe to the arithmetic): for z >= 0 the integer order
 // of the high words is the numeric order.
+// The interpolant of piece k at v = make_v(c_k), the caller's form of
+// z - c_k (c_k the piece's centre, the row's first entry).
+template <typename MakeV>
+__device__ __forceinline__ double erfcx_piece(int k, const MakeV& make_v) {
+  // row k: centre, then the coefficients of v^0 .. v^8
+  const double2* c = reinterpret_cast<const double2*>(kErfcxTable + k * FV_ERFCX_STRIDE);
+  const double2 c0 = __ldg(c), c1 = __ldg(c + 1), c2 = __ldg(c + 2), c3 = __ldg(c + 3),
+                c4 = __ldg(c + 4);
+  const double v = make_v(c0.x);
+  double p = fma(c4.y, v, c4.x);
+  p = fma(p, v, c3.y);
+  p = fma(p, v, c3.x);
+  p = fma(p, v, c2.y);
+  p = fma(p, v, c2.x);
+  p = fma(p, v, c1.y);
+  p = fma(p, v, c1.x);
+  return fma(p, v, c0.y);
+}
+
+// z >= 128, +inf (gives 0) or NaN (gives NaN)
+__device__ __forceinline__ double erfcx_asymptotic(double z) {
+  const double r = 1.0 / z, w = r * r;
+  const double sum = fma(w, fma(w, fma(w, fma(w, 6.5625, -1.875), 0.75), -0.5), 1.0);
+  return kInvSqrtPi * r * sum;
+}
+
 __device__ __forceinline__ double erfcx_nonneg(double z) {
   const int hi = __double2hiint(z);
   if (hi < 0x40600000) {  // z < 128 (FV_ERFCX_TABLE_END)
@@ -222,24 +259,31 @@ __device__ __forceinline__ double erfcx_nonneg(double z) {
       // floor(16 z) = (1.f x 2^20) >> (16 - e) for e = -4..-2, else 0: k in 0..7
       k = e >= -4 ? ((hi & 0xfffff) | 0x100000) >> (16 - e) : 0;
     }
-    // row k: centre, then the coefficients of v^0 .. v^8
-    const double2* c = reinterpret_cast<const double2*>(kErfcxTable + k * FV_ERFCX_STRIDE);
-    const double2 c0 = __ldg(c), c1 = __ldg(c + 1), c2 = __ldg(c + 2), c3 = __ldg(c + 3),
-                  c4 = __ldg(c + 4);
-    const double v = z - c0.x;  // exact
-    double p = fma(c4.y, v, c4.x);
-    p = fma(p, v, c3.y);
-    p = fma(p, v, c3.x);
-    p = fma(p, v, c2.y);
-    p = fma(p, v, c2.x);
-    p = fma(p, v, c1.y);
-    p = fma(p, v, c1.x);
-    return fma(p, v, c0.y);
+    return erfcx_piece(k, [&](double c) { return z - c; });  // exact
   }
-  // z >= 128, +inf (gives 0) or NaN (gives NaN)
-  const double r = 1.0 / z, w = r * r;
-  const double sum = fma(w, fma(w, fma(w, fma(w, 6.5625, -1.875), 0.75), -0.5), 1.0);
-  return kInvSqrtPi * r * sum;
+  return erfcx_asymptotic(z);
+}
+
+// erfcx(w/sqrt2) for w >= 0, the form the kernels call (their arguments come
+// as h + t, t - h, h, |d|): v = w/sqrt2 - c_k is one FMA, and the piece index
+// comes from the FP32 view of z = w/sqrt2 on the integer unit.  That view may
+// place z in the neighbouring piece next to an edge (it is within 2^-22 of
+// z), where the piece's interpolant, evaluated that little outside its
+// interval, keeps its accuracy.
+__device__ __forceinline__ double erfcx_nonneg_w(double w) {
+  const unsigned b = __float_as_uint(f32_trunc(w) * 0.70710677f);
+  if (b < 0x43000000u) {  // z < 128 in FP32
+    const int e = (int)(b >> 23) - 127;
+    int k;
+    if (e >= -1) {
+      k = 8 + ((e + 1) << 4) + (int)((b >> 19) & 15u);
+    } else {
+      // floor(16 z) = (1.f x 2^23) >> (19 - e) for e = -4..-2, else 0
+      k = e >= -4 ? (int)(((b & 0x7fffffu) | 0x800000u) >> (19 - e)) : 0;
+    }
+    return erfcx_piece(k, [&](double c) { return fma(w, kInvSqrt2, -c); });
+  }
+  return erfcx_asymptotic(w * kInvSqrt2);
 }
 
 // erfcx for any z: below zero by reflection, erfcx(z) = 2 exp(z^2) - erfcx(-z),
@@ -251,6 +295,16 @@ __device__ __forceinline__ double erfcx64(double z) {
   const double zz = z * z, zl = fma(z, z, -zz);
   const double e2 = 2.0 * exp64(zz);
   return isinf(e2) ? e2 : fma(e2, zl, e2) - p;
+}
+
+// erfcx(w/sqrt2) for any w, by the same reflection; z^2 = w^2/2 is split
+// exactly from w (the halving is exact)
+__device__ __forceinline__ double erfcx64_w(double w) {
+  const double p = erfcx_nonneg_w(fabs(w));
+  if (__double2hiint(w) >= 0) return p;
+  const double ww = w * w, wl = fma(w, w, -ww);
+  const double e2 = 2.0 * exp64(0.5 * ww);
+  return isinf(e2) ? e2 : fma(e2, 0.5 * wl, e2) - p;
 }
 
 // FP64 natural logarithm, the table-driven method of P. T. P. Tang (ACM TOMS
@@ -307,6 +361,11 @@ __device__ __forceinline__ double f_erfcx(double v) { return erfcx64(v); }
 __device__ __forceinline__ double f_exp(double v) { return exp64(v); }
 __device__ __forceinline__ double f_log(double v) { return log64(v); }
 __device__ __forceinline__ float f_erfcx(float v) { return erfcxf(v); }
+// erfcx(w/sqrt2)
+__device__ __forceinline__ double f_erfcx_w(double w) { return erfcx64_w(w); }
+__device__ __forceinline__ float f_erfcx_w(float w) { return erfcxf(w * float(kInvSqrt2)); }
+__device__ __forceinline__ double f_half(double v) { return half64(v); }
+__device__ __forceinline__ float f_half(float v) { return 0.5f * v; }
 __device__ __forceinline__ double f_ncdf(double v) { return normcdf(v); }
 __device__ __forceinline__ float f_ncdf(float v) { return normcdff(v); }
 __device__ __forceinline__ double f_ncdfinv(double v) { return normcdfinv(v); }
@@ -531,14 +590,14 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
                                         T bmax = T(-1), bool log_space = false) {
   o.inv_s = recip(s);
   o.h = x * o.inv_s;
-  o.t = T(0.5) * s;
+  o.t = f_half(s);
   const T h = o.h, t = o.t;
-  o.e = with_e ? f_exp(T(-0.5) * (h * h + t * t)) : T(0);
+  o.e = with_e ? f_exp(-f_half(h * h + t * t)) : T(0);
   const bool small = small_t(t) && !comp && (!log_space || series_in_log_space(x, s));
   const bool via_comp = with_e && !comp && !small && has_bound(bmax) && positive(h + t);
-  const T a1 = small ? -h * T(kInvSqrt2)
-                     : ((comp || via_comp) ? (h + t) : -(h + t)) * T(kInvSqrt2);
-  const T Y1 = f_erfcx(a1);
+  // erfcx of w/sqrt2 with w = -h, h + t or -(h + t)
+  const T w1 = small ? -h : ((comp || via_comp) ? (h + t) : -(h + t));
+  const T Y1 = f_erfcx_w(w1);
   if (small) {
     if (f_abs(h) < Prec<T>::h_asym) {
       o.B = T(kSqrt2OverPi) * small_t_series<T>(h, t, T(kSqrtPiOver2) * Y1);
@@ -549,8 +608,8 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
       o.B = T(kSqrt2OverPi) * (t / D) * (T(1) - (T(3) * h * h + t * t) / (D * D));
     }
   } else {
-    const T Y2 = f_erfcx((t - h) * T(kInvSqrt2));
-    o.B = (comp || via_comp) ? T(0.5) * (Y1 + Y2) : T(0.5) * (Y1 - Y2);
+    const T Y2 = f_erfcx_w(t - h);
+    o.B = f_half((comp || via_comp) ? Y1 + Y2 : Y1 - Y2);
   }
   o.b = via_comp ? bmax - o.e * o.B : o.e * o.B;
 }

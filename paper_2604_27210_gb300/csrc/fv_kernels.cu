@@ -547,7 +547,7 @@ __device__ __forceinline__ double gauss64(double z) {
 // Phi(z) from the table erfcx and ez = e^{-z^2/2}: the lower tail
 // erfcx(|z|/sqrt2) ez / 2 (no cancellation), or one minus it above zero
 __device__ __forceinline__ double ncdf64(double z, double ez) {
-  const double tail = 0.5 * erfcx64(fabs(z) * kInvSqrt2) * ez;
+  const double tail = half64(erfcx64_w(fabs(z)) * ez);
   return z <= 0.0 ? tail : 1.0 - tail;
 }
 __device__ __forceinline__ D12 d12(double x, double s, int th) {
@@ -703,7 +703,8 @@ __global__ void __launch_bounds__(256) k_math(const double* z, int64_t n, double
              : FN == 1 ? log64(v)
              : FN == 2 ? exp64(v)
              : FN == 3 ? (exp_expm1_64(v, em1), em1)
-                       : log1p64(v);
+             : FN == 4 ? log1p64(v)
+                       : erfcx64_w(v);
   }
 }
 
@@ -713,7 +714,8 @@ cudaError_t launch_math(int fn, const double* z, int64_t n, double* out, cudaStr
     case 1: launch_shaped<k_math<1>>(n, st, z, n, out); break;
     case 2: launch_shaped<k_math<2>>(n, st, z, n, out); break;
     case 3: launch_shaped<k_math<3>>(n, st, z, n, out); break;
-    default: launch_shaped<k_math<4>>(n, st, z, n, out); break;
+    case 4: launch_shaped<k_math<4>>(n, st, z, n, out); break;
+    default: launch_shaped<k_math<5>>(n, st, z, n, out); break;
   }
   return cudaGetLastError();
 }

@@ -301,7 +301,7 @@ def fv_normalised_black(x, s, theta, out=None, stream=None):
     return out
 
 
-FV_MATH_ERFCX, FV_MATH_LOG, FV_MATH_EXP, FV_MATH_EXPM1, FV_MATH_LOG1P = 0, 1, 2, 3, 4
+FV_MATH_ERFCX, FV_MATH_LOG, FV_MATH_EXP, FV_MATH_EXPM1, FV_MATH_LOG1P, FV_MATH_ERFCX_SQRT2 = 0, 1, 2, 3, 4, 5
 
 
 def fv_math(which, z, out=None, stream=None):

@@ -75,7 +75,7 @@ def test_argument_errors_before_any_launch(lib):
     # the Halley solver has no mixed path
     assert lib.fv_implied_vol_ex(0, 1, 1, 0, p, p, p, p, p, None, p, N(4), p, p, None) == -3
     lib.fv_math.restype = ctypes.c_int
-    assert lib.fv_math(5, p, N(4), p, None) == -1
+    assert lib.fv_math(6, p, N(4), p, None) == -1
     assert b"unknown function" in lib.fv_last_error()
     assert lib.fv_math(4, p, N(-1), p, None) == -1
     assert lib.fv_math(3, None, N(4), p, None) == -1

@@ -122,6 +122,41 @@ def test_erfcx_against_binary128(fv, torch_dev):
     assert sp[0] == 0 and sp[1] == np.inf and sp[2] == np.inf and np.isnan(sp[3]) and sp[4] == 1.0
 
 
+def test_erfcx_of_w_over_sqrt2_against_binary128(fv, torch_dev):
+    # the solvers' form erfcx(w/sqrt2): its piece index comes from an FP32 view
+    # of w/sqrt2, so arguments next to every piece edge are included.  The
+    # reference is the oracle's erfcx at z = fl(w/sqrt2) moved to the exact
+    # w/sqrt2 by the derivative erfcx'(z) = 2 z erfcx(z) - 2/sqrt(pi).
+    torch, dev = torch_dev
+    g = np.random.default_rng(13)
+    edges = np.array([k / 16 for k in range(1, 9)] + [2.0 ** e * (1 + j / 16) for e in range(-1, 7)
+                                                      for j in range(16)] + [128.0])
+    we = edges * np.sqrt(2.0)
+    w = np.concatenate([g.uniform(0, 0.8, 20000), np.exp(g.uniform(np.log(0.7), np.log(181), 50000)),
+                        np.exp(g.uniform(np.log(181), np.log(1e300), 5000)), we, np.nextafter(we, 0),
+                        np.nextafter(we, np.inf), we * (1 - 3e-7), we * (1 + 3e-7), [0.0, 5e-324],
+                        -g.uniform(0, 37.6, 20000)])
+    got = _np(fv.fv_math(fv.FV_MATH_ERFCX_SQRT2, torch.tensor(w, device=dev)))
+    k = np.longdouble(1) / np.sqrt(np.longdouble(2))
+    z_ld = w.astype(np.longdouble) * k
+    z = z_ld.astype(np.float64)
+    delta = (z_ld - z.astype(np.longdouble)).astype(np.float64)
+    fz = orc.erfcx(z)
+    # (beyond z = 10 the derivative's two terms cancel: take erfcx'/erfcx ~ -1/z)
+    big = z > 10
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref = np.where(big, fz * (1 - delta / np.where(big, z, 1.0)),
+                       fz + delta * (2 * z * fz - 2 / np.sqrt(np.pi)))
+    fin = np.isfinite(ref) & (ref > 0)
+    rel = np.abs(got[fin] - ref[fin]) / ref[fin]
+    wf = w[fin]
+    # the table's 1.2 ulp, the rounded constant 1/sqrt2 inside v = w/sqrt2 - c
+    # (z |d ln erfcx/dz| <= ~1 of its 0.35 ulp) and v's rounding, and the
+    # reference's own final rounding
+    assert rel[wf >= 0].max() <= 6e-16, rel[wf >= 0].max()
+    assert rel[wf < 0].max() <= 1e-15, rel[wf < 0].max()
+
+
 def test_log_against_extended_precision(fv, torch_dev):
     # the kernels' own FP64 log (Tang's table-driven method) against numpy's
     # long double log (binary128 on Arm, 64-bit mantissa on x86)
