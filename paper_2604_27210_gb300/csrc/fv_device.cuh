@@ -460,7 +460,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   const double x = model_x(model, SF, K, T, r, qq);
   double beta;
   const double rate = model == M_BLACK76 ? __dmul_rn(r, T)
-                                         : __dmul_rn(__dmul_rn(0.5, __dadd_rn(r, qq)), T);
+                                         : __dmul_rn(half64(__dadd_rn(r, qq)), T);
   // P e^{rate} / sqrt(F K) as a product with the reciprocal square root (one
   // FP64 step instead of a square root and a division; within 1.5 ulp)
   beta = __dmul_rn(__dmul_rn(P, exp64(rate)), rsqrt(__dmul_rn(SF, K)));
@@ -475,7 +475,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   // accurate near the money) an in-the-money quote's intrinsic value is
   // e^{|x|/2} - e^{-|x|/2} = -E (1 + Em) / Em, accurate for every x
   double E;
-  const double Em = exp_expm1_64(-0.5 * fabs(x), E);
+  const double Em = exp_expm1_64(-half64(fabs(x)), E);
   // in the money: x > 0 for a call, x < 0 for a put (sign tests on the bits)
   const long long bx = __double_as_longlong(x);
   const bool itm = flag > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL);
@@ -617,13 +617,13 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
 // ln of the value nb_eval describes
 template <typename T>
 __device__ __forceinline__ T nb_log(const NB<T>& v) {
-  return T(-0.5) * (v.h * v.h + v.t * v.t) + f_log(v.B);
+  return f_log(v.B) - f_half(v.h * v.h + v.t * v.t);
 }
 
 // full normalised Black b(x, s, theta) for any x, s >= 0 (FP64)
 __device__ __forceinline__ double normalised_black(double x, double s, int theta) {
   double E;
-  const double Em = exp_expm1_64(-0.5 * fabs(x), E);  // e^{-|x|/2}, its expm1
+  const double Em = exp_expm1_64(-half64(fabs(x)), E);  // e^{-|x|/2}, its expm1
   double iota = 0.0;
   const long long bx = __double_as_longlong(x);  // theta x > 0 on the sign bits
   if (theta > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL))
@@ -733,6 +733,18 @@ template <typename T>
 __device__ __forceinline__ T hh3_step(const Objective<T>& o) {
   const T ds = o.nu * (T(1) + T(0.5) * o.h2 * o.nu) / (T(1) + o.nu * (o.h2 + o.h3 * o.nu / T(6)));
   return f_finite(ds) ? ds : o.nu;
+}
+
+// |ds| > tol s; for FP64 with tol a power of two and s >= 2^-960 (every
+// solver's case) on the patterns: tol s is s with tol's exponent added
+__device__ __forceinline__ bool moved_more(float ds, float s, float tol) {
+  return fabsf(ds) > tol * s;
+}
+__device__ __forceinline__ bool moved_more(double ds, double s, double tol) {
+  const long long bt = __double_as_longlong(tol), bs = __double_as_longlong(s);
+  if ((bt & 0xfffffffffffffLL) != 0 || bs < (64LL << 52) || bt <= 0) return fabs(ds) > tol * s;
+  const long long lim = bs + (bt - (1023LL << 52));  // pattern of tol * s
+  return (__double_as_longlong(ds) & 0x7fffffffffffffffLL) > lim;
 }
 
 template <typename T>
@@ -900,7 +912,7 @@ __device__ __forceinline__ T lbr_iterate(Reduced<T> q, T s, int reg, int n_min, 
     else
       ds = hh3_step<T>(objective<T>(q, s, reg));
     s = guarded<T>(s, ds);
-    if (k + 1 >= n_min && !(f_abs(ds) > conv_tol * s)) break;
+    if (k + 1 >= n_min && !moved_more(ds, s, conv_tol)) break;
   }
   return s;
 }
