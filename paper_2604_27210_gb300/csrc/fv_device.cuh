@@ -627,7 +627,7 @@ __device__ __forceinline__ double normalised_black(double x, double s, int theta
   double iota = 0.0;
   const long long bx = __double_as_longlong(x);  // theta x > 0 on the sign bits
   if (theta > 0 ? bx > 0 : (bx < 0 && bx != (long long)0x8000000000000000ULL))
-    iota = -E * (1.0 + Em) / Em;
+    iota = div64(-E * (1.0 + Em), Em);
   if (!(s > 0.0)) return iota;
   NB<double> v;
   nb_eval<double>(-fabs(x), s, false, v, true, Em);

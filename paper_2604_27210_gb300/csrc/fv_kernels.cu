@@ -506,7 +506,7 @@ __device__ __forceinline__ double price_scale(int model, double SF, double K, do
                                               double q) {
   if (model == M_BLACK76) return exp64(-r * T) * sqrt(SF * K);
   const double qq = model == M_BSM ? q : 0.0;
-  return exp64(-0.5 * (r + qq) * T) * sqrt(SF * K);
+  return exp64(-half64(r + qq) * T) * sqrt(SF * K);
 }
 
 __global__ void __launch_bounds__(256)
@@ -553,7 +553,7 @@ __device__ __forceinline__ double ncdf64(double z, double ez) {
 __device__ __forceinline__ D12 d12(double x, double s, int th) {
   D12 o;
   o.s = s;
-  o.d1 = x / s + 0.5 * s;
+  o.d1 = fma(x, recip64(s), half64(s));
   const double d2 = o.d1 - s;
   const double e1 = gauss64(o.d1), e2 = gauss64(d2);
   o.N1 = ncdf64(th * o.d1, e1);
@@ -580,17 +580,17 @@ __global__ void __launch_bounds__(256)
       if (model == M_BLACK76) {
         const double V = Dr * sqrt(sf * k) * normalised_black(x, s, th);
         gd = th * Dr * d.N1;
-        gg = Dr * d.n1 / (sf * s);
+        gg = div64(Dr * d.n1, sf * s);
         gv = sf * Dr * d.n1 * sq * 0.01;
-        gt = (-sf * Dr * d.n1 * sg / (2.0 * sq) + rr * V) / 365.0;
+        gt = (-sf * Dr * d.n1 * sg * half64(recip64(sq)) + rr * V) * (1.0 / 365.0);
         gr = -t * V * 0.01;
       } else {
         const double Dq = exp64(-qq * t);
         gd = th * Dq * d.N1;
-        gg = Dq * d.n1 / (sf * s);
+        gg = div64(Dq * d.n1, sf * s);
         gv = sf * Dq * d.n1 * sq * 0.01;
-        gt = (-sf * Dq * d.n1 * sg / (2.0 * sq) - th * rr * k * Dr * d.N2 +
-              th * qq * sf * Dq * d.N1) / 365.0;
+        gt = (-sf * Dq * d.n1 * sg * half64(recip64(sq)) - th * rr * k * Dr * d.N2 +
+              th * qq * sf * Dq * d.N1) * (1.0 / 365.0);
         gr = th * k * t * Dr * d.N2 * 0.01;
       }
     }
@@ -634,20 +634,20 @@ __global__ void __launch_bounds__(256)
           vega = sf * Dr * d.n1 * sq;
           VS = th * Dr * d.N1;
           VK = -th * Dr * d.N2;
-          VT = -rr * V + Dr * sf * d.n1 * sg / (2.0 * sq);
+          VT = -rr * V + Dr * sf * d.n1 * sg * half64(recip64(sq));
           Vr = -t * V;
         } else {
           const double Dq = exp64(-qq * t);
           vega = sf * Dq * d.n1 * sq;
           VS = th * Dq * d.N1;
           VK = -th * Dr * d.N2;
-          VT = sf * Dq * d.n1 * sg / (2.0 * sq) - th * qq * sf * Dq * d.N1 +
+          VT = sf * Dq * d.n1 * sg * half64(recip64(sq)) - th * qq * sf * Dq * d.N1 +
                th * rr * k * Dr * d.N2;
           Vr = th * k * t * Dr * d.N2;
           Vq = (model == M_BSM) ? -th * sf * t * Dq * d.N1 : 0.0;
         }
         if (vega > 0.0) {
-          const double g = gsig[i] / vega;
+          const double g = div64(gsig[i], vega);
           oP = g;
           oS = -g * VS;
           oK = -g * VK;
