@@ -38,16 +38,16 @@ BYTES_PER_QUOTE = 58
 # DADD + DMUL + 2 x DFMA from ncu's smsp__sass_thread_inst_executed_op_*_pred_on
 # counters on 4,194,304 quotes of the same grid distribution.  This is the
 # ALU roofline's work per quote (the kernels are bound by the FP64 pipe).
-FP64_FLOPS_PER_QUOTE = {"lbr": 315.0, "mixed": 232.0, "fp32": 124.0}
+FP64_FLOPS_PER_QUOTE = {"lbr": 308.0, "mixed": 229.0, "fp32": 121.0}
 # DRAM bytes (read + write) per quote of the same kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid;
 # traffic grows in proportion to the quotes, so a launch's traffic is this x n.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205971968 + 24865024) / 4194304,
-                            "mixed": (206093312 + 24786432) / 4194304}
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205688576 + 24795904) / 4194304,
+                            "mixed": (205760768 + 24775168) / 4194304}
 # share of cycles the FP64 pipe was busy in the same captures (the flops above
 # leave out conversions, compares and the FP64 steps of divisions and square
 # roots, which occupy the pipe too)
-FP64_PIPE_BUSY_NCU = {"lbr": 0.833, "mixed": 0.787, "fp32": 0.821}
+FP64_PIPE_BUSY_NCU = {"lbr": 0.821, "mixed": 0.764, "fp32": 0.820}
 # FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock (ncu's sustained peak of
 # the thread-level DFMA counter) x 2 flops x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
