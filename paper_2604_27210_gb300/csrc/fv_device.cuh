@@ -56,7 +56,8 @@ enum { Q_OK = 0, Q_BELOW = 1, Q_ABOVE = 2, Q_INVALID = 3 };
 enum { M_BLACK76 = 0, M_BS = 1, M_BSM = 2 };
 
 // ---------------------------------------------------------------------------
-// precision traits and special-function wrappers (CUDA's math library)
+// precision traits and special-function wrappers (FP64: this file's table-driven
+// functions; FP32: CUDA's math library)
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Prec;

@@ -1,7 +1,10 @@
-"""The integer-unit FP64 <-> FP32 conversions of the kernels' hot loops
-(f32_trunc, f64_of in csrc/fv_device.cuh), step by step on the CPU, against
-numpy's conversions: truncation within 2^-23 relative, exact widening, and
-the stated handling of zeros, FP32 range limits, infinities and NaN."""
+"""The integer-unit helpers of the kernels' hot loops (csrc/fv_device.cuh),
+step by step on the CPU: the FP64 <-> FP32 conversions f32_trunc and f64_of
+against numpy's (truncation within 2^-23 relative, exact widening, the stated
+handling of zeros, FP32 range limits, infinities and NaN), the reciprocal
+recip64 and Markstein's division div64 against the rounded quotient, the
+exponent-field halving half64, and the convergence test |ds| > tol s on the
+bit patterns against the FP64 comparison."""
 import struct
 
 import numpy as np
@@ -103,3 +106,49 @@ def test_reciprocal_and_markstein_division():
             miss += 1
             assert abs(q - exact) <= abs(np.spacing(exact)), (ai, bi)
     assert miss <= len(a) * 2e-3, miss
+
+
+def _half64(v):
+    """The kernels' half64: v/2 on the bit pattern."""
+    b = struct.unpack("<q", struct.pack("<d", v))[0]
+    e = (b >> 52) & 0x7ff
+    sign = b & -0x8000000000000000
+    if e >= 2:
+        r = b if e == 0x7ff else b - (1 << 52)
+    else:
+        r = sign | ((b & 0x7fffffffffffffff) >> 1)
+    return struct.unpack("<d", struct.pack("<q", r))[0]
+
+
+def test_half_on_the_exponent_field():
+    g = np.random.default_rng(4)
+    v = np.concatenate([np.exp(g.uniform(np.log(1e-307), np.log(1e307), 5000)) * g.choice([-1, 1], 5000),
+                        [1.0, -3.0, 2.2250738585072014e-308 * 2, 2.2250738585072014e-308, 1.7976931348623157e308]])
+    for x in v:
+        assert _half64(float(x)) == float(x) / 2, x
+    # subnormals: truncated halving (within one subnormal step)
+    for x in (5e-324, 1e-310, -3e-320):
+        assert abs(_half64(x) - x / 2) <= 5e-324
+    assert _half64(0.0) == 0.0 and str(_half64(-0.0)) == "-0.0"
+    assert _half64(np.inf) == np.inf and _half64(-np.inf) == -np.inf and np.isnan(_half64(np.nan))
+
+
+def _moved_more(ds, s, tol):
+    """The kernels' |ds| > tol s for a power-of-two tol, on the patterns."""
+    q = lambda d: struct.unpack("<q", struct.pack("<d", d))[0]
+    bt, bs = q(tol), q(s)
+    if (bt & 0xfffffffffffff) != 0 or bs < (64 << 52) or bt <= 0:
+        return abs(ds) > tol * s
+    return (q(ds) & 0x7fffffffffffffff) > bs + (bt - (1023 << 52))
+
+
+def test_convergence_test_on_the_patterns():
+    g = np.random.default_rng(5)
+    tol = 2.0 ** -17
+    s = np.exp(g.uniform(np.log(1e-250), np.log(1e250), 3000))
+    for si in s:
+        si = float(si)
+        lim = tol * si
+        for ds in (lim, -lim, np.nextafter(lim, 0), np.nextafter(lim, np.inf), -np.nextafter(lim, np.inf),
+                   lim * g.uniform(0.5, 2.0), 0.0):
+            assert _moved_more(float(ds), si, tol) == (abs(float(ds)) > lim), (ds, si)

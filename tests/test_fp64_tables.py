@@ -275,3 +275,65 @@ def test_log1p_near_the_money_within_one_and_a_half_ulp():
             continue
         worst = max(worst, abs(float((got - ref) / ref)))
     assert worst <= 1.5 * 2.0 ** -52, worst
+
+
+def _f32_trunc(d):
+    """FP64 -> FP32 with the fraction truncated (the kernels' f32_trunc)."""
+    hi = struct.unpack("<Q", struct.pack("<d", d))[0] >> 32
+    lo = struct.unpack("<Q", struct.pack("<d", d))[0] & 0xffffffff
+    e = ((hi >> 20) & 0x7ff) - 896
+    sign = hi & 0x80000000
+    frac = ((hi & 0xfffff) << 3) | (lo >> 29)
+    bits = sign if e <= 0 else (sign | 0x7f800000 if e >= 255 else sign | (e << 23) | frac)
+    return np.frombuffer(struct.pack("<I", bits), dtype=np.float32)[0]
+
+
+def _piece_w(w):
+    """The kernel's piece index for erfcx(w/sqrt2), w >= 0: from the FP32 view
+    z_f = trunc32(w) * 0.70710677f (None: the asymptotic branch)."""
+    zf = np.float32(_f32_trunc(w) * np.float32(0.70710677))
+    b = struct.unpack("<I", struct.pack("<f", zf))[0]
+    if b >= 0x43000000:
+        return None
+    e = (b >> 23) - 127
+    if e >= -1:
+        return 8 + ((e + 1) << 4) + ((b >> 19) & 15)
+    return ((b & 0x7fffff) | 0x800000) >> (19 - e) if e >= -4 else 0
+
+
+def test_w_form_piece_index_and_accuracy_next_to_edges():
+    # erfcx(w/sqrt2): the FP32 view may put z = w/sqrt2 in the neighbouring
+    # piece within ~2^-22 z of an edge; there the interpolant, taken that little
+    # outside its interval (v = w/sqrt2 - c by one FMA), keeps its accuracy
+    mp.mp.dps = 40
+    tab = _table()
+    bounds = [k / 16 for k in range(9)] + [2.0 ** e * (1 + j / 16) for e in range(-1, 7) for j in range(1, 17)]
+    edges = np.array(bounds[1:])
+    rt2 = float(np.sqrt(2.0))
+    g = np.random.default_rng(11)
+    w = np.concatenate([edges * rt2, np.nextafter(edges * rt2, 0), np.nextafter(edges * rt2, 1e3),
+                        edges * rt2 * (1 - 2e-7), edges * rt2 * (1 + 2e-7),
+                        g.uniform(0, 181, 300), [0.0, 5e-324]])
+    inv_rt2 = float(1 / mp.sqrt(2))
+    worst_ext = worst = 0.0
+    for wi in w:
+        wi = float(wi)
+        k = _piece_w(wi)
+        z = mp.mpf(wi) / mp.sqrt(2)
+        if k is None:
+            assert z > 127.99
+            continue
+        assert 0 <= k <= 135
+        a, b = bounds[k], bounds[k + 1]
+        ext = max(float(a - z), float(z - b), 0.0) / max(float(z), 1e-300)
+        worst_ext = max(worst_ext, ext)
+        row = tab[k]
+        v = _fma(wi, inv_rt2, -row[0])
+        p = row[9]
+        for j in range(8, 0, -1):
+            p = _fma(p, v, row[j])
+        ref = mp.exp(z * z) * mp.erfc(z)
+        worst = max(worst, abs(float((p - ref) / ref)))
+    assert worst_ext <= 3e-7, worst_ext
+    # the table's 1.25 ulp plus the rounded constant 1/sqrt2 inside v
+    assert worst <= 2.0 * 2.0 ** -52, worst
