@@ -277,12 +277,13 @@ static void launch_binned(const IvArgs& a, cudaStream_t st) {
 }
 
 // Tile shapes measured on GB300 (16.8 M quotes of the BSM grid, one resident
-// wave of blocks): the FP64 solve runs best with 2 quotes per thread and 4
-// blocks per SM (13.8 ms; 2 x 3 13.9 ms, 1 x 4 14.2 ms, 1 x 5 14.4 ms); the
-// mixed path with 2 quotes per thread, 4 blocks per SM and its FP32
-// iterations in phase 2, where they interleave with the FP64 correction
-// (10.9 ms; 1 or 2 quotes per thread at 3 to 5 blocks per SM within 1.2 %).
-// The FP32 path has no FP64 solve to sort for and stays unbinned.
+// wave of blocks): the FP64 solve runs 2 quotes per thread at 4 blocks per SM
+// (9.39 ms; 1 x 4 9.30 ms, 3 x 4 9.32 ms, 2 x 3 9.45 ms: within 1 %, while
+// 5 blocks per SM would cap the registers at 48 and spill); the mixed path
+// 2 quotes per thread, 4 blocks per SM and its FP32 iterations in phase 2,
+// where they interleave with the FP64 correction (1 or 2 quotes per thread at
+// 3 to 5 blocks per SM within 1.2 % when it was tuned).  The FP32 path has
+// no FP64 solve to sort for and stays unbinned.
 
 template <typename InT, int PREC>
 static void launch_flat_prec(const IvArgs& a, int block, cudaStream_t st) {
