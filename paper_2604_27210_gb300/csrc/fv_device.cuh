@@ -586,14 +586,25 @@ __device__ __forceinline__ bool series_in_log_space(T x, T s) {
   return !(x <= T(-1) && -x < T(1e12) * s * s);
 }
 
-template <typename T>
+//
+// kIntHalf: the exact halvings on the exponent field (integer operations,
+// FP64 issue slots saved) or as multiplications by 1/2 (fewer instructions:
+// faster in the divergent Halley kernels, which are bound by issue rather than
+// by the FP64 pipe); the values are the same.
+template <typename T, bool kIntHalf = true>
+__device__ __forceinline__ T halved(T v) {
+  if constexpr (kIntHalf) return f_half(v);
+  return T(0.5) * v;
+}
+
+template <typename T, bool kIntHalf = true>
 __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e,
                                         T bmax = T(-1), bool log_space = false) {
   o.inv_s = recip(s);
   o.h = x * o.inv_s;
-  o.t = f_half(s);
+  o.t = halved<T, kIntHalf>(s);
   const T h = o.h, t = o.t;
-  o.e = with_e ? f_exp(-f_half(h * h + t * t)) : T(0);
+  o.e = with_e ? f_exp(-halved<T, kIntHalf>(h * h + t * t)) : T(0);
   const bool small = small_t(t) && !comp && (!log_space || series_in_log_space(x, s));
   const bool via_comp = with_e && !comp && !small && has_bound(bmax) && positive(h + t);
   // erfcx of w/sqrt2 with w = -h, h + t or -(h + t)
@@ -610,15 +621,15 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
     }
   } else {
     const T Y2 = f_erfcx_w(t - h);
-    o.B = f_half((comp || via_comp) ? Y1 + Y2 : Y1 - Y2);
+    o.B = halved<T, kIntHalf>((comp || via_comp) ? Y1 + Y2 : Y1 - Y2);
   }
   o.b = via_comp ? bmax - o.e * o.B : o.e * o.B;
 }
 
 // ln of the value nb_eval describes
-template <typename T>
+template <typename T, bool kIntHalf = true>
 __device__ __forceinline__ T nb_log(const NB<T>& v) {
-  return f_log(v.B) - f_half(v.h * v.h + v.t * v.t);
+  return f_log(v.B) - halved<T, kIntHalf>(v.h * v.h + v.t * v.t);
 }
 
 // full normalised Black b(x, s, theta) for any x, s >= 0 (FP64)
@@ -988,7 +999,7 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
   double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
   for (int k = 0; k < kHalleySteps; k++) {
     NB<double> v;
-    nb_eval<double>(x, s, upper, v, true, bmax);
+    nb_eval<double, false>(x, s, upper, v, true, bmax);
     const double g = upper ? c_beta - v.e * v.B : v.b - beta;
     if (g < 0.0) {
       lo = s;
@@ -1044,8 +1055,8 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
   double s = (lo > 0.0 && has_hi) ? 0.5 * (lo + hi) : (has_hi ? 0.5 * hi : fmax(2.0 * lo, 1e-3));
   for (int it = 0; it < 400; it++) {
     NB<double> v;
-    nb_eval<double>(x, s, upper, v, false);
-    const double L = nb_log(v);
+    nb_eval<double, false>(x, s, upper, v, false);
+    const double L = nb_log<double, false>(v);
     // 1/f' = b/b' (lower: times ln^2 b) or (b_max - b)/b' = B sqrt(2 pi): no division
     const double bq = v.B * kSqrt2Pi;
     double f, inv_fp;
