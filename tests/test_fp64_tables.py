@@ -337,3 +337,61 @@ def test_w_form_piece_index_and_accuracy_next_to_edges():
     assert worst_ext <= 3e-7, worst_ext
     # the table's 1.25 ulp plus the rounded constant 1/sqrt2 inside v
     assert worst <= 2.0 * 2.0 ** -52, worst
+
+
+def _b_exact(x, s):
+    """b(x, s) for the call, x <= 0, from mpmath at 40 digits."""
+    x, s = mp.mpf(x), mp.mpf(s)
+    return mp.exp(x / 2) * mp.ncdf(x / s + s / 2) - mp.exp(-x / 2) * mp.ncdf(x / s - s / 2)
+
+
+def test_value_past_the_inflection_point_from_the_complement():
+    # e exp((h+t)^2/2) = e^{ht} = e^{x/2} = b_max, so past the inflection point
+    # (h + t > 0) b = b_max - e [erfcx((h+t)/sqrt2) + erfcx((t-h)/sqrt2)]/2
+    mp.mp.dps = 40
+    g = np.random.default_rng(12)
+    for _ in range(300):
+        x = -float(np.exp(g.uniform(np.log(1e-4), np.log(30))))
+        sc = (2 * -x) ** 0.5
+        s = sc * float(g.uniform(1.0001, 8.0))
+        X, S = mp.mpf(x), mp.mpf(s)
+        h, t = X / S, S / 2
+        e = mp.exp(-(h * h + t * t) / 2)
+        C = (mp.exp(((h + t) / mp.sqrt(2)) ** 2) * mp.erfc((h + t) / mp.sqrt(2))
+             + mp.exp(((t - h) / mp.sqrt(2)) ** 2) * mp.erfc((t - h) / mp.sqrt(2))) / 2
+        b = mp.exp(X / 2) - e * C
+        ref = _b_exact(x, s)
+        assert abs((b - ref) / ref) < mp.mpf(10) ** -30, (x, s)
+
+
+def test_lowest_region_erfcx_difference_moves_s_by_eps_over_x():
+    # In the lowest region the objective is ln b.  For small t the erfcx
+    # difference loses a factor ~|x|/s^2 to cancellation; with FP64 erfcx
+    # values (error 1 ulp each) the error reaches ln b as an absolute error,
+    # which moves s by that error over s (ln b)'.  For |x| >= 1 that is within
+    # a few eps, the claim behind taking the difference there.
+    mp.mp.dps = 40
+    eps = 2.0 ** -52
+
+    def worst_shift(x_lo, x_hi, n, seed):
+        g = np.random.default_rng(seed)
+        worst = 0.0
+        for _ in range(n):
+            x = -float(np.exp(g.uniform(np.log(x_lo), np.log(x_hi))))
+            s = float(np.exp(g.uniform(np.log(1e-3), np.log(0.2))))
+            X, S = mp.mpf(x), mp.mpf(s)
+            h, t = X / S, S / 2
+            z1, z2 = -(h + t) / mp.sqrt(2), (t - h) / mp.sqrt(2)
+            y1 = mp.exp(z1 * z1) * mp.erfc(z1)
+            y2 = mp.exp(z2 * z2) * mp.erfc(z2)
+            # each FP64 erfcx value one ulp off, in the directions that add up
+            lnb_true = mp.log((y1 - y2) / 2)
+            lnb_fp = mp.log((y1 * (1 + eps) - y2 * (1 - eps)) / 2)
+            dlnb = mp.diff(lambda ss: mp.log(_b_exact(x, ss)), S)
+            worst = max(worst, float(abs((lnb_fp - lnb_true) / (S * dlnb)) / eps))
+        return worst
+
+    assert worst_shift(1.0, 20.0, 300, 13) < 4.0
+    # near the money the same difference would move s by hundreds of eps:
+    # there the series stays
+    assert worst_shift(1e-3, 0.1, 60, 14) > 100.0
