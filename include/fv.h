@@ -265,7 +265,10 @@ fv_err fv_stream_plan_destroy(fv_stream_plan* plan);
  * pageable memory works but serialises them).  The batch is cut into chunks
  * that alternate between the plan's two streams: while chunk k solves, chunk
  * k+1's inputs travel to the device and chunk k-1's sigma and status travel
- * back.  The pipeline starts after the work already queued on `stream`, and
+ * back.  Chunks hold chunk_quotes quotes except at the ends: the first three
+ * ramp up (1/8, 1/4, 1/2 of it) so that the first solve starts after a short
+ * copy, and the last ones halve so that the last solve and copy-out are
+ * short.  The pipeline starts after the work already queued on `stream`, and
  * `stream` waits for it, so the outputs are in place once `stream` has
  * completed.  Arguments as fv_implied_vol_ex (contiguous arrays, q may be
  * NULL unless FV_BSM); one call at a time per plan. */

@@ -593,6 +593,23 @@ fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan) {
   return FV_SUCCESS;
 }
 
+}  // extern "C"
+
+// Quotes in chunk k of a host batch with `remaining` quotes left and chunks of
+// up to C: the first three ramp up (C/8, C/4, C/2) so that the first solve
+// starts after a short copy; once at most 2C remain the chunks halve (down to
+// C/8, then the rest) so that the last solve and copy-out are short.
+static int64_t host_chunk(int64_t k, int64_t remaining, int64_t C) {
+  int64_t m = k < 3 ? std::max<int64_t>(C >> (3 - k), 1) : C;
+  if (remaining <= 2 * C && C >= 8) {
+    const int64_t half = (remaining + 1) / 2;
+    m = std::min(m, half > C / 8 ? half : remaining);
+  }
+  return std::min(m, remaining);
+}
+
+extern "C" {
+
 fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solver,
                            fv_precision precision, fv_dtype in_dtype, const void* price,
                            const void* S_or_F, const void* K, const void* T, const void* r,
@@ -615,10 +632,10 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
   cudaError_t ce = cudaEventRecord(plan->ev_start, caller);
   for (int b = 0; b < 2 && ce == cudaSuccess; b++) ce = cudaStreamWaitEvent(plan->st[b], plan->ev_start, 0);
   const int64_t C = plan->chunk;
-  for (int64_t k = 0, off = 0; off < n && ce == cudaSuccess; k++, off += C) {
+  for (int64_t k = 0, off = 0, m = 0; off < n && ce == cudaSuccess; k++, off += m) {
     const int b = (int)(k & 1);
     cudaStream_t s = plan->st[b];
-    const int64_t m = (n - off < C) ? n - off : C;
+    m = host_chunk(k, n - off, C);
     // buffer b's previous chunk finished on this same stream: stream order
     // keeps its outputs' copies ahead of this chunk's inputs
     for (int j = 0; j < 6 && ce == cudaSuccess; j++)

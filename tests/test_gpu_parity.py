@@ -635,7 +635,7 @@ def test_host_streaming_matches_device(fv, torch_dev, solver, prec):
     w = wl.fill_prices(wl.bsm_grid(1000, 300, seed=41), orc.price_f64)
     keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
     host = {k: torch.tensor(w[k]).pin_memory() for k in keys}
-    plan = fv.fv_stream_plan_create(100000)  # 3 chunks of 100,000 quotes
+    plan = fv.fv_stream_plan_create(100000)  # chunks of up to 100,000 quotes, ramped at both ends
     s_h, st_h = plan.implied_vol(fv.FV_BSM, solver, prec, *[host[k] for k in keys])
     torch.cuda.synchronize()
     s_d, st_d = fv.fv_implied_vol_ex(fv.FV_BSM, solver, prec, *_args(torch_dev, w),
