@@ -76,7 +76,8 @@ fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const 
 /* Implied volatility (Section 3 "Implied volatility": fast_implied_volatility
  * for BSM quotes, fast_implied_volatility_black for discounted Black-76 mids;
  * Section 2.2 for the solvers).  FP64 inputs; the status decision, every
- * residual and every Newton step in FP64.
+ * residual and every Newton step in FP64 (their divisions take an FP32
+ * reciprocal refined by FP64 Newton steps).
  *   FV_LBR:    normalised coordinates, four-region initial guess (built in
  *              FP32: it is ~1e-2 off and only seeds the iteration),
  *              three-branch objective, Householder(3) iteration (two steps,
