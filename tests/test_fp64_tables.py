@@ -114,7 +114,8 @@ def _exp_expm1(v, tab):
     t = _fma(v, inv, big)
     k = int(t - big)
     kd = t - big
-    if abs(v) < 0.005:
+    # |v| < 0.005 on the high word, as the kernel tests it
+    if (struct.unpack("<Q", struct.pack("<d", v))[0] >> 32) & 0x7fffffff < 0x3f747ae1:
         k, kd = 0, 0.0
     r = _fma(kd, -hi, v)
     r = _fma(kd, -lo, r)
