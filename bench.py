@@ -181,7 +181,19 @@ def run_path(fv, t, path, out, st):
         raise ValueError(path)
 
 
-LAUNCHES_PER_STEP = {"lbr": 1, "mixed": 1, "fp32": 1, "halley": 2}
+LAUNCHES_PER_STEP = {"lbr": 1, "mixed": 1, "fp32": 1, "halley": 1}
+
+
+def halley_fallback_fraction(fv, torch, t):
+    """Share of the quotes whose eight Halley sweeps fail the convergence test:
+    the workspace arrangement of the same solver leaves the length of its
+    compacted fallback list in the first four bytes of the workspace."""
+    n = t["P"].numel()
+    ws = torch.zeros(fv.fv_workspace_size(fv.FV_HALLEY, n), dtype=torch.uint8, device=t["P"].device)
+    fv.fv_implied_vol_ws(fv.FV_BSM, fv.FV_HALLEY, t["P"], t["S_or_F"], t["K"], t["T"], t["r"],
+                         t["q"], t["flag"], ws)
+    torch.cuda.synchronize()
+    return int(ws[:4].cpu().numpy().view(np.uint32)[0]) / n
 
 
 def time_steps(torch, fn, steps, warmup, world_size):
@@ -377,6 +389,7 @@ def main():
             extras[p] = {"value": ws * n / (max_over_ranks(tm / k, ws) * 1e-3),
                          "ms_per_step": tm / k,
                          "hbm_frac": BYTES_PER_QUOTE * n / (statistics.mean(km) * 1e-3) / 1e9 / hbm_peak}
+        extras.setdefault("halley", {})["fallback_fraction"] = halley_fallback_fraction(fv, torch, t)
         # pricing and Greeks on the same grid
         sig = t["P"].new_tensor(w["sigma_true"])
         for name, fn in (("price", lambda: fv.fv_price(fv.FV_BSM, t["flag"], t["S_or_F"], t["K"],

@@ -1,6 +1,6 @@
-// throughput_probe.cu -- issue rate of FP64 / FP32 FMA and of CUDA math-library
+// bench_fp64_probe.cu -- issue rate of FP64 / FP32 FMA and of CUDA math-library
 // calls on this GPU (independent chains, full occupancy).  Standalone program:
-// python -m paper_2604_27210_gb300.throughput_probe builds and runs it.
+// python bench_fp64_probe.py builds and runs it.
 #include <cstdio>
 #include <cuda_runtime.h>
 

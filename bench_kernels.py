@@ -3,7 +3,7 @@
 Used for profiler captures of a single kernel and for throughput-versus-N
 sweeps.  Prints one JSON line per size:
 
-  python -m paper_2604_27210_gb300.kernel_bench --kernel lbr --workload grid \
+  python bench_kernels.py --kernel lbr --workload grid \
       --n 4194304 --reps 5 --warmup 2
 
 kernels:   lbr, mixed, fp32, halley, halley32, price, greeks, adjoint, chains
@@ -20,7 +20,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -16,7 +16,12 @@
  *    alignment is accepted.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
  *    asynchronous: they launch on `stream` and return; they never synchronise
- *    and, except where stated, allocate nothing.
+ *    and, except where stated, allocate nothing, so they can be captured into
+ *    a CUDA graph.
+ *  - The implied-volatility solvers hand out work in tiles: for batches of
+ *    131,072 quotes or more, the first two elements of out_sigma serve as
+ *    the tile counters while the call runs (a 16-byte memset on `stream`
+ *    precedes the kernel) and receive their own results last.
  *  - Models: FV_BLACK76 takes the forward F and a DISCOUNTED price, and uses
  *    the same r for discounting and inversion (Section 2.4).  FV_BLACK_SCHOLES
  *    takes the spot S with q = 0.  FV_BSM takes S and a continuous dividend
@@ -84,14 +89,13 @@ fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const 
  *              plus a third wherever the second still moved sigma; the
  *              step's second-order correction factor in FP32).
  *   FV_HALLEY: Brenner-Subrahmanyam guess, eight Halley sweeps on the
- *              residual, bisection with Newton steps on the LBR's
- *              transformed residual for the quotes that fail the
- *              convergence test.  Uses a library-owned device workspace,
- *              one per device, allocated on the first call for a given size
- *              (make that first call before capturing the stream into a CUDA
- *              graph).  Halley calls whose GPU work may overlap (on different
- *              streams) must not share it: give each its own workspace
- *              through fv_implied_vol_ws.
+ *              residual, and for the quotes that fail the convergence test a
+ *              fallback inside the sweeps' bracket: the LBR's rational
+ *              guess, then Householder(3) steps on the LBR's transformed
+ *              objective, each replaced by a bisection when it would leave
+ *              the bracket.  The failures of each tile of quotes are
+ *              compacted in shared memory and solved by the same kernel: no
+ *              workspace, no second launch.
  * out_sigma: FP64, NaN where status != FV_Q_OK.  status: uint8 per quote. */
 fv_err fv_implied_vol(fv_model model, fv_solver solver, const double* price, const double* S_or_F,
                       const double* K, const double* T, const double* r, const double* q,
@@ -104,9 +108,12 @@ size_t fv_workspace_size(fv_solver solver, int64_t n);
 
 /* fv_implied_vol with a caller-owned device workspace of at least
  * fv_workspace_size(solver, n) bytes, 16-byte aligned; allocates nothing.
- * The workspace holds the compacted list of quotes handed to the bisection
- * fallback (Section 2.2, Halley item); its contents are undefined after the
- * call, and two calls in flight must not share it. */
+ * With FV_HALLEY the sweep kernel appends the quotes that fail the
+ * convergence test to a compacted list in the workspace (Section 2.2, Halley
+ * item) and a second kernel runs the same fallback as fv_implied_vol over the
+ * whole list; the results are those of fv_implied_vol.  The workspace's
+ * contents are undefined after the call, and two calls in flight must not
+ * share it.  With FV_LBR the workspace is not used (its size is 0). */
 fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
                          const double* S_or_F, const double* K, const double* T, const double* r,
                          const double* q, const int8_t* flag, int64_t n, double* out_sigma,
@@ -126,7 +133,7 @@ fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
  * e^{x/2} Phi(h+t) - e^{-x/2} Phi(h-t) with plain FP32 normal CDFs, and an
  * FP32 bisection fallback on the quotes that fail the convergence test (about
  * five digits where the normalised vega exceeds 1e-8; the plain residual
- * loses the deep wings).  It uses the library-owned workspace like
+ * loses the deep wings), its fallback in the same kernel as in
  * fv_implied_vol.  FV_HALLEY with FV_MIXED is FV_ERR_UNSUPPORTED.
  * in_dtype says whether price, S_or_F, K, T, r, q point to double or float.
  * out_sigma is always FP64. */
@@ -140,8 +147,7 @@ fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precisio
  * strides for price, S_or_F, K, T, r, q and flag, in that order: quote i reads
  * element i * stride, so 0 broadcasts one value (a scalar spot, rate or
  * maturity for a whole strip) and 1 is a contiguous array.  Negative strides
- * are FV_ERR_ARG.  Outputs stay contiguous.  Otherwise as fv_implied_vol_ex
- * (the Halley solver takes the library-owned workspace). */
+ * are FV_ERR_ARG.  Outputs stay contiguous.  Otherwise as fv_implied_vol_ex. */
 fv_err fv_implied_vol_strided(fv_model model, fv_solver solver, fv_precision precision,
                               fv_dtype in_dtype, const void* price, const void* S_or_F,
                               const void* K, const void* T, const void* r, const void* q,
@@ -255,7 +261,7 @@ fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
 
 /* ---- host-resident batches: copies overlapped with the solve ----------- */
 /* A stream plan holds device staging for two chunks of up to chunk_quotes
- * quotes (inputs, outputs and a Halley workspace) and two CUDA streams.
+ * quotes (inputs and outputs) and two CUDA streams.
  * Created once (allocates device memory); used by fv_implied_vol_host. */
 typedef struct fv_stream_plan fv_stream_plan;
 fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan);
@@ -283,12 +289,13 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
 /* The paper has no counterpart to this entry point; it serves callers that
  * may not allocate device memory (a host process that pre-reserves all of it,
  * an allocator that forbids raw cudaMalloc, a latency-critical path that
- * cannot take a first-call allocation or the synchronisation of freeing one).
- * It runs the Halley x8 solver with its bisection fallback exactly as
- * fv_implied_vol does, but the fallback list lives in a scratch array
- * compiled into the library: device global memory of about 20 bytes per
- * quote of capacity (about 5 MiB), held by every GPU that loads the library
- * until the process exits.
+ * cannot take a first-call allocation or the synchronisation of freeing one)
+ * and that want the Halley solver in its compacted-list arrangement.  It
+ * runs the Halley x8 solver with its fallback exactly as fv_implied_vol_ws
+ * does (the same results as fv_implied_vol), but the fallback list lives in
+ * a scratch array compiled into the library: device global memory of about
+ * 20 bytes per quote of capacity (about 5 MiB), held by every GPU that loads
+ * the library until the process exits.
  *  - n may not exceed FV_NOALLOC_MAX_QUOTES (FV_ERR_ARG otherwise, nothing
  *    launched); split larger batches.
  *  - The first call on each device looks up the array's device address
@@ -298,7 +305,7 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
  *    All calls on a device share the one array, so two calls whose GPU work
  *    overlaps (different streams, or different threads) race and give wrong
  *    results: serialise them on one stream.
- *  - Calls cudaMalloc, cudaFree and no allocating routine.
+ *  - Calls no cudaMalloc, no cudaFree and no other allocating routine.
  * Arguments, outputs and errors as fv_implied_vol with FV_HALLEY. */
 #define FV_NOALLOC_MAX_QUOTES 262144
 fv_err fv_implied_vol_halley_noalloc(fv_model model, const double* price, const double* S_or_F,

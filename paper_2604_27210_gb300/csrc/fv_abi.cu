@@ -66,44 +66,13 @@ fv_err check_iv_args(const char* fn, int model, int solver, const void* P, const
   return FV_SUCCESS;
 }
 
-// library-owned Halley workspace, one per device, grown on demand
-struct WsCache {
-  std::mutex mu;
-  void* ptr[64] = {nullptr};
-  size_t bytes[64] = {0};
-};
-WsCache g_ws;
-
-fv_err cached_workspace(size_t need, void** out) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return fail(FV_ERR_UNSUPPORTED, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lk(g_ws.mu);
-  if (g_ws.bytes[dev] < need) {
-    if (g_ws.ptr[dev]) {
-      // the previous buffer may still be in use by queued work on any stream
-      cudaDeviceSynchronize();
-      cudaFree(g_ws.ptr[dev]);
-      g_ws.ptr[dev] = nullptr;
-      g_ws.bytes[dev] = 0;
-    }
-    void* p = nullptr;
-    const cudaError_t e = cudaMalloc(&p, need);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(FV_ERR_NOMEM, "Halley workspace of %zu bytes: %s", need, cudaGetErrorString(e));
-    }
-    g_ws.ptr[dev] = p;
-    g_ws.bytes[dev] = need;
-  }
-  *out = g_ws.ptr[dev];
-  return FV_SUCCESS;
-}
-
+// ws_path: the caller passed a workspace (fv_implied_vol_ws); the Halley
+// solver then compacts its failures there and runs the fallback as a second
+// kernel.  Otherwise every solver runs in one kernel without a workspace.
 fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const void* P,
               const void* SF, const void* K, const void* T, const void* r, const void* q,
               const int8_t* flag, int64_t n, double* sigma, uint8_t* status, void* ws,
-              size_t ws_bytes, bool use_cache, void* stream, const int64_t* strides = nullptr) {
+              size_t ws_bytes, bool ws_path, void* stream, const int64_t* strides = nullptr) {
   fv_err e = check_iv_args(fn, model, solver, P, SF, K, T, r, q, flag, n, sigma, status);
   if (e != FV_SUCCESS || n == 0) return e;
   if (strides)
@@ -111,10 +80,8 @@ fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const v
       if (strides[k] < 0) return fail(FV_ERR_ARG, "%s: stride %d is negative", fn, k);
   if (solver == FV_HALLEY && prec == fvk::P_MIXED)
     return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 or FP32", fn);
-  if (solver == FV_HALLEY && prec == fvk::P_FP32 && !use_cache)
-    return fail(FV_ERR_UNSUPPORTED, "%s: FP32 Halley takes the library workspace", fn);
   const size_t need = solver == FV_HALLEY ? fvk::halley_workspace_bytes(n) : 0;
-  if (solver == FV_HALLEY && !use_cache) {
+  if (solver == FV_HALLEY && ws_path) {
     if (ws == nullptr) return fail(FV_ERR_ARG, "%s: workspace is NULL", fn);
     if (ws_bytes < need)
       return fail(FV_ERR_ARG, "%s: workspace of %zu bytes, %zu needed", fn, ws_bytes, need);
@@ -139,9 +106,13 @@ fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const v
   for (int k = 0; k < 7; k++) a.st[k] = strides ? strides[k] : 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (solver == FV_LBR) return cuda_result(fvk::launch_iv_lbr(a, prec, st), fn);
-  if (use_cache && (e = cached_workspace(need, &ws)) != FV_SUCCESS) return e;
-  if (prec == fvk::P_FP32) return cuda_result(fvk::launch_iv_halley32(a, ws, st), fn);
-  return cuda_result(fvk::launch_iv_halley(a, ws, st), fn);
+  if (ws_path)
+    return cuda_result(prec == fvk::P_FP32 ? fvk::launch_iv_halley32_ws(a, ws, st)
+                                           : fvk::launch_iv_halley_ws(a, ws, st),
+                       fn);
+  return cuda_result(prec == fvk::P_FP32 ? fvk::launch_iv_halley32(a, st)
+                                         : fvk::launch_iv_halley(a, st),
+                     fn);
 }
 
 }  // namespace
@@ -248,7 +219,7 @@ fv_err fv_implied_vol(fv_model model, fv_solver solver, const double* price, con
                       const int8_t* flag, int64_t n, double* out_sigma, uint8_t* status,
                       void* stream) {
   return run_iv("fv_implied_vol", model, solver, fvk::P_FP64, false, price, S_or_F, K, T, r, q,
-                flag, n, out_sigma, status, nullptr, 0, true, stream);
+                flag, n, out_sigma, status, nullptr, 0, false, stream);
 }
 
 size_t fv_workspace_size(fv_solver solver, int64_t n) {
@@ -261,7 +232,7 @@ fv_err fv_implied_vol_ws(fv_model model, fv_solver solver, const double* price,
                          const double* q, const int8_t* flag, int64_t n, double* out_sigma,
                          uint8_t* status, void* workspace, size_t workspace_bytes, void* stream) {
   return run_iv("fv_implied_vol_ws", model, solver, fvk::P_FP64, false, price, S_or_F, K, T, r, q,
-                flag, n, out_sigma, status, workspace, workspace_bytes, false, stream);
+                flag, n, out_sigma, status, workspace, workspace_bytes, true, stream);
 }
 
 fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precision,
@@ -276,7 +247,7 @@ fv_err fv_implied_vol_ex(fv_model model, fv_solver solver, fv_precision precisio
   if (solver == FV_HALLEY && precision == FV_MIXED)
     return fail(FV_ERR_UNSUPPORTED, "%s: the Halley solver runs in FP64 or FP32", fn);
   return run_iv(fn, model, solver, (int)precision, in_dtype == FV_DTYPE_F32, price, S_or_F, K, T, r,
-                q, flag, n, out_sigma, status, nullptr, 0, true, stream);
+                q, flag, n, out_sigma, status, nullptr, 0, false, stream);
 }
 
 fv_err fv_implied_vol_strided(fv_model model, fv_solver solver, fv_precision precision,
@@ -291,7 +262,7 @@ fv_err fv_implied_vol_strided(fv_model model, fv_solver solver, fv_precision pre
     return fail(FV_ERR_ARG, "%s: unknown input dtype %d", fn, (int)in_dtype);
   if (n > 0) FV_REQUIRE(strides, "strides", fn);
   return run_iv(fn, model, solver, (int)precision, in_dtype == FV_DTYPE_F32, price, S_or_F, K, T, r,
-                q, flag, n, out_sigma, status, nullptr, 0, true, stream, strides);
+                q, flag, n, out_sigma, status, nullptr, 0, false, stream, strides);
 }
 
 fv_err fv_greeks(fv_model model, const int8_t* flag, const double* S_or_F, const double* K,
@@ -535,8 +506,6 @@ struct fv_stream_plan {
   int8_t* flag[2];
   double* sigma[2];
   uint8_t* status[2];
-  void* ws[2];
-  size_t ws_bytes;
   cudaStream_t st[2];
   cudaEvent_t ev_start, ev_end[2];
 };
@@ -552,7 +521,6 @@ fv_err fv_stream_plan_destroy(fv_stream_plan* p) {
     if (p->flag[b]) cudaFree(p->flag[b]);
     if (p->sigma[b]) cudaFree(p->sigma[b]);
     if (p->status[b]) cudaFree(p->status[b]);
-    if (p->ws[b]) cudaFree(p->ws[b]);
     if (p->st[b]) cudaStreamDestroy(p->st[b]);
     if (p->ev_end[b]) cudaEventDestroy(p->ev_end[b]);
   }
@@ -571,7 +539,6 @@ fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan) {
   fv_stream_plan* p = new fv_stream_plan();
   memset(p, 0, sizeof(*p));
   p->chunk = chunk_quotes;
-  p->ws_bytes = fvk::halley_workspace_bytes(chunk_quotes);
   const size_t c = (size_t)chunk_quotes;
   cudaError_t ce = cudaSuccess;
   for (int b = 0; b < 2 && ce == cudaSuccess; b++) {
@@ -579,7 +546,6 @@ fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan) {
     if (ce == cudaSuccess) ce = cudaMalloc(&p->flag[b], c);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->sigma[b], c * 8);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->status[b], c);
-    if (ce == cudaSuccess) ce = cudaMalloc(&p->ws[b], p->ws_bytes);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->st[b], cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_end[b], cudaEventDisableTiming);
   }
@@ -662,9 +628,9 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
     if (solver == FV_LBR)
       ce = fvk::launch_iv_lbr(a, (int)precision, s);
     else if (precision == FV_FP32)
-      ce = fvk::launch_iv_halley32(a, plan->ws[b], s);
+      ce = fvk::launch_iv_halley32(a, s);
     else
-      ce = fvk::launch_iv_halley(a, plan->ws[b], s);
+      ce = fvk::launch_iv_halley(a, s);
     if (ce == cudaSuccess)
       ce = cudaMemcpyAsync(out_sigma + off, plan->sigma[b], m * 8, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess)

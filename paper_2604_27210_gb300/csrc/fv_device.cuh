@@ -783,7 +783,8 @@ __device__ __forceinline__ double guarded<double>(double s, double ds) {
 // relative error enters the step at order nu^2.  Returns the step ds (0 where
 // it is not finite); the FP64 solver iterates it, the mixed solver applies it
 // once after its FP32 iterations.
-__device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg) {
+__device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg,
+                                               double* nu_out = nullptr) {
   NB<double> v;
   nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax, reg == 0);
   const float hf = f32_trunc(v.h), sf = f32_trunc(s);
@@ -814,6 +815,7 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
       h3 = h2 * h2 + du + qf * h2;
     }
   }
+  if (nu_out) *nu_out = nu;
   const float nf = f32_trunc(nu);
   const float phi = nf * (-0.5f * h2 - h3 * nf * (1.0f / 6.0f)) / (1.0f + nf * (h2 + h3 * nf * (1.0f / 6.0f)));
   const double ds = isfinite(phi) ? fma(nu, f64_of(phi), nu) : nu;
@@ -982,6 +984,17 @@ __device__ __forceinline__ double lbr_solve64(const Reduced<double>& q, float g,
 // ---------------------------------------------------------------------------
 constexpr int kHalleySteps = 8;
 constexpr double kHalleyConvTol = 1e-10;
+// The convergence test reads the relative Newton distance of the last sweep
+// (at s_7).  Halley's iteration converges cubically, so from a distance d_k
+// at sweep k it can reach the tolerance by then only if
+// d_k <= kHalleyConvTol^(3^-(7-k)); a quote beyond that bound after its
+// second sweep or later goes to the fallback at once instead of spending the
+// sweeps left (the fallback returns the same root; a quote the bound sends
+// there too early only trades its remaining sweeps for the fallback's two or
+// three evaluations).
+__constant__ const double kHalleyReach[kHalleySteps] = {
+    0.9895267209580416, 0.9689080827862817, 0.9095943135230796, 0.7525636023261612,
+    0.4262158829015324, 0.07742636826811272, 0.0004641588833612781, 1e-10};
 
 struct HalleyOut {
   double s, lo, hi;
@@ -1014,6 +1027,7 @@ __device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double 
     // and its distance to the root relative to s (the convergence test)
     const double nu = g * (kSqrt2Pi * inv_e(v.e));
     nerr = fabs(nu) * v.inv_s;
+    if (k >= 1 && k < kHalleySteps - 1 && !(nerr <= kHalleyReach[k])) break;
     // Halley: ds = -2 g g' / (2 g'^2 - g g'') = -nu / (1 - nu u / 2), u = b''/b';
     // the factor 1 / (1 - nu u / 2) only shapes the step (its rounding enters at
     // order nu^2), so it is formed in FP32
@@ -1084,6 +1098,61 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
     const double ds = sn - s;
     s = sn;
     if (lo > 0.0 && isfinite(hi) && (fabs(ds) <= 2.0 * eps * s || hi - lo <= 4.0 * eps * hi)) break;
+  }
+  return s;
+}
+
+// The fallback of the Halley solver for a quote whose sweeps failed the
+// convergence test (Section 2.2 sends those quotes to a bracketing fallback).
+// The sweeps leave the root inside [lo, hi] (hi = +inf when no sweep landed
+// above it).  The fallback starts from the LBR's four-region rational guess,
+// moved into the bracket when it falls outside, and takes Householder(3)
+// steps on the LBR objective of the guess's region (the transformed residuals
+// under which Newton-type steps do not crawl in the wings).  A step that
+// would leave the bracket is replaced by a bisection (or, without an upper
+// end, by doubling s); the sign of the Newton step nu = -g/g' tells which end
+// s replaces.  It stops after a Householder step, not the first, that moved s
+// by at most 2^-17 relative (the LBR's criterion: with quartic convergence the
+// remaining error is far below an ulp) or when the bracket has shrunk to a
+// few ulp: two or three evaluations from the guess, against ~50 halvings of
+// a plain bisection.
+__device__ __forceinline__ double halley_fallback64(Reduced<double> q, double lo, double hi) {
+  int reg = 1;
+  double s;
+  {
+    // region and guess as the FP64 LBR solver takes them: FP32 where FP32
+    // holds the quote's scales, FP64 otherwise
+    Reduced<float> q32 = reduced32(q);
+    int reg32 = 1;
+    const float g32 = lbr_guess<float>(q32, reg32);
+    if (q.bmax > 1e-20 && g32 > 1e-30f && g32 < 1e30f) {
+      s = f64_of(g32);
+      reg = reg32;
+    } else {
+      s = lbr_guess<double>(q, reg);
+    }
+  }
+  const bool has_hi = bits_finite(hi);
+  if (!(s > lo && s < hi)) s = has_hi ? 0.5 * (lo + hi) : 2.0 * fmax(lo, 0.5 * s);
+  wing_logs<double>(q, reg);
+  for (int it = 0; it < 64; it++) {
+    double nu;
+    const double ds = hh3_ds_mixed(q, s, reg, &nu);
+    // nu > 0: the root lies above s (a NaN step comes from b underflowing at
+    // an s far below the root)
+    if (nu > 0.0 || nu != nu)
+      lo = s;
+    else if (nu < 0.0)
+      hi = s;
+    else
+      break;  // the residual vanished: s is the root
+    double sn = s + ds;
+    const bool inside = sn > lo && sn < hi && ds != 0.0;
+    if (!inside) sn = bits_finite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
+    const bool done = (inside && it >= 1 && !moved_more(ds, sn, 0x1p-17)) ||
+                      (bits_finite(hi) && hi - lo <= 0x1p-50 * hi);
+    s = sn;
+    if (done) break;
   }
   return s;
 }

@@ -27,13 +27,23 @@ struct IvArgs {
 int sm_count();
 int grid_for(int64_t n, int block, int per_sm);
 
+// LBR: batches of kSmallBatch quotes or more run the region-binned kernel with
+// dynamic tiles, whose counters are the first two sigma outputs (zeroed on
+// `st` before the launch)
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
 
-// Halley workspace: [count u32 | pad to 16][idx u32 x n | pad to 16][lo f64 x n][hi f64 x n]
+// Halley x8 with the fallback inside the same kernel (tile-local compaction
+// in shared memory): no workspace.  Large batches zero the first two sigma
+// outputs on `st` before the launch (the dynamic tile counters).
+cudaError_t launch_iv_halley(const IvArgs& a, cudaStream_t st);
+// Halley x8 in FP32 on the plain-Phi residual, the same arrangement
+cudaError_t launch_iv_halley32(const IvArgs& a, cudaStream_t st);
+// The same solvers with the failures compacted into a caller's workspace and
+// a second kernel for the fallback.  Workspace layout:
+// [count u32 | pad to 16][idx u32 x n | pad to 16][lo f64 x n][hi f64 x n]
 size_t halley_workspace_bytes(int64_t n);
-cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st);
-// Halley x8 in FP32 on the plain-Phi residual (same workspace layout)
-cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st);
+cudaError_t launch_iv_halley_ws(const IvArgs& a, void* ws, cudaStream_t st);
+cudaError_t launch_iv_halley32_ws(const IvArgs& a, void* ws, cudaStream_t st);
 
 cudaError_t launch_price(int model, const int8_t* flag, const double* SF, const double* K,
                          const double* T, const double* r, const double* q, const double* sigma,

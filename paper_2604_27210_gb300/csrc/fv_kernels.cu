@@ -93,6 +93,70 @@ __device__ __forceinline__ void load_quote(const IvArgs& a, int64_t i, double& P
 }
 
 // ---------------------------------------------------------------------------
+// Tile scheduling of the persistent tiled kernels
+//
+// Static (ctr == nullptr): block b solves tile b, one tile per block (small
+// batches, where the grid covers the batch).  Dynamic: one resident wave of
+// blocks claims tiles from an atomic counter, so that the blocks that drew
+// cheap tiles take more of them and every SM finishes at about the same time
+// (a static round-robin leaves the SMs' totals a few per cent apart).  The
+// two 64-bit counters -- the next tile, and the blocks that have finished --
+// live in the first two outputs sigma[0], sigma[1] (8-byte aligned doubles),
+// which the launcher zeroes on the stream before the launch.  Tiles cover
+// quotes [kHead, n); the head quotes [0, kHead), among them sigma[0..1], are
+// solved by the last block to finish, after every other block has stopped
+// using the counters, so the counters cost no memory of their own.  No block
+// ever waits for another.
+// ---------------------------------------------------------------------------
+constexpr int64_t kHead = 32;
+
+struct TileSched {
+  unsigned long long* ctr;  // nullptr: static
+  int64_t n_tiles;          // tiles after the head
+  int64_t head;             // kHead (dynamic) or 0 (static)
+};
+
+static TileSched make_sched(const IvArgs& a, int tile, bool dynamic) {
+  TileSched t;
+  t.ctr = dynamic ? reinterpret_cast<unsigned long long*>(a.sigma) : nullptr;
+  t.head = dynamic ? kHead : 0;
+  t.n_tiles = (a.n - t.head + tile - 1) / tile;
+  return t;
+}
+
+// Runs body(first quote, quotes in the tile) for every tile this block takes.
+// Every thread of the block calls it; body may use __syncthreads().
+template <typename Body>
+__device__ __forceinline__ void for_each_tile(const TileSched& ts, int tile, int64_t n,
+                                              const Body& body) {
+  __shared__ unsigned long long s_tile;
+  __shared__ int s_last;
+  if (ts.ctr == nullptr) {
+    const int64_t base = (int64_t)blockIdx.x * tile;
+    if (base < n) body(base, (int)min((int64_t)tile, n - base));
+    return;
+  }
+  for (;;) {
+    __syncthreads();  // the previous tile's readers of s_tile are done
+    if (threadIdx.x == 0) s_tile = atomicAdd(ts.ctr, 1ULL);
+    __syncthreads();
+    const int64_t t = (int64_t)s_tile;
+    if (t >= ts.n_tiles) break;
+    const int64_t base = ts.head + t * tile;
+    body(base, (int)min((int64_t)tile, n - base));
+  }
+  if (threadIdx.x == 0) s_last = atomicAdd(ts.ctr + 1, 1ULL) == (unsigned long long)gridDim.x - 1;
+  __syncthreads();
+  if (s_last) body(0, (int)min(ts.head, n));
+}
+
+// zero the counters of a dynamic schedule on the launch stream
+static cudaError_t reset_sched(const TileSched& ts, cudaStream_t st) {
+  if (ts.ctr == nullptr) return cudaSuccess;
+  return cudaMemsetAsync(ts.ctr, 0, 2 * sizeof(unsigned long long), st);
+}
+
+// ---------------------------------------------------------------------------
 // implied volatility, LBR: FP64, mixed (FP32 bulk + one FP64 HH3 step), FP32
 // ---------------------------------------------------------------------------
 template <typename InT, int PREC>
@@ -254,26 +318,30 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<Q>& sm, int model, const
 }
 
 template <typename InT, int PREC, int Q, int MINB, bool LATE32>
-__global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a) {
+__global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, TileSched ts) {
   __shared__ BinSmem<Q> sm;
-  constexpr int TILE = kBinThreads * Q;
-  for (int64_t base = (int64_t)blockIdx.x * TILE; base < a.n; base += (int64_t)gridDim.x * TILE) {
+  for_each_tile(ts, kBinThreads * Q, a.n, [&](int64_t base, int count) {
     auto load = [&](int li, double& P, double& SF, double& K, double& T, double& r, double& q,
                     int& flag) {
-      const int64_t i = base + li;
-      if (i >= a.n) return false;
-      load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+      if (li >= count) return false;
+      load_quote<InT>(a, base + li, P, SF, K, T, r, q, flag);
       return true;
     };
     lbr_binned_tile<PREC, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
-  }
+  });
 }
 
+// binned batches are large (>= kSmallBatch quotes): dynamic tiles over one
+// resident wave
 template <typename InT, int PREC, int Q, int MINB, bool LATE32>
-static void launch_binned(const IvArgs& a, cudaStream_t st) {
+static cudaError_t launch_binned(const IvArgs& a, cudaStream_t st) {
   constexpr auto kernel = k_iv_lbr_binned<InT, PREC, Q, MINB, LATE32>;
+  const TileSched ts = make_sched(a, kBinThreads * Q, true);
+  const cudaError_t e = reset_sched(ts, st);
+  if (e != cudaSuccess) return e;
   const int grid = persistent_grid<kernel>(a.n, kBinThreads * Q, kBinThreads);
-  kernel<<<grid, kBinThreads, 0, st>>>(a);
+  kernel<<<grid, kBinThreads, 0, st>>>(a, ts);
+  return cudaGetLastError();
 }
 
 // Tile shapes measured on GB300 (16.8 M quotes of the BSM grid, one resident
@@ -310,19 +378,202 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
       launch_flat<double>(a, prec, block, st);
     return cudaGetLastError();
   }
-  if (a.f32_inputs) {
-    if (prec == P_FP64) launch_binned<float, P_FP64, 2, 4, false>(a, st);
-    else launch_binned<float, P_MIXED, 2, 4, true>(a, st);
-  } else {
-    if (prec == P_FP64) launch_binned<double, P_FP64, 2, 4, false>(a, st);
-    else launch_binned<double, P_MIXED, 2, 4, true>(a, st);
-  }
-  return cudaGetLastError();
+  if (a.f32_inputs)
+    return prec == P_FP64 ? launch_binned<float, P_FP64, 2, 4, false>(a, st)
+                          : launch_binned<float, P_MIXED, 2, 4, true>(a, st);
+  return prec == P_FP64 ? launch_binned<double, P_FP64, 2, 4, false>(a, st)
+                        : launch_binned<double, P_MIXED, 2, 4, true>(a, st);
 }
 
 // ---------------------------------------------------------------------------
-// implied volatility, Halley x8 + compacted bisection fallback
+// implied volatility, Halley x8 + fallback on the quotes that fail the
+// convergence test (Section 2.2)
+//
+// Two arrangements of the same per-quote arithmetic:
+//  - tiled (fv_implied_vol, the stream plan): a block sweeps a tile of quotes,
+//    compacts the tile's failures into shared memory and runs the fallback
+//    on them with every thread of the block, so the fallback needs no device
+//    workspace and no second launch;
+//  - workspace (fv_implied_vol_ws, the no-allocation entry point): the sweep
+//    kernel appends the failures to a compacted list in a device workspace
+//    and a second kernel runs the fallback over the whole list.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ Reduced<double> reduced_of(double beta, double x, double bmax,
+                                                      double ln_beta) {
+  Reduced<double> q;
+  q.beta = beta;
+  q.x = x;
+  q.bmax = bmax;
+  q.c_beta = bmax - beta;
+  q.ln_beta = ln_beta;
+  q.inv_ln_beta = 0.0;
+  q.ln_c_beta = 0.0;
+  return q;
+}
+
+template <int THREADS, int Q>
+struct HalleySmem {
+  // the tile's quotes that failed the convergence test: reduced quote,
+  // maturity, the sweeps' bracket and the quote's place in the tile
+  double beta[THREADS * Q], x[THREADS * Q], bmax[THREADS * Q], lnb[THREADS * Q], T[THREADS * Q],
+      lo[THREADS * Q], hi[THREADS * Q];
+  unsigned short li[THREADS * Q];
+  int n;
+};
+
+template <typename InT, int THREADS, int Q>
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled(IvArgs a, TileSched ts) {
+  __shared__ HalleySmem<THREADS, Q> sm;
+  for_each_tile(ts, THREADS * Q, a.n, [&](int64_t base, int count) {
+    if (threadIdx.x == 0) sm.n = 0;
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < Q; k++) {
+      const int li = k * THREADS + threadIdx.x;
+      if (li >= count) break;
+      const int64_t i = base + li;
+      double P, SF, K, T, r, q;
+      int flag;
+      load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+      const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+      a.status[i] = (uint8_t)nq.status;
+      double sigma = qnan();
+      if (nq.status == Q_OK) {
+        if (!nq.solve) {
+          sigma = 0.0;
+        } else {
+          const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax);
+          if (h.converged) {
+            sigma = h.s * rsqrt(T);
+          } else {
+            const Reduced<double> q64 = reduced64(nq);
+            const int j = atomicAdd(&sm.n, 1);
+            sm.beta[j] = q64.beta;
+            sm.x[j] = q64.x;
+            sm.bmax[j] = q64.bmax;
+            sm.lnb[j] = q64.ln_beta;
+            sm.T[j] = T;
+            sm.lo[j] = h.lo;
+            sm.hi[j] = h.hi;
+            sm.li[j] = (unsigned short)li;
+            continue;  // sigma comes from the fallback
+          }
+        }
+      }
+      a.sigma[i] = sigma;
+    }
+    __syncthreads();
+    const int nf = sm.n;
+    for (int j = threadIdx.x; j < nf; j += THREADS) {
+      const double s = halley_fallback64(reduced_of(sm.beta[j], sm.x[j], sm.bmax[j], sm.lnb[j]),
+                                         sm.lo[j], sm.hi[j]);
+      a.sigma[base + sm.li[j]] = s * rsqrt(sm.T[j]);
+    }
+    __syncthreads();
+  });
+}
+
+template <int THREADS, int Q>
+struct Halley32Smem {
+  float beta[THREADS * Q], c_beta[THREADS * Q], x[THREADS * Q], lo[THREADS * Q], hi[THREADS * Q];
+  double T[THREADS * Q];
+  unsigned short li[THREADS * Q];
+  int n;
+};
+
+template <typename InT, int THREADS, int Q>
+__global__ void __launch_bounds__(THREADS) k_iv_halley32_tiled(IvArgs a, TileSched ts) {
+  __shared__ Halley32Smem<THREADS, Q> sm;
+  for_each_tile(ts, THREADS * Q, a.n, [&](int64_t base, int count) {
+    if (threadIdx.x == 0) sm.n = 0;
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < Q; k++) {
+      const int li = k * THREADS + threadIdx.x;
+      if (li >= count) break;
+      const int64_t i = base + li;
+      double P, SF, K, T, r, q;
+      int flag;
+      load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+      const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+      a.status[i] = (uint8_t)nq.status;
+      double sigma = qnan();
+      if (nq.status == Q_OK) {
+        if (!nq.solve) {
+          sigma = 0.0;
+        } else {
+          const float b32 = (float)nq.beta_otm, c32 = (float)(nq.bmax - nq.beta_otm),
+                      x32 = (float)nq.x_otm;
+          const Halley32Out h = halley32_solve(b32, c32, x32);
+          if (h.converged) {
+            sigma = (double)h.s * rsqrt(T);
+          } else {
+            const int j = atomicAdd(&sm.n, 1);
+            sm.beta[j] = b32;
+            sm.c_beta[j] = c32;
+            sm.x[j] = x32;
+            sm.lo[j] = h.lo;
+            sm.hi[j] = h.hi;
+            sm.T[j] = T;
+            sm.li[j] = (unsigned short)li;
+            continue;
+          }
+        }
+      }
+      a.sigma[i] = sigma;
+    }
+    __syncthreads();
+    const int nf = sm.n;
+    for (int j = threadIdx.x; j < nf; j += THREADS) {
+      const float s = bisect32_fallback(sm.beta[j], sm.c_beta[j], sm.x[j], sm.lo[j], sm.hi[j]);
+      a.sigma[base + sm.li[j]] = (double)s * rsqrt(sm.T[j]);
+    }
+    __syncthreads();
+  });
+}
+
+// Small batches: 64-thread blocks, one tile each (as many SMs as the batch can
+// fill); large ones: 256-thread blocks of two quotes per thread, dynamic tiles
+// over one resident wave.
+template <typename InT>
+static cudaError_t launch_halley64_tiled(const IvArgs& a, cudaStream_t st) {
+  if (a.n < kSmallBatch) {
+    const TileSched ts = make_sched(a, 64, false);
+    k_iv_halley_tiled<InT, 64, 1><<<(unsigned)ts.n_tiles, 64, 0, st>>>(a, ts);
+    return cudaGetLastError();
+  }
+  constexpr auto kernel = k_iv_halley_tiled<InT, 256, 2>;
+  const TileSched ts = make_sched(a, 512, true);
+  const cudaError_t e = reset_sched(ts, st);
+  if (e != cudaSuccess) return e;
+  kernel<<<persistent_grid<kernel>(a.n, 512, 256), 256, 0, st>>>(a, ts);
+  return cudaGetLastError();
+}
+
+template <typename InT>
+static cudaError_t launch_halley32_tiled(const IvArgs& a, cudaStream_t st) {
+  if (a.n < kSmallBatch) {
+    const TileSched ts = make_sched(a, 64, false);
+    k_iv_halley32_tiled<InT, 64, 1><<<(unsigned)ts.n_tiles, 64, 0, st>>>(a, ts);
+    return cudaGetLastError();
+  }
+  constexpr auto kernel = k_iv_halley32_tiled<InT, 256, 2>;
+  const TileSched ts = make_sched(a, 512, true);
+  const cudaError_t e = reset_sched(ts, st);
+  if (e != cudaSuccess) return e;
+  kernel<<<persistent_grid<kernel>(a.n, 512, 256), 256, 0, st>>>(a, ts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iv_halley(const IvArgs& a, cudaStream_t st) {
+  return a.f32_inputs ? launch_halley64_tiled<float>(a, st) : launch_halley64_tiled<double>(a, st);
+}
+
+cudaError_t launch_iv_halley32(const IvArgs& a, cudaStream_t st) {
+  return a.f32_inputs ? launch_halley32_tiled<float>(a, st) : launch_halley32_tiled<double>(a, st);
+}
+
+// ---- workspace arrangement ------------------------------------------------
 size_t halley_workspace_bytes(int64_t n) {
   const size_t idx_bytes = ((size_t)n * 4 + 15) / 16 * 16;
   return 16 + idx_bytes + (size_t)n * 16;
@@ -344,6 +595,26 @@ static HalleyWs halley_ws(void* ws, int64_t n) {
   w.lo = reinterpret_cast<double*>(p + 16 + idx_bytes);
   w.hi = w.lo + n;
   return w;
+}
+
+// warp-aggregated append of the quotes that failed the convergence test
+template <typename F>
+__device__ __forceinline__ void ws_append(const HalleyWs& w, bool fallback, int64_t i, F lo, F hi) {
+  const unsigned active = __activemask();
+  const unsigned m = __ballot_sync(active, fallback);
+  if (m) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(w.count, (unsigned)__popc(m));
+    base = __shfl_sync(active, base, leader);
+    if (fallback) {
+      const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+      w.idx[pos] = (unsigned)i;
+      w.lo[pos] = lo;
+      w.hi[pos] = hi;
+    }
+  }
 }
 
 template <typename InT>
@@ -373,22 +644,7 @@ __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
     }
     a.sigma[i] = sigma;
     a.status[i] = (uint8_t)nq.status;
-    // warp-aggregated append of the quotes that failed the convergence test
-    const unsigned active = __activemask();
-    const unsigned m = __ballot_sync(active, fallback);
-    if (m) {
-      const int lane = threadIdx.x & 31;
-      const int leader = __ffs(m) - 1;
-      unsigned base = 0;
-      if (lane == leader) base = atomicAdd(w.count, (unsigned)__popc(m));
-      base = __shfl_sync(active, base, leader);
-      if (fallback) {
-        const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
-        w.idx[pos] = (unsigned)i;
-        w.lo[pos] = lo;
-        w.hi[pos] = hi;
-      }
-    }
+    ws_append(w, fallback, i, lo, hi);
   }
 }
 
@@ -402,9 +658,7 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
     int flag;
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
-    const Reduced<double> q64 = reduced64(nq);
-    const double lnb = q64.ln_beta != 0.0 ? q64.ln_beta : log64(q64.beta);
-    const double s = bisect_fallback(lnb, q64.beta, q64.x, q64.bmax, w.lo[k], w.hi[k]);
+    const double s = halley_fallback64(reduced64(nq), w.lo[k], w.hi[k]);
     a.sigma[i] = s * rsqrt(T);
   }
 }
@@ -437,21 +691,7 @@ __global__ void __launch_bounds__(256) k_iv_halley32(IvArgs a, HalleyWs w) {
     }
     a.sigma[i] = sigma;
     a.status[i] = (uint8_t)nq.status;
-    const unsigned active = __activemask();
-    const unsigned m = __ballot_sync(active, fallback);
-    if (m) {
-      const int lane = threadIdx.x & 31;
-      const int leader = __ffs(m) - 1;
-      unsigned base = 0;
-      if (lane == leader) base = atomicAdd(w.count, (unsigned)__popc(m));
-      base = __shfl_sync(active, base, leader);
-      if (fallback) {
-        const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
-        w.idx[pos] = (unsigned)i;
-        w.lo[pos] = lo;
-        w.hi[pos] = hi;
-      }
-    }
+    ws_append(w, fallback, i, (double)lo, (double)hi);
   }
 }
 
@@ -471,7 +711,7 @@ __global__ void __launch_bounds__(256) k_halley32_fallback(IvArgs a, HalleyWs w)
   }
 }
 
-cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st) {
+cudaError_t launch_iv_halley32_ws(const IvArgs& a, void* ws, cudaStream_t st) {
   const HalleyWs w = halley_ws(ws, a.n);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
@@ -485,7 +725,7 @@ cudaError_t launch_iv_halley32(const IvArgs& a, void* ws, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_iv_halley(const IvArgs& a, void* ws, cudaStream_t st) {
+cudaError_t launch_iv_halley_ws(const IvArgs& a, void* ws, cudaStream_t st) {
   const HalleyWs w = halley_ws(ws, a.n);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;

@@ -649,6 +649,71 @@ def test_host_streaming_matches_device(fv, torch_dev, solver, prec):
 
 
 # ---------------------------------------------------------------------------
+# the implied-volatility calls allocate nothing and never synchronise
+# ---------------------------------------------------------------------------
+def test_iv_calls_capture_into_a_graph(fv, torch_dev):
+    # Each solver captures into a CUDA graph on a side stream in the global
+    # capture mode, which fails on any synchronising or allocating call from
+    # any thread; the batch (1,433,600 quotes, dynamic tiles with their
+    # counter memset) is larger than every Halley call before it in this module.
+    # Replays reproduce the direct call bit for bit, also after the outputs
+    # (which hold the tile counters while a call runs) were overwritten.
+    torch, dev = torch_dev
+    w = wl.fill_prices(wl.bsm_grid(2048, 700, seed=43), orc.price_f64)
+    args = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    n = flag.numel()
+    for solver, prec in ((fv.FV_HALLEY, fv.FV_FP64), (fv.FV_HALLEY, fv.FV_FP32),
+                         (fv.FV_LBR, fv.FV_FP64), (fv.FV_LBR, fv.FV_MIXED)):
+        out = torch.full((n,), -1.0, dtype=torch.float64, device=dev)
+        st = torch.full((n,), 9, dtype=torch.uint8, device=dev)
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="global"):
+            fv.fv_implied_vol_ex(fv.FV_BSM, solver, prec, *args, flag, out, st)
+        torch.cuda.synchronize()
+        s_ref, st_ref = fv.fv_implied_vol_ex(fv.FV_BSM, solver, prec, *args, flag)
+        for fill in (-1.0, 3.0):
+            out.fill_(fill)
+            st.fill_(9)
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(st, st_ref), (solver, prec)
+            assert torch.equal(out.nan_to_num(-7.0), s_ref.nan_to_num(-7.0)), (solver, prec)
+        del g
+    _sampled_parity(fv, torch_dev, w, _np(s_ref), _np(st_ref), fv.FV_BSM, n_sample=2048, seed=8)
+
+
+def test_halley_workspace_and_tiled_arrangements_agree(fv, torch_dev):
+    # fv_implied_vol_ws compacts the failures into a device list and runs the
+    # fallback as a second kernel; fv_implied_vol compacts them per tile in
+    # shared memory.  Same per-quote arithmetic, same results, on a batch
+    # where both the static (small) and dynamic (large) tilings run.
+    torch, dev = torch_dev
+    for n_s, n_m in ((300, 100), (1024, 300)):
+        w = wl.fill_prices(wl.bsm_grid(n_s, n_m, seed=44), orc.price_f64)
+        args = _args(torch_dev, w)
+        flag = _dev(torch_dev, w["flag"])
+        n = flag.numel()
+        ws = torch.zeros(fv.fv_workspace_size(fv.FV_HALLEY, n), dtype=torch.uint8, device=dev)
+        s_ws, st_ws = fv.fv_implied_vol_ws(fv.FV_BSM, fv.FV_HALLEY, *args, flag, ws)
+        torch.cuda.synchronize()
+        n_fallback = int(ws[:4].cpu().numpy().view(np.uint32)[0])
+        s_t, st_t = fv.fv_implied_vol(fv.FV_BSM, fv.FV_HALLEY, *args, flag)
+        assert torch.equal(st_ws, st_t)
+        a, b = _np(s_ws), _np(s_t)
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        ok = ~np.isnan(b) & (b > 0)
+        # the compiler may contract the same source into FMAs differently in
+        # the two kernels: only rounding, amplified by the conditioning, differs
+        rel = np.abs(a[ok] - b[ok]) / b[ok]
+        assert rel.max() <= 1e-12, rel.max()
+        # the grid's wings fail the sweeps' convergence test: the fallback runs
+        assert 0 < n_fallback < n
+
+
+# ---------------------------------------------------------------------------
 # binned (large batches) and unbinned (small batches) kernels agree
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -707,22 +772,76 @@ def _sampled_parity(fv, torch_dev, w, sig, st, model, n_sample=2048, seed=0, tol
                  tol_rest=1e-12 if tol_gate <= 1e-12 else None)
 
 
-def test_full_size_bsm_grid_lbr_and_mixed(fv, torch_dev):
+@pytest.fixture(scope="module")
+def full_grid():
+    """The 16,777,216-quote BSM grid the benchmark times, priced in binary128,
+    with the oracle's status rule for every quote, the oracle's step-by-step
+    FP64 LBR for every quote, and the definition (binary128 root) on 262,144
+    quotes sampled among those clear of a status threshold."""
     w = wl.fill_prices(wl.bsm_grid(4096, 4096, seed=1), orc.price)
-    args = _args(torch_dev, w)
-    flag = _dev(torch_dev, w["flag"])
-    s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *args, flag)
-    _sampled_parity(fv, torch_dev, w, _np(s), _np(st), fv.FV_BSM)
-    s, st = fv.fv_implied_vol_ex(fv.FV_BSM, fv.FV_LBR, fv.FV_MIXED, *args, flag)
-    _sampled_parity(fv, torch_dev, w, _np(s), _np(st), fv.FV_BSM, seed=1)
+    keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
+    st_all, _, beta, margin = orc.status(wl.BSM, *[w[k] for k in keys])
+    lbr, st_lbr, _ = orc.iv_lbr(wl.BSM, *[w[k] for k in keys], n_iter=3)
+    g = np.random.default_rng(17)
+    idx = np.sort(g.choice(np.nonzero(margin > 16.0)[0], size=262144, replace=False))
+    sub = {k: np.asarray(w[k])[idx] for k in keys}
+    sub["model"] = wl.BSM
+    return dict(w=w, st=st_all, beta=beta, margin=margin, lbr=lbr, st_lbr=st_lbr, idx=idx,
+                ref=_iv_ref(sub))
 
 
-def test_full_size_bsm_grid_status_with_exact_prices(fv, torch_dev):
-    # binary128 prices: every status bit-identical, no ambiguous quote allowed
-    w = wl.fill_prices(wl.bsm_grid(4096, 4096, seed=1), orc.price)
-    s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *_args(torch_dev, w), _dev(torch_dev, w["flag"]))
-    st_all = orc.status(fv.FV_BSM, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], w["q"], w["flag"])[0]
-    assert np.array_equal(_np(st), st_all)
+# (solver, precision, gated tolerance, conditioning bound) of every path the
+# benchmark times on the grid
+FULL_PATHS = {"lbr": (0, 0, 1e-12, 1e-12), "mixed": (0, 1, 1e-12, 1e-12),
+              "halley": (1, 0, 1e-12, 1e-12), "fp32": (0, 2, 1e-5, None),
+              "halley32": (1, 2, 1e-4, None)}
+
+
+@pytest.mark.parametrize("path", list(FULL_PATHS))
+def test_full_size_bsm_grid(fv, torch_dev, full_grid, path):
+    # the launch configuration of the benchmark: one call over the whole grid
+    solver, prec, tol, tol_rest = FULL_PATHS[path]
+    w = full_grid["w"]
+    s, st = fv.fv_implied_vol_ex(fv.FV_BSM, solver, prec, *_args(torch_dev, w),
+                                 _dev(torch_dev, w["flag"]))
+    s, st = _np(s), _np(st)
+    # status: bit-identical for every quote (binary128 prices keep every quote
+    # clear of the rule's thresholds)
+    assert np.array_equal(st, full_grid["st"]), "%d statuses differ" % (st != full_grid["st"]).sum()
+    # sigma against the definition on the sampled quotes
+    idx = full_grid["idx"]
+    ref, st_ref, v, kap = full_grid["ref"]
+    assert np.array_equal(st[idx], st_ref)
+    _check_sigma(s[idx], ref, st_ref, v, kap, tol_gate=tol, tol_rest=tol_rest, name=path)
+    if tol_rest is None:
+        return
+    # every quote against the oracle's FP64 LBR (within 4 eps (1 + kappa) of
+    # the definition, a pin of the oracle): the two may differ by both
+    # errors, so the bound is 1e-12 + 16 eps (1 + kappa) with kappa from the
+    # oracle at its own sigma.  The oracle's FP64 LBR works on beta itself,
+    # so it covers the quotes whose normalised price is a normal FP64 number
+    # (beta >= 1e-290); below it (prices at the bottom of the FP64 range,
+    # ~6 % of the grid, most of them 0) the sampled comparison with the
+    # definition above applies, and a zero price must give sigma = 0.
+    lbr = full_grid["lbr"]
+    assert np.array_equal(full_grid["st_lbr"], full_grid["st"])
+    assert np.all(np.isnan(s[st != orc.OK])), path
+    assert np.all(s[(st == orc.OK) & (w["P"] == 0)] == 0.0), path
+    normal = (st == orc.OK) & (full_grid["beta"] >= 1e-290)
+    assert np.all(s[normal & (lbr == 0)] == 0.0), path
+    solved = normal & (lbr > 0)
+    assert solved.sum() > 0.9 * (st == orc.OK).sum()
+    keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
+    v_all, kap_all = orc.conditioning(wl.BSM, *[w[k] for k in keys], lbr)
+    rel = np.abs(s[solved] - lbr[solved]) / lbr[solved]
+    k = np.nan_to_num(kap_all[solved], nan=np.inf, posinf=np.inf)
+    bound = 1e-12 + 16 * EPS * (1 + k)
+    bad = rel > bound
+    assert not bad.any(), "%s: %d of %d quotes beyond the bound (worst %.3g)" % (
+        path, bad.sum(), solved.sum(), rel[bad].max())
+    gate = (v_all[solved] > 1e-8) & (k <= 1e3)
+    assert rel[gate].max() <= 2e-12, "%s: gated max rel %.3g vs the oracle's LBR" % (
+        path, rel[gate].max())
 
 
 def test_full_size_fp32_inputs_mixed(fv, torch_dev):
