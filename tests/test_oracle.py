@@ -255,6 +255,113 @@ def test_status_decisions_at_exact_bounds():
         assert st[0] == orc.INVALID and math.isnan(sig[0])
 
 
+# ---------------------------------------------------------------------------
+# conditioning (normalised vega, kappa) and the status margin: the quantities
+# the parity tests use to gate and to excuse quotes
+# ---------------------------------------------------------------------------
+def _textbook_price_mp(model, SF, K, T, r, q, sigma, theta):
+    """theta e^{-rT} [F Phi(theta d1) - K Phi(theta d2)] at mpmath's working
+    precision (the caller sets it)."""
+    SF, K, T, r, q = (mp.mpf(v) for v in (SF, K, T, r, q))
+    F = SF if model == orc.BLACK76 else SF * mp.exp((r - q) * T)
+    s = sigma * mp.sqrt(T)
+    d1 = (mp.log(F / K) + s * s / 2) / s
+    d2 = d1 - s
+    return mp.exp(-r * T) * theta * (F * mp.ncdf(theta * d1) - K * mp.ncdf(theta * d2))
+
+
+COND_CASES = [  # (model, S|F, K, T, r, q, sigma, flag): out of and in the money, wings, spot + dividends
+    (orc.BLACK76, 100.0, 95.0, 0.25, 0.05, 0.0, 0.2, 1),
+    (orc.BLACK76, 100.0, 95.0, 0.25, 0.05, 0.0, 0.2, -1),
+    (orc.BLACK76, 100.0, 60.0, 2.0, 0.03, 0.0, 0.15, 1),
+    (orc.BLACK76, 100.0, 160.0, 0.5, 0.01, 0.0, 0.9, 1),
+    (orc.BLACK76, 100.0, 100.0, 1.0, 0.0, 0.0, 2.5, -1),
+    (orc.BLACK76, 100.0, 140.0, 0.1, 0.02, 0.0, 0.4, -1),
+    (orc.BSM, 100.0, 80.0, 1.5, 0.04, 0.02, 0.3, 1),
+    (orc.BSM, 100.0, 125.0, 0.75, 0.02, 0.04, 0.6, -1),
+    (orc.BSM, 100.0, 101.0, 3.0, 0.05, 0.01, 0.05, 1),
+    (orc.BSM, 100.0, 30.0, 5.0, 0.06, 0.0, 1.2, -1),
+]
+
+
+def test_normalised_vega_is_the_price_derivative():
+    # b'(x, s) = dP/dsigma / (e^{-rT} sqrt(F K) sqrt(T)): the derivative of the
+    # textbook price by mpmath's numerical differentiation, in 50 digits
+    for model, SF, K, T, r, q, sig, th in COND_CASES:
+        v, _ = orc.conditioning(model, 1.0, SF, K, T, r, q, th, sig)
+        with mp.workdps(50):
+            vega = mp.diff(lambda x: _textbook_price_mp(model, SF, K, T, r, q, x, th), mp.mpf(sig))
+            F = mp.mpf(SF) if model == orc.BLACK76 else SF * mp.exp((mp.mpf(r) - q) * T)
+            want = vega / (mp.exp(-mp.mpf(r) * T) * mp.sqrt(F * K) * mp.sqrt(T))
+        assert v[0] == pytest.approx(float(want), rel=1e-12), (model, SF, K, T, sig, th)
+
+
+def test_kappa_is_the_sensitivity_of_sigma_to_the_price():
+    # kappa = beta / (s b') = d ln(sigma) / d ln(P) (beta is proportional to P):
+    # central differences of the definition's root at P (1 +- d), Richardson-
+    # extrapolated from d and d/2, with d = 1e-6 / max(1, coarse estimate)
+    # (the truncation error grows like d^2 kappa^3)
+    def central(model, P, SF, K, T, r, q, th, d):
+        Pp, Pm = P * (1 + d), P * (1 - d)
+        sp, _ = orc.iv(model, Pp, SF, K, T, r, q, th)
+        sm, _ = orc.iv(model, Pm, SF, K, T, r, q, th)
+        mp.mp.dps = 30
+        return mp.log(mp.mpf(sp[0]) / mp.mpf(sm[0])) / mp.log(mp.mpf(Pp) / mp.mpf(Pm))
+
+    for model, SF, K, T, r, q, sig, th in COND_CASES:
+        P = orc.price(model, SF, K, T, r, q, sig, th)[0]
+        s0, st = orc.iv(model, P, SF, K, T, r, q, th)
+        assert st[0] == orc.OK
+        _, kap = orc.conditioning(model, P, SF, K, T, r, q, th, s0[0])
+        d = 1e-6 / max(1.0, float(central(model, P, SF, K, T, r, q, th, 1e-6)))
+        fd = (4 * central(model, P, SF, K, T, r, q, th, d / 2) -
+              central(model, P, SF, K, T, r, q, th, d)) / 3
+        assert kap[0] == pytest.approx(float(fd), rel=1e-6), (model, SF, K, T, sig, th)
+    # in the money the intrinsic value dominates beta: kappa is large
+    P = orc.price(orc.BLACK76, 100.0, 60.0, 1.0, 0.0, 0.0, 0.1, 1)[0]
+    s0, _ = orc.iv(orc.BLACK76, P, 100.0, 60.0, 1.0, 0.0, None, 1)
+    _, kap = orc.conditioning(orc.BLACK76, P, 100.0, 60.0, 1.0, 0.0, None, 1, s0[0])
+    assert kap[0] > 1e3
+
+
+def test_status_margin_counts_ulps_to_the_nearest_threshold():
+    # Black-76 with r = 0 (no discounting), T = 1: beta = P / sqrt(F K).  Each
+    # quote is built in 50 digits at k units of 2^-52 (relative) from one
+    # threshold of the rule: below intrinsic at iota (1 - e_s), at intrinsic
+    # at iota (1 + e_s), above the bound at b_max (1 - e_s) for the reduced
+    # quote, with e_s = 64 * 2^-52.  The margin counts those units (relative
+    # to beta for the in-the-money bound), up to the FP64 rounding of beta and
+    # of the intrinsic value and bound (a few units).
+    mp.mp.dps = 50
+    F, u, es = 100.0, mp.mpf(2) ** -52, 64 * mp.mpf(2) ** -52
+    cases = []
+    for k in (-48, -20, -6, 6, 20, 48):
+        for K, fl, which in ((90.0, 1, "below"), (110.0, -1, "below"), (90.0, 1, "at"),
+                             (110.0, 1, "above"), (90.0, -1, "above"), (90.0, 1, "above")):
+            cases.append((K, fl, which, k))
+    for K, fl, which, k in cases:
+        x = mp.log(mp.mpf(F) / K)
+        itm = fl * x > 0
+        iota = 2 * mp.sinh(abs(x) / 2) if itm else mp.mpf(0)
+        bmax = mp.exp(-abs(x) / 2)
+        if which == "below":
+            beta, scale = iota * (1 - es) * (1 + k * u), 1
+        elif which == "at":
+            beta, scale = iota * (1 + es) * (1 + k * u), 1
+        else:
+            beta = iota + bmax * (1 - es) * (1 + k * u)
+            scale = bmax / beta if beta > bmax else 1
+        P = float(beta * mp.sqrt(mp.mpf(F) * K))
+        if which != "above" and not itm:
+            continue
+        margin = orc.status(orc.BLACK76, P, F, K, 1.0, 0.0, None, fl)[3][0]
+        want = float(abs(k) * scale)
+        assert abs(margin - want) <= 2.0, (K, fl, which, k, margin, want)
+    # far from every threshold the margin is large; an invalid quote has none
+    assert orc.status(orc.BLACK76, 12.0, F, 90.0, 1.0, 0.0, None, 1)[3][0] > 1e10
+    assert orc.status(orc.BLACK76, 5.0, F, 90.0, 1.0, 0.0, None, 0)[3][0] == np.inf
+
+
 def test_paper_quick_use_example():
     with open(os.path.join(GOLDEN, "paper_quick_use.json")) as f:
         g = json.load(f)

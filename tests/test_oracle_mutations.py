@@ -56,6 +56,29 @@ MUTANTS = [
     ("status: in-the-money test with the wrong sign",
      "const int itm = th * x > 0;\n  const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x",
      "const int itm = th * x < 0;\n  const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x"),
+    # conditioning (normalised vega, kappa) and the status margin: the
+    # quantities the parity tests gate and excuse quotes with
+    ("conditioning: kappa without the factor s",
+     "c->out2[i] = (double)(beta / (s * v));", "c->out2[i] = (double)(beta / v);"),
+    ("conditioning: kappa with t = s/2 for s",
+     "c->out2[i] = (double)(beta / (s * v));", "c->out2[i] = (double)(beta / (t * v));"),
+    ("conditioning: normalised vega with t^2 of the wrong sign",
+     "q128 v = q_inv_sqrt_2pi() * expf128(-0.5f128 * (h * h + t * t));",
+     "q128 v = q_inv_sqrt_2pi() * expf128(-0.5f128 * (h * h - t * t));"),
+    ("conditioning: normalised vega without 1/sqrt(2 pi)",
+     "q128 v = q_inv_sqrt_2pi() * expf128(-0.5f128 * (h * h + t * t));",
+     "q128 v = expf128(-0.5f128 * (h * h + t * t));"),
+    ("status margin: below-intrinsic threshold without its band",
+     "m = fmin(m, fabs(beta / (iota * (1.0 - EPS_S)) - 1.0));", "m = fmin(m, fabs(beta / iota - 1.0));"),
+    ("status margin: at-intrinsic threshold on the wrong side of the band",
+     "m = fmin(m, fabs(beta / (iota * (1.0 + EPS_S)) - 1.0));",
+     "m = fmin(m, fabs(beta / (iota * (1.0 - EPS_S)) - 1.0));"),
+    ("status margin: upper threshold without its band",
+     "fabs(beta_otm / (bmax_otm * (1.0 - EPS_S)) - 1.0)", "fabs(beta_otm / bmax_otm - 1.0)"),
+    ("status margin: in-the-money bound distance not relative to beta",
+     "* (bmax_otm / (beta > bmax_otm ? beta : bmax_otm))", ""),
+    ("status margin: not in units of 2^-52",
+     "return m / eps;", "return m;"),
     # the definition of implied volatility
     ("definition: bisection keeps the wrong half",
      "    if (nb_q_e(x, mid, 1, ep, em) < beta)\n      lo = mid;",
