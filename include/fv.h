@@ -236,13 +236,24 @@ typedef struct {
 
 typedef struct fv_chains_plan fv_chains_plan;
 
-/* Build a plan for one batch of chains: copy the descriptors and a tile
- * table (tile -> chain, offset) to the device, pick the block size and quotes
- * per thread by timing the candidates on `stream` (autotune = 1; 0 takes the
- * default), and capture the persistent launch into a CUDA graph.  Allocates
- * device memory and synchronises `stream`; owned by the plan.  Only FV_LBR in
- * FP64 is supported.  The chains' arrays must stay valid while the plan is
- * used. */
+/* Build a plan for one batch of chains (Section 3, batching): copy the
+ * descriptors and a tile table (tile -> chain, offset) to the device, choose
+ * the launch shape, and capture the persistent launch (a memset of the tile
+ * counter, then the kernel) into a CUDA graph.  Allocates device memory and
+ * synchronises `stream`; owned by the plan.  Only FV_LBR in FP64 is
+ * supported.  The chains' arrays must stay valid while the plan is used.
+ *
+ * Launch shape: block size x quotes per thread (64 x {1,2,4}, 128 x {1,2,4},
+ * 256 x {1,2,4}, 512 x {1,2}) and resident blocks per SM (every block that
+ * fits, or half of them).  autotune = 0 takes 256 x 4 at every resident
+ * block.  autotune = 1 looks the workload's key up in the tuning cache (this
+ * process's winners, then the file named by the environment variable
+ * FV_AUTOTUNE_CACHE if set) and otherwise times every candidate on `stream`
+ * (the median of three launches after one untimed launch; a few seconds on
+ * tens of millions of quotes) and records the winner in both.  The
+ * environment variable FV_AUTOTUNE = 0 or 1 overrides the argument.  The key
+ * names the device (name, SM count), the model and floor(log2) of the chain
+ * count, the quote count and the mean chain length. */
 fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* chains,
                              int64_t n_chains, int autotune, void* stream, fv_chains_plan** plan);
 
@@ -256,6 +267,29 @@ fv_err fv_implied_vol_chains_direct(fv_chains_plan* plan, void* stream);
 /* Block size, quotes per thread, grid size and tile count the plan uses. */
 fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_per_thread,
                            int* grid, int64_t* tiles, int64_t* quotes);
+
+/* How the plan's launch shape was chosen: resident blocks per SM, the source
+ * (FV_TUNE_DEFAULT, FV_TUNE_TIMED, FV_TUNE_CACHED), the number of candidates
+ * timed (0 unless timed), the median launch time of the chosen shape in ms
+ * (as timed, or as recorded in the cache; 0 for the default) and the tuning
+ * key (written to `key`, at most key_bytes bytes with the terminating NUL;
+ * NULL skips it).  Any output may be NULL. */
+typedef enum { FV_TUNE_DEFAULT = 0, FV_TUNE_TIMED = 1, FV_TUNE_CACHED = 2 } fv_tune_source;
+fv_err fv_chains_plan_tuning(const fv_chains_plan* plan, int* blocks_per_sm, int* source,
+                             int* candidates, double* best_ms, char* key, size_t key_bytes);
+
+/* The tuning cache file (host only; no GPU needed), so that a deployment can
+ * inspect it or seed it with shapes tuned elsewhere.  get: the entry for
+ * `key`, or block = quotes_per_thread = blocks_per_sm = 0 and ms = 0 when the
+ * file or the entry is absent.  put: adds or replaces the entry (the file is
+ * rewritten through a temporary file and a rename).  Keys may not be empty
+ * or hold quotes, backslashes or line breaks (FV_ERR_ARG); put also rejects
+ * non-positive shapes.  A plan ignores an entry that names no compiled
+ * variant and times the candidates instead. */
+fv_err fv_autotune_cache_get(const char* path, const char* key, int* block, int* quotes_per_thread,
+                             int* blocks_per_sm, double* ms);
+fv_err fv_autotune_cache_put(const char* path, const char* key, int block, int quotes_per_thread,
+                             int blocks_per_sm, double ms);
 
 fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
 

@@ -4,11 +4,16 @@
 // fv_kernels.cu.  Nothing here synchronises except plan creation.
 #include <cuda_runtime.h>
 
+#include <unistd.h>
+
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "fv.h"
@@ -126,14 +131,20 @@ void set_last_error(const char* msg) { fail(FV_ERR_ARG, "%s", msg); }
 // ---------------------------------------------------------------------------
 struct fv_chains_plan {
   int model;
-  int block, qpt, grid;
+  int block, qpt, grid, blocks_per_sm;
   int64_t n_tiles, n_quotes;
   fvk::ChainDesc* d_chains;
   fvk::Tile* d_tiles;
+  unsigned long long* d_counter;  // dynamic tile counter (zeroed before each launch)
   std::vector<fvk::ChainDesc> h_chains;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int device;
+  // how the launch shape was chosen
+  int source;      // FV_TUNE_DEFAULT, FV_TUNE_TIMED or FV_TUNE_CACHED
+  int candidates;  // candidates timed
+  double best_ms;  // median launch time of the chosen shape (timed or cached; 0 for the default)
+  std::string key;
 };
 
 namespace {
@@ -169,10 +180,158 @@ fv_err upload_tiles(fv_chains_plan* p, const std::vector<fvk::Tile>& tiles, cuda
   return cuda_result(e, "fv_chains_plan_create: tile upload");
 }
 
-int plan_grid(int qpt, int64_t n_tiles) {
-  const int per_sm = fvk::chains_max_blocks_per_sm(qpt);
-  const int64_t g = std::min<int64_t>((int64_t)fvk::sm_count() * per_sm, std::max<int64_t>(1, n_tiles));
-  return (int)g;
+int plan_grid(int blocks_per_sm, int64_t n_tiles) {
+  return (int)std::min<int64_t>((int64_t)fvk::sm_count() * blocks_per_sm,
+                                std::max<int64_t>(1, n_tiles));
+}
+
+// ---- the tuning cache ------------------------------------------------------
+// A plan's launch shape (block size, quotes per thread, resident blocks per
+// SM) is keyed by the device (name, SM count), the model and the workload's
+// shape: floor(log2) of the chain count, of the quote count and of the mean
+// chain length.  Winners are kept for the process and, when the environment
+// variable FV_AUTOTUNE_CACHE names a file, in that file as one JSON object
+// {"<key>": {"block": B, "qpt": Q, "blocks_per_sm": S, "ms": T}, ...}.
+struct TuneEntry {
+  int block, qpt, bps;
+  double ms;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune_mem;
+
+bool key_ok(const char* key) {
+  if (key == nullptr || *key == 0) return false;
+  for (const char* c = key; *c; c++)
+    if (*c == '"' || *c == '\\' || *c == '\n' || *c == '\r') return false;
+  return true;
+}
+
+// every entry of a cache file (an unreadable or absent file has none)
+std::map<std::string, TuneEntry> cache_load(const char* path) {
+  std::map<std::string, TuneEntry> out;
+  FILE* f = fopen(path, "r");
+  if (!f) return out;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    const char* q0 = strchr(line, '"');
+    if (!q0) continue;
+    const char* q1 = strstr(q0 + 1, "\": {");
+    if (!q1) continue;
+    TuneEntry t{0, 0, 0, 0.0};
+    const char* b = strstr(q1, "\"block\":");
+    const char* q = strstr(q1, "\"qpt\":");
+    const char* s = strstr(q1, "\"blocks_per_sm\":");
+    const char* m = strstr(q1, "\"ms\":");
+    if (!b || !q || !s || sscanf(b + 8, "%d", &t.block) != 1 || sscanf(q + 6, "%d", &t.qpt) != 1 ||
+        sscanf(s + 16, "%d", &t.bps) != 1)
+      continue;
+    if (m) sscanf(m + 5, "%lf", &t.ms);
+    if (t.block <= 0 || t.qpt <= 0 || t.bps <= 0) continue;
+    out[std::string(q0 + 1, q1)] = t;
+  }
+  fclose(f);
+  return out;
+}
+
+// add or replace one entry; the file is rewritten through a temporary file
+// and a rename, so a reader never sees half a file
+fv_err cache_store(const char* path, const std::string& key, const TuneEntry& t) {
+  std::map<std::string, TuneEntry> all = cache_load(path);
+  all[key] = t;
+  char tmp[4096];
+  snprintf(tmp, sizeof(tmp), "%s.tmp%ld", path, (long)getpid());
+  FILE* f = fopen(tmp, "w");
+  if (!f) return fail(FV_ERR_ARG, "tuning cache: cannot write %s", tmp);
+  fprintf(f, "{\n");
+  size_t k = 0;
+  for (const auto& kv : all) {
+    fprintf(f, "  \"%s\": {\"block\": %d, \"qpt\": %d, \"blocks_per_sm\": %d, \"ms\": %.6f}%s\n",
+            kv.first.c_str(), kv.second.block, kv.second.qpt, kv.second.bps, kv.second.ms,
+            ++k < all.size() ? "," : "");
+  }
+  fprintf(f, "}\n");
+  const bool ok = fclose(f) == 0 && rename(tmp, path) == 0;
+  if (!ok) {
+    remove(tmp);
+    return fail(FV_ERR_ARG, "tuning cache: cannot replace %s", path);
+  }
+  return FV_SUCCESS;
+}
+
+int floor_log2(int64_t v) {
+  int b = 0;
+  while (v > 1) {
+    v >>= 1;
+    b++;
+  }
+  return b;
+}
+
+std::string tune_key(int model, int64_t n_chains, int64_t n_quotes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  char name[256] = "unknown";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+    snprintf(name, sizeof(name), "%s", prop.name);
+    for (char* c = name; *c; c++)
+      if (*c == '"' || *c == '\\' || *c == '|') *c = '_';
+  } else {
+    cudaGetLastError();
+  }
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|sm%d|model%d|chains2^%d|quotes2^%d|len2^%d", name, fvk::sm_count(),
+           model, floor_log2(n_chains), floor_log2(n_quotes),
+           floor_log2(n_chains > 0 ? n_quotes / n_chains : 0));
+  return buf;
+}
+
+// FV_AUTOTUNE=0 or 1 overrides the plan's autotune argument
+int autotune_setting(int requested) {
+  const char* v = getenv("FV_AUTOTUNE");
+  if (v && (v[0] == '0' || v[0] == '1') && v[1] == 0) return v[0] - '0';
+  return requested ? 1 : 0;
+}
+
+bool variant_exists(int block, int qpt) {
+  for (int k = 0; k < fvk::chains_variant_count(); k++) {
+    int b, q;
+    fvk::chains_variant(k, &b, &q);
+    if (b == block && q == qpt) return true;
+  }
+  return false;
+}
+
+// median of `reps` timed launches of one shape (after one untimed launch)
+fv_err time_shape(fv_chains_plan* p, int block, int qpt, int grid, cudaStream_t st, int reps,
+                  double* ms_out) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_result(cudaGetLastError(), "autotune");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_result(cudaGetLastError(), "autotune");
+  }
+  std::vector<float> t;
+  cudaError_t ce = fvk::launch_chains(p->model, p->d_chains, p->d_tiles, p->n_tiles, p->d_counter,
+                                      block, qpt, grid, st);
+  for (int k = 0; k < reps && ce == cudaSuccess; k++) {
+    ce = cudaEventRecord(e0, st);
+    if (ce == cudaSuccess)
+      ce = fvk::launch_chains(p->model, p->d_chains, p->d_tiles, p->n_tiles, p->d_counter, block,
+                              qpt, grid, st);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_result(ce, "fv_chains_plan_create: autotune");
+  std::sort(t.begin(), t.end());
+  *ms_out = t[t.size() / 2];
+  return FV_SUCCESS;
 }
 
 }  // namespace
@@ -372,9 +531,14 @@ fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* c
   p->model = model;
   p->d_chains = nullptr;
   p->d_tiles = nullptr;
+  p->d_counter = nullptr;
   p->graph = nullptr;
   p->exec = nullptr;
   p->n_quotes = 0;
+  p->n_tiles = 0;
+  p->source = FV_TUNE_DEFAULT;
+  p->candidates = 0;
+  p->best_ms = 0.0;
   cudaGetDevice(&p->device);
   p->h_chains.resize((size_t)n_chains);
   for (int64_t c = 0; c < n_chains; c++) {
@@ -402,60 +566,88 @@ fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* c
                          cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: upload"));
   }
-  // candidates: (block, quotes per thread); the default first.  A tile is
-  // block * quotes-per-thread quotes of one chain, binned by LBR region.
-  const int cand[][2] = {{256, 4}, {256, 2}, {256, 1}};
-  const int n_cand = autotune ? (int)(sizeof(cand) / sizeof(cand[0])) : 1;
+  cudaError_t ce = cudaMalloc(&p->d_counter, 16);
+  if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: tile counter"));
+  p->key = tune_key(model, n_chains, p->n_quotes);
+  // the default shape: 256 threads, 4 quotes per thread, every resident block
+  p->block = 256;
+  p->qpt = 4;
+  p->blocks_per_sm = fvk::chains_max_blocks_per_sm(p->block, p->qpt);
   std::vector<fvk::Tile> tiles;
-  int best = 0;
-  if (n_cand > 1 && p->n_quotes > 0) {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best_ms = 1e30f;
-    for (int k = 0; k < n_cand; k++) {
-      build_tiles(p, cand[k][0], cand[k][1], tiles);
-      if ((e = upload_tiles(p, tiles, st)) != FV_SUCCESS) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cleanup(e);
-      }
-      const int grid = plan_grid(cand[k][1], p->n_tiles);
-      // one warm-up launch, then the timed one
-      fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, cand[k][0], cand[k][1], grid, st);
-      cudaEventRecord(e0, st);
-      fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, cand[k][0], cand[k][1], grid, st);
-      cudaEventRecord(e1, st);
-      cudaError_t ce = cudaEventSynchronize(e1);
-      if (ce != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cleanup(cuda_result(ce, "fv_chains_plan_create: autotune"));
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = k;
+  if (p->n_quotes > 0 && autotune_setting(autotune)) {
+    TuneEntry hit{0, 0, 0, 0.0};
+    bool found = false;
+    const char* path = getenv("FV_AUTOTUNE_CACHE");
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_mem.find(p->key);
+      if (it != g_tune_mem.end()) {
+        hit = it->second;
+        found = true;
+      } else if (path && *path) {
+        const auto all = cache_load(path);
+        auto jt = all.find(p->key);
+        if (jt != all.end()) {
+          hit = jt->second;
+          found = true;
+        }
       }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (found && variant_exists(hit.block, hit.qpt)) {
+      p->block = hit.block;
+      p->qpt = hit.qpt;
+      p->blocks_per_sm = hit.bps;
+      p->best_ms = hit.ms;
+      p->source = FV_TUNE_CACHED;
+    } else {
+      // time every variant at all its resident blocks and at half of them
+      double best = 1e300;
+      TuneEntry win{p->block, p->qpt, p->blocks_per_sm, 0.0};
+      for (int k = 0; k < fvk::chains_variant_count(); k++) {
+        int block, qpt;
+        fvk::chains_variant(k, &block, &qpt);
+        build_tiles(p, block, qpt, tiles);
+        if ((e = upload_tiles(p, tiles, st)) != FV_SUCCESS) return cleanup(e);
+        const int maxb = fvk::chains_max_blocks_per_sm(block, qpt);
+        const int bps_cand[2] = {maxb, maxb / 2};
+        for (int j = 0; j < 2; j++) {
+          const int bps = bps_cand[j];
+          if (bps < 1 || (j == 1 && bps == maxb)) continue;
+          double ms = 0.0;
+          if ((e = time_shape(p, block, qpt, plan_grid(bps, p->n_tiles), st, 3, &ms)) != FV_SUCCESS)
+            return cleanup(e);
+          p->candidates++;
+          if (ms < best) {
+            best = ms;
+            win = TuneEntry{block, qpt, bps, ms};
+          }
+        }
+      }
+      p->block = win.block;
+      p->qpt = win.qpt;
+      p->blocks_per_sm = win.bps;
+      p->best_ms = win.ms;
+      p->source = FV_TUNE_TIMED;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_mem[p->key] = win;
+      if (path && *path && (e = cache_store(path, p->key, win)) != FV_SUCCESS) return cleanup(e);
+    }
   }
-  p->block = cand[best][0];
-  p->qpt = cand[best][1];
   build_tiles(p, p->block, p->qpt, tiles);
   if ((e = upload_tiles(p, tiles, st)) != FV_SUCCESS) return cleanup(e);
-  p->grid = plan_grid(p->qpt, p->n_tiles);
-  // capture the persistent launch into a graph on a private stream
+  p->grid = plan_grid(p->blocks_per_sm, p->n_tiles);
+  // capture the counter reset and the persistent launch into a graph on a
+  // private stream
   if (p->n_tiles > 0) {
     cudaStream_t cs;
-    cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return cleanup(cuda_result(ce, "fv_chains_plan_create: stream"));
     ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
-      fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles, p->block, p->qpt, p->grid, cs);
+      const cudaError_t le = fvk::launch_chains(model, p->d_chains, p->d_tiles, p->n_tiles,
+                                                p->d_counter, p->block, p->qpt, p->grid, cs);
       ce = cudaStreamEndCapture(cs, &p->graph);
+      if (ce == cudaSuccess) ce = le;
     }
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
     cudaStreamDestroy(cs);
@@ -481,7 +673,7 @@ fv_err fv_implied_vol_chains_direct(fv_chains_plan* plan, void* stream) {
   fv_err e = pending_error(fn);
   if (e != FV_SUCCESS) return e;
   return cuda_result(fvk::launch_chains(plan->model, plan->d_chains, plan->d_tiles, plan->n_tiles,
-                                        plan->block, plan->qpt, plan->grid,
+                                        plan->d_counter, plan->block, plan->qpt, plan->grid,
                                         static_cast<cudaStream_t>(stream)),
                      fn);
 }
@@ -496,6 +688,44 @@ fv_err fv_chains_plan_info(const fv_chains_plan* plan, int* block, int* quotes_p
   if (tiles) *tiles = plan->n_tiles;
   if (quotes) *quotes = plan->n_quotes;
   return FV_SUCCESS;
+}
+
+fv_err fv_chains_plan_tuning(const fv_chains_plan* plan, int* blocks_per_sm, int* source,
+                             int* candidates, double* best_ms, char* key, size_t key_bytes) {
+  const char* fn = "fv_chains_plan_tuning";
+  FV_REQUIRE(plan, "plan", fn);
+  if (blocks_per_sm) *blocks_per_sm = plan->blocks_per_sm;
+  if (source) *source = plan->source;
+  if (candidates) *candidates = plan->candidates;
+  if (best_ms) *best_ms = plan->best_ms;
+  if (key && key_bytes > 0) snprintf(key, key_bytes, "%s", plan->key.c_str());
+  return FV_SUCCESS;
+}
+
+fv_err fv_autotune_cache_get(const char* path, const char* key, int* block, int* quotes_per_thread,
+                             int* blocks_per_sm, double* ms) {
+  const char* fn = "fv_autotune_cache_get";
+  FV_REQUIRE(path, "path", fn);
+  if (!key_ok(key)) return fail(FV_ERR_ARG, "%s: empty key or a key with quotes or newlines", fn);
+  const auto all = cache_load(path);
+  const auto it = all.find(key);
+  const TuneEntry t = it == all.end() ? TuneEntry{0, 0, 0, 0.0} : it->second;
+  if (block) *block = t.block;
+  if (quotes_per_thread) *quotes_per_thread = t.qpt;
+  if (blocks_per_sm) *blocks_per_sm = t.bps;
+  if (ms) *ms = t.ms;
+  return FV_SUCCESS;
+}
+
+fv_err fv_autotune_cache_put(const char* path, const char* key, int block, int quotes_per_thread,
+                             int blocks_per_sm, double ms) {
+  const char* fn = "fv_autotune_cache_put";
+  FV_REQUIRE(path, "path", fn);
+  if (!key_ok(key)) return fail(FV_ERR_ARG, "%s: empty key or a key with quotes or newlines", fn);
+  if (block <= 0 || quotes_per_thread <= 0 || blocks_per_sm <= 0)
+    return fail(FV_ERR_ARG, "%s: block, quotes per thread and blocks per SM must be positive", fn);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return cache_store(path, key, TuneEntry{block, quotes_per_thread, blocks_per_sm, ms});
 }
 
 }  // extern "C"
@@ -649,6 +879,7 @@ fv_err fv_chains_plan_destroy(fv_chains_plan* plan) {
   if (plan->graph) cudaGraphDestroy(plan->graph);
   if (plan->d_tiles) cudaFree(plan->d_tiles);
   if (plan->d_chains) cudaFree(plan->d_chains);
+  if (plan->d_counter) cudaFree(plan->d_counter);
   delete plan;
   return FV_SUCCESS;
 }

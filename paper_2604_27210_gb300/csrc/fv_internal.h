@@ -79,8 +79,15 @@ struct Tile {
 // record the message fv_last_error() returns on the calling thread
 void set_last_error(const char* msg);
 
+// the chains kernel's variants (block size x quotes per thread) the plan's
+// autotuner chooses from
+int chains_variant_count();
+void chains_variant(int k, int* block, int* quotes_per_thread);
+// resident blocks of a variant on one SM (1 if the variant does not exist)
+int chains_max_blocks_per_sm(int block, int quotes_per_thread);
+// zero `counter` on `st`, then launch the variant over the tile table
 cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
-                          int block, int qpt, int grid, cudaStream_t st);
-int chains_max_blocks_per_sm(int quotes_per_thread);
+                          unsigned long long* counter, int block, int qpt, int grid,
+                          cudaStream_t st);
 
 }  // namespace fvk

@@ -25,7 +25,8 @@ EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws
            "fv_implied_vol_ex", "fv_implied_vol_strided", "fv_greeks", "fv_iv_adjoint",
            "fv_normalised_black", "fv_math",
            "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
-           "fv_chains_plan_info", "fv_chains_plan_destroy", "fv_stream_plan_create",
+           "fv_chains_plan_info", "fv_chains_plan_tuning", "fv_autotune_cache_get",
+           "fv_autotune_cache_put", "fv_chains_plan_destroy", "fv_stream_plan_create",
            "fv_stream_plan_destroy", "fv_implied_vol_host", "fv_implied_vol_halley_noalloc",
            "fv_status_string", "fv_last_error"]
 
@@ -73,6 +74,13 @@ def _load():
     lib.fv_implied_vol_chains.argtypes = [_P, _P]
     lib.fv_implied_vol_chains_direct.argtypes = [_P, _P]
     lib.fv_chains_plan_info.argtypes = [_P] + [ctypes.POINTER(_I)] * 3 + [ctypes.POINTER(_N)] * 2
+    lib.fv_chains_plan_tuning.argtypes = [_P, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                          ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_char_p, ctypes.c_size_t]
+    lib.fv_autotune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p] + \
+        [ctypes.POINTER(_I)] * 3 + [ctypes.POINTER(ctypes.c_double)]
+    lib.fv_autotune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p, _I, _I, _I,
+                                          ctypes.c_double]
     lib.fv_chains_plan_destroy.argtypes = [_P]
     lib.fv_stream_plan_create.argtypes = [_N, ctypes.POINTER(ctypes.c_void_p)]
     lib.fv_stream_plan_destroy.argtypes = [_P]
@@ -354,6 +362,17 @@ class fv_chains_plan:
         return dict(block=b.value, quotes_per_thread=q.value, grid=g.value, tiles=t.value,
                     quotes=n.value)
 
+    def tuning(self):
+        """How the launch shape was chosen: blocks_per_sm, source ("default",
+        "timed" or "cached"), candidates timed, best_ms and the tuning key."""
+        b, src, c = _I(), _I(), _I()
+        ms = ctypes.c_double()
+        key = ctypes.create_string_buffer(512)
+        _check(_lib.fv_chains_plan_tuning(self._h, ctypes.byref(b), ctypes.byref(src), ctypes.byref(c),
+                                          ctypes.byref(ms), key, 512), "fv_chains_plan_tuning")
+        return dict(blocks_per_sm=b.value, source=("default", "timed", "cached")[src.value],
+                    candidates=c.value, best_ms=ms.value, key=key.value.decode())
+
     def destroy(self):
         if getattr(self, "_h", None):
             _lib.fv_chains_plan_destroy(self._h)
@@ -364,6 +383,24 @@ class fv_chains_plan:
             self.destroy()
         except Exception:
             pass
+
+
+def fv_autotune_cache_get(path, key):
+    """The tuning-cache entry for key: dict(block, quotes_per_thread,
+    blocks_per_sm, ms), or None when the file or the entry is absent."""
+    b, q, s = _I(), _I(), _I()
+    ms = ctypes.c_double()
+    _check(_lib.fv_autotune_cache_get(os.fsencode(path), key.encode(), ctypes.byref(b), ctypes.byref(q),
+                                      ctypes.byref(s), ctypes.byref(ms)), "fv_autotune_cache_get")
+    if b.value == 0:
+        return None
+    return dict(block=b.value, quotes_per_thread=q.value, blocks_per_sm=s.value, ms=ms.value)
+
+
+def fv_autotune_cache_put(path, key, block, quotes_per_thread, blocks_per_sm, ms=0.0):
+    _check(_lib.fv_autotune_cache_put(os.fsencode(path), key.encode(), int(block),
+                                      int(quotes_per_thread), int(blocks_per_sm), float(ms)),
+           "fv_autotune_cache_put")
 
 
 def _host_ptr(t, n, dtypes, name, allow_none=False):

@@ -119,3 +119,27 @@ def test_status_strings(lib):
     for code, word in ((0, b"SUCCESS"), (-1, b"ARG"), (-2, b"CUDA"), (-3, b"UNSUPPORTED"),
                        (-4, b"NOMEM")):
         assert word in lib.fv_status_string(code)
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    # the chains plan's tuning cache is host code: seeded, read back, replaced
+    # and rejected keys, all without a GPU
+    from paper_2604_27210_gb300 import fv
+    path = str(tmp_path / "tune.json")
+    key = "NVIDIA GB300|sm152|model0|chains2^13|quotes2^26|len2^12"
+    assert fv.fv_autotune_cache_get(path, key) is None  # no file yet
+    fv.fv_autotune_cache_put(path, key, 128, 2, 6, 35.5)
+    fv.fv_autotune_cache_put(path, "other|sm1", 512, 1, 1, 1.25)
+    assert fv.fv_autotune_cache_get(path, key) == dict(block=128, quotes_per_thread=2,
+                                                       blocks_per_sm=6, ms=35.5)
+    fv.fv_autotune_cache_put(path, key, 256, 4, 2, 30.0)  # replaced, the other entry kept
+    assert fv.fv_autotune_cache_get(path, key)["block"] == 256
+    assert fv.fv_autotune_cache_get(path, "other|sm1")["quotes_per_thread"] == 1
+    import json
+    with open(path) as f:
+        assert set(json.load(f)) == {key, "other|sm1"}  # the file is plain JSON
+    for bad in ('quote"d', "", "line\nbreak"):
+        with pytest.raises(fv.FvError):
+            fv.fv_autotune_cache_put(path, bad, 256, 2, 1, 1.0)
+    with pytest.raises(fv.FvError):
+        fv.fv_autotune_cache_put(path, "k", 0, 2, 1, 1.0)

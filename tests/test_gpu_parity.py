@@ -526,7 +526,58 @@ def test_chains_match_flat_and_oracle(fv, torch_dev, autotune):
     assert np.array_equal(np.concatenate([_np(ch["sigma"]) for ch in chains]), sig, equal_nan=True)
     info = plan.info()
     assert info["quotes"] == c["offsets"][-1] and info["tiles"] > 0
+    tune = plan.tuning()
+    if autotune:
+        assert tune["source"] in ("timed", "cached") and tune["best_ms"] > 0
+    else:
+        assert tune["source"] == "default" and (info["block"], info["quotes_per_thread"]) == (256, 4)
     plan.destroy()
+
+
+def test_chains_every_launch_shape_and_the_cache_file(fv, torch_dev, tmp_path, monkeypatch):
+    # Every compiled launch shape, forced through a seeded tuning-cache file,
+    # gives the flat kernel's results; then a timed plan records its winner
+    # in the file (FV_AUTOTUNE_CACHE), and FV_AUTOTUNE=0 overrides the argument.
+    c = wl.fill_prices(wl.chains(40, seed=29, max_len=5000), orc.price_f64)
+    chains = _chain_tensors(torch_dev, c)
+    s_flat, st_flat = fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR,
+                                        *_args(torch_dev, c, ("P", "S_or_F", "K", "T", "r")), None,
+                                        _dev(torch_dev, c["flag"]))
+    s_flat, st_flat = _np(s_flat), _np(st_flat)
+    path = str(tmp_path / "tune.json")
+    monkeypatch.setenv("FV_AUTOTUNE_CACHE", path)
+    key = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=False).tuning()["key"]
+    assert key.count("|") == 5
+    shapes = [(b, q) for b in (64, 128, 256, 512) for q in (1, 2, 4) if b * q <= 1024]
+    for block, qpt in shapes:
+        fv.fv_autotune_cache_put(path, key, block, qpt, 1, 1.0)
+        plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=True)
+        info, tune = plan.info(), plan.tuning()
+        assert tune["source"] == "cached" and tune["blocks_per_sm"] == 1
+        assert (info["block"], info["quotes_per_thread"]) == (block, qpt)
+        assert info["grid"] == min(info["tiles"], torch_dev[0].cuda.get_device_properties(0).multi_processor_count)
+        for ch in chains:
+            ch["sigma"].fill_(-7.0)
+            ch["status"].fill_(9)
+        plan.run()
+        sig = np.concatenate([_np(ch["sigma"]) for ch in chains])
+        st = np.concatenate([_np(ch["status"]) for ch in chains])
+        assert np.array_equal(st, st_flat), (block, qpt)
+        assert np.array_equal(np.isnan(sig), np.isnan(s_flat))
+        ok = ~np.isnan(sig) & (s_flat > 0)
+        assert np.all(np.abs(sig[ok] - s_flat[ok]) <= 1e-13 * s_flat[ok]), (block, qpt)
+        plan.destroy()
+    # an entry naming no compiled shape is ignored: the plan times the candidates
+    fv.fv_autotune_cache_put(path, key, 96, 3, 1, 1.0)
+    plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=True)
+    tune = plan.tuning()
+    assert tune["source"] == "timed" and tune["candidates"] >= len(shapes)
+    rec = fv.fv_autotune_cache_get(path, key)
+    assert (rec["block"], rec["quotes_per_thread"], rec["blocks_per_sm"]) == (
+        plan.info()["block"], plan.info()["quotes_per_thread"], tune["blocks_per_sm"])
+    plan.destroy()
+    monkeypatch.setenv("FV_AUTOTUNE", "0")
+    assert fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=True).tuning()["source"] == "default"
 
 
 def test_chains_with_empty_chains(fv, torch_dev):
@@ -853,17 +904,22 @@ def test_full_size_fp32_inputs_mixed(fv, torch_dev):
     s, st = fv.fv_implied_vol_ex(fv.FV_BLACK76, fv.FV_LBR, fv.FV_MIXED, *args, None, flag)
     w64 = {k: (None if w.get(k) is None else np.asarray(w[k], dtype=np.float64) if k != "flag"
                else w[k]) for k in ("P", "S_or_F", "K", "T", "r", "q", "flag")}
-    _sampled_parity(fv, torch_dev, w64, _np(s), _np(st), fv.FV_BLACK76)
+    _sampled_parity(fv, torch_dev, w64, _np(s), _np(st), fv.FV_BLACK76, n_sample=65536)
 
 
 def test_full_size_chains(fv, torch_dev):
+    # 10,000 chains (74.0 M quotes), the plan tuned on them (every shape timed)
     c = wl.fill_prices(wl.chains(10000, seed=3), orc.price)
     chains = _chain_tensors(torch_dev, c)
-    plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=False)
+    plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=True)
+    assert plan.tuning()["source"] in ("timed", "cached")
+    for ch in chains:
+        ch["sigma"].fill_(-7.0)
+        ch["status"].fill_(9)
     plan.run()
     sig = np.concatenate([_np(ch["sigma"]) for ch in chains])
     st = np.concatenate([_np(ch["status"]) for ch in chains])
-    _sampled_parity(fv, torch_dev, c, sig, st, fv.FV_BLACK76)
+    _sampled_parity(fv, torch_dev, c, sig, st, fv.FV_BLACK76, n_sample=65536)
     plan.destroy()
 
 
