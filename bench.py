@@ -265,43 +265,79 @@ def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
 
 
 def cpu_baseline(w_host, P_host, n_sample, seed=123):
-    """The oracle's FP64 LBR (as it stands) on a seeded sample of the workload,
-    all host cores."""
+    """The oracle's FP64 LBR (its own FP64 normalised Black, as it stands) on
+    the workload (all of it, or a seeded sample of n_sample quotes), all host
+    cores.  Returns (IV/s, cores, quotes, seconds, index, sigma, status)."""
     from oracle import oracle as orc
-    g = np.random.default_rng(seed)
-    idx = np.sort(g.choice(P_host.size, size=min(n_sample, P_host.size), replace=False))
+    n = P_host.size
+    if n_sample >= n:
+        idx = np.arange(n)
+    else:
+        idx = np.sort(np.random.default_rng(seed).choice(n, size=n_sample, replace=False))
     sub = {k: np.ascontiguousarray(np.asarray(w_host[k])[idx]) for k in
            ("S_or_F", "K", "T", "r", "q", "flag")}
     P = np.ascontiguousarray(P_host[idx])
     cores = orc.num_threads()
     t0 = time.perf_counter()
-    orc.iv_lbr(orc.BSM, P, sub["S_or_F"], sub["K"], sub["T"], sub["r"], sub["q"], sub["flag"],
-               n_iter=3, nthreads=cores)
+    sig, st, _ = orc.iv_lbr_f64(orc.BSM, P, sub["S_or_F"], sub["K"], sub["T"], sub["r"], sub["q"],
+                                sub["flag"], n_iter=3, nthreads=cores)
     dt = time.perf_counter() - t0
-    return idx.size / dt, cores, idx.size, dt
+    return idx.size / dt, cores, idx.size, dt, idx, sig, st
+
+
+def error_stats(w_host, P_host, idx, sig_gpu, st_gpu, sig_cpu, st_cpu):
+    """The timed GPU path against the oracle's FP64 LBR on the same quotes:
+    status agreement and the relative sigma difference where the normalised
+    vega b' exceeds 1e-8 (x and beta from the oracle's FP64 status rule)."""
+    from oracle import oracle as orc
+    sub = {k: np.asarray(w_host[k])[idx] for k in ("S_or_F", "K", "T", "r", "q", "flag")}
+    _, x, beta, _ = orc.status(orc.BSM, P_host[idx], sub["S_or_F"], sub["K"], sub["T"], sub["r"],
+                               sub["q"], sub["flag"])
+    g, c = sig_gpu[idx], sig_cpu
+    solved = (st_cpu == 0) & (c > 0) & (st_gpu[idx] == 0)
+    s = c[solved] * np.sqrt(sub["T"][solved])
+    h, t = -np.abs(x[solved]) / s, 0.5 * s
+    v = np.exp(-0.5 * (h * h + t * t)) / np.sqrt(2 * np.pi)
+    rel = np.abs(g[solved] - c[solved]) / c[solved]
+    gate = v > 1e-8
+    return {"quotes": int(idx.size), "status_agree": float(np.mean(st_gpu[idx] == st_cpu)),
+            "rel_diff_p50": float(np.median(rel[gate])) if gate.any() else None,
+            "rel_diff_p99_99": float(np.quantile(rel[gate], 0.9999)) if gate.any() else None,
+            "rel_diff_max": float(rel[gate].max()) if gate.any() else None,
+            "gate": "normalised vega > 1e-8", "against": "oracle FP64 LBR"}
 
 
 def reference_arm(args):
-    """CPU oracle arm: each step inverts a bounded seeded sample of the grid."""
+    """CPU oracle arm: each step inverts the grid (or a seeded sample of
+    --ref-sample quotes of it) with the oracle's FP64 LBR on all host cores."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import oracle as orc
     n_s, n_m = args.strikes, args.maturities
     w = wl.bsm_grid(n_s, n_m, seed=1)
-    sample = args.ref_sample
+    n = w["K"].size
+    sample = n if args.ref_sample <= 0 else min(args.ref_sample, n)
     g = np.random.default_rng(7)
     cores = orc.num_threads()
+    keys = ("S_or_F", "K", "T", "r", "q", "flag", "sigma_true", "below_mask", "below_factor")
+    full = None
+    if sample == n:
+        full = {key: np.asarray(w[key]) for key in keys}
+        full["model"] = wl.BSM
+        wl.fill_prices(full, orc.price_f64)
     times = []
     for k in range(args.warmup + args.steps):
-        idx = np.sort(g.choice(w["K"].size, size=sample, replace=False))
-        sub = {key: np.ascontiguousarray(np.asarray(w[key])[idx]) for key in
-               ("S_or_F", "K", "T", "r", "q", "flag", "sigma_true", "below_mask", "below_factor")}
-        sub["model"] = wl.BSM
-        wl.fill_prices(sub, orc.price_f64)
+        if full is not None:
+            sub = full
+        else:
+            idx = np.sort(g.choice(n, size=sample, replace=False))
+            sub = {key: np.ascontiguousarray(np.asarray(w[key])[idx]) for key in keys}
+            sub["model"] = wl.BSM
+            wl.fill_prices(sub, orc.price_f64)
         t0 = time.perf_counter()
-        orc.iv_lbr(orc.BSM, sub["P"], sub["S_or_F"], sub["K"], sub["T"], sub["r"], sub["q"],
-                   sub["flag"], n_iter=3, nthreads=cores)
+        orc.iv_lbr_f64(orc.BSM, sub["P"], sub["S_or_F"], sub["K"], sub["T"], sub["r"], sub["q"],
+                       sub["flag"], n_iter=3, nthreads=cores)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
@@ -311,11 +347,12 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "BSM grid %d strikes x %d maturities (sampled %d quotes per step)"
-                                   % (n_s, n_m, sample), "solver": "LBR (CPU oracle, FP64 steps, "
-                                                                   "binary128 normalised Black)"},
+            "config": {"workload": "BSM grid %d strikes x %d maturities (%d quotes per step)"
+                                   % (n_s, n_m, sample),
+                       "solver": "LBR (CPU oracle, FP64 steps and FP64 normalised Black)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d seeded quotes of the grid per step" % sample},
+                             "sample": ("the whole grid per step" if sample == n else
+                                        "%d seeded quotes of the grid per step" % sample)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -329,8 +366,8 @@ def main():
     ap.add_argument("--path", default="lbr", choices=["lbr", "mixed", "fp32", "halley"])
     ap.add_argument("--strikes", type=int, default=4096)
     ap.add_argument("--maturities", type=int, default=4096)
-    ap.add_argument("--ref-sample", type=int, default=262144)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 23)
+    ap.add_argument("--ref-sample", type=int, default=0, help="quotes per reference step (0: all)")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 30, help="quotes of the CPU baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the selected path (for profiler runs)")
     args = ap.parse_args()
@@ -404,12 +441,18 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, ws)
 
     cpu = None
+    errors = None
     if rank == 0 and ws == 1:
         P_host = t["P"].cpu().numpy()
-        rate, cores, m, dt = cpu_baseline(w, P_host, args.cpu_sample)
+        rate, cores, m, dt, idx, sig_cpu, st_cpu = cpu_baseline(w, P_host, args.cpu_sample)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d seeded quotes of the grid, oracle FP64 LBR (3 Householder steps, "
-                         "binary128 normalised Black), %.1f s" % (m, dt)}
+               "sample": "%d quotes of the grid (%s), oracle FP64 LBR (3 Householder steps, its own "
+                         "FP64 normalised Black), %.1f s" % (m, "all" if m == n else "seeded sample",
+                                                              dt)}
+        # the timed path's outputs of its last step against the CPU solver
+        run_path(fv, t, args.path, out, st)
+        torch.cuda.synchronize()
+        errors = error_stats(w, P_host, idx, out.cpu().numpy(), st.cpu().numpy(), sig_cpu, st_cpu)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -430,7 +473,7 @@ def main():
                 "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP[args.path] * args.steps,
                 "e2e": {"value": ws * n / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "cpu_baseline": cpu, "paths": extras}
+                "cpu_baseline": cpu, "errors": errors, "paths": extras}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist

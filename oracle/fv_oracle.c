@@ -233,6 +233,7 @@ static q128 solve_definition_q(q128 beta, q128 x) {
 /* ------------------------------------------------------------------------- */
 /* exported: normalised Black, price, status                                  */
 /* ------------------------------------------------------------------------- */
+typedef struct nb_eval_s nb_eval_t; /* a normalised-Black evaluation (below) */
 typedef struct {
   int model;
   const double *P, *SF, *K, *T, *r, *q, *sigma, *x, *s, *grad;
@@ -242,6 +243,7 @@ typedef struct {
   uint8_t* status;
   int8_t* region;
   int n_iter;
+  const nb_eval_t* ev;
 } ctx_t;
 
 static void nb_range(void* c_, int64_t i0, int64_t i1) {
@@ -557,6 +559,113 @@ static double Phi_inv_d(double p) {
   return z;
 }
 
+/* ------------------------------------------------------------------------- */
+/* The normalised Black function in plain FP64 (the oracle's own evaluation, */
+/* for the FP64 LBR that serves as the CPU baseline)                          */
+/* ------------------------------------------------------------------------- */
+static const double SQRT_PI = 1.77245385090551602729816748334114518;
+static const double SQRT_PI_OVER_2 = 1.25331413731550025120788264240552263;
+static const double LN_SQRT_2PI = 0.918938533204672741780329736405617640;
+
+/* erfcx(z) = exp(z^2) erfc(z) for z >= 0 (the solvers' arguments).  Below
+ * z = 2: glibc's erfc times exp(z^2) (the rounding of z^2 < 4 costs a few
+ * ulp at most).  From z = 2 on: the Laplace continued fraction (Abramowitz &
+ * Stegun 7.1.14)
+ *   sqrt(pi) erfcx(z) = 1/(z + (1/2)/(z + (2/2)/(z + (3/2)/(z + ...)))),
+ * evaluated by the modified Lentz method, which never forms exp(-z^2). */
+static double erfcx_f64(double z) {
+  if (z != z) return z;
+  if (z < 2.0) return exp(z * z) * erfc(z);
+  if (isinf(z)) return 0.0;
+  const double tiny = 1e-300;
+  double f = z, C = z, D = 0.0;
+  for (int k = 1; k < 1000; k++) {
+    const double a = 0.5 * k;
+    D = z + a * D;
+    if (D == 0) D = tiny;
+    D = 1.0 / D;
+    C = z + a / C;
+    if (C == 0) C = tiny;
+    const double delta = C * D;
+    f *= delta;
+    if (fabs(delta - 1.0) < 2e-16) break;
+  }
+  return 1.0 / (SQRT_PI * f);
+}
+
+/* Mills ratio R(z) = Phi(z) / phi(z) = sqrt(pi/2) erfcx(-z/sqrt 2) */
+static double mills_f64(double z) { return SQRT_PI_OVER_2 * erfcx_f64(-z * 0.70710678118654752440); }
+
+/* D = R(h+t) - R(h-t) for h + t <= 0, so that b = b' D with the normalised
+ * vega b' = e^{x/2} phi(h+t) = e^{-x/2} phi(h-t) = exp(-(h^2+t^2)/2)/sqrt(2pi)
+ * (x = 2 h t).  For small t the difference cancels; there the odd part of
+ * its Taylor series in t is summed instead,
+ *   R(h+t) - R(h-t) = 2 sum_{k odd} R^(k)(h) t^k / k!,
+ * with the derivatives from R' = 1 + h R (since phi' = -z phi), hence
+ * R^(k+1) = k R^(k-1) + h R^(k) for k >= 1.  The series is taken where
+ * t < 0.1 and |h| <= 10 (its recurrence loses about log10(h^2) digits);
+ * elsewhere the erfcx difference (which loses log10(|h|/2t) digits). */
+static double mills_diff_f64(double h, double t) {
+  if (t < 0.1 && fabs(h) <= 10.0) {
+    double Rm = mills_f64(h);   /* R^(k-1), starting at R^(0) */
+    double Rk = 1.0 + h * Rm;   /* R^(k),   starting at R^(1) */
+    double tk = t, fact = 1.0;  /* t^k and k! */
+    double sum = Rk * t;
+    for (int k = 1; k < 40; k += 2) {
+      const double R2 = k * Rm + h * Rk;        /* R^(k+1) */
+      const double R3 = (k + 1) * Rk + h * R2;  /* R^(k+2) */
+      tk *= t * t;
+      fact *= (double)(k + 1) * (k + 2);
+      const double term = R3 * tk / fact;
+      sum += term;
+      Rm = R2;
+      Rk = R3;
+      if (fabs(term) <= 1e-18 * fabs(sum)) break;
+    }
+    return 2.0 * sum;
+  }
+  return mills_f64(h + t) - mills_f64(h - t);
+}
+
+/* b(x, s) of the call with x <= 0, s > 0: b' D, except past the inflection
+ * point (h + t > 0) outside the small-t series' domain, where b is not small
+ * and the CDF-direct form e^{x/2} Phi(h+t) - e^{-x/2} Phi(h-t) loses at most
+ * a small factor (with t < 0.1 it would cancel: there the series applies). */
+static int cdf_direct(double h, double t) { return h + t > 0 && !(t < 0.1 && fabs(h) <= 10.0); }
+static double nb_f64(double x, double s) {
+  const double h = x / s, t = 0.5 * s;
+  if (cdf_direct(h, t)) return exp(0.5 * x) * Phi_d(h + t) - exp(-0.5 * x) * Phi_d(h - t);
+  return vega_d(x, s) * mills_diff_f64(h, t);
+}
+/* ln b and b'/b without underflow: ln b = ln D - (h^2+t^2)/2 - ln sqrt(2pi) */
+static void nb_log_f64(double x, double s, double* L, double* qb) {
+  const double h = x / s, t = 0.5 * s;
+  if (cdf_direct(h, t)) {
+    const double b = nb_f64(x, s);
+    *L = log(b);
+    *qb = vega_d(x, s) / b;
+    return;
+  }
+  const double D = mills_diff_f64(h, t);
+  *L = log(D) - 0.5 * (h * h + t * t) - LN_SQRT_2PI;
+  *qb = 1.0 / D;
+}
+/* b_max - b = e^{x/2} Phi(-(h+t)) + e^{-x/2} Phi(h-t): two positive terms */
+static double nbc_f64(double x, double s) {
+  const double h = x / s, t = 0.5 * s;
+  return exp(0.5 * x) * Phi_d(-(h + t)) + exp(-0.5 * x) * Phi_d(h - t);
+}
+
+/* The normalised Black evaluation the step-by-step solvers use: b, ln b with
+ * b'/b, and b_max - b of the reduced call (x <= 0). */
+struct nb_eval_s {
+  double (*nb)(double x, double s);
+  void (*nb_log)(double x, double s, double* L, double* qb);
+  double (*nbc)(double x, double s);
+};
+static const nb_eval_t NB_BINARY128 = {nb_d, nb_log_d, nbc_d};
+static const nb_eval_t NB_FP64 = {nb_f64, nb_log_f64, nbc_f64};
+
 /* cubic Hermite interpolation of s(beta) on [b0, b1] from end values and
  * slopes ds/dbeta = 1/b' (the interior initial guess of Section 2.2) */
 static double hermite_guess(double beta, double b0, double b1, double s0, double s1, double d0,
@@ -573,7 +682,7 @@ static double hermite_guess(double beta, double b0, double b1, double s0, double
 /* "Let's Be Rational" (Section 2.2, first item), FP64 step by step           */
 /* ------------------------------------------------------------------------- */
 /* beta in (0, e^{x/2}), x <= 0 (the reduced out-of-the-money call). */
-static double lbr_otm(double beta, double x, int n_iter, int* region) {
+static double lbr_otm(double beta, double x, int n_iter, int* region, const nb_eval_t* ev) {
   const double bmax = exp(0.5 * x);
   double sc, bc, vc, sl = 0, bl = 0, vl = 0;
   /* boundary points: inflection s_c = sqrt(2|x|), where the tangent of b meets
@@ -581,11 +690,11 @@ static double lbr_otm(double beta, double x, int n_iter, int* region) {
    * s_l, s_c, s_h) */
   if (x < 0) {
     sc = sqrt(-2.0 * x);
-    bc = nb_d(x, sc);
+    bc = ev->nb(x, sc);
     vc = vega_d(x, sc);
     sl = sc - bc / vc;
     if (sl > 0) {
-      bl = nb_d(x, sl);
+      bl = ev->nb(x, sl);
       vl = vega_d(x, sl);
     } else {
       sl = 0;
@@ -596,7 +705,7 @@ static double lbr_otm(double beta, double x, int n_iter, int* region) {
     vc = INV_SQRT_2PI;
   }
   const double sh = sc + (bmax - bc) / vc;
-  const double bh = nb_d(x, sh), vh = vega_d(x, sh);
+  const double bh = ev->nb(x, sh), vh = vega_d(x, sh);
 
   /* four-region initial guess */
   int reg;
@@ -618,7 +727,7 @@ static double lbr_otm(double beta, double x, int n_iter, int* region) {
   } else {
     /* highest wing: b_max - b ~ c' Phi(-s/2) as s -> inf; c' matched at s_h */
     reg = 3;
-    const double ch = nbc_d(x, sh) / Phi_d(-0.5 * sh);
+    const double ch = ev->nbc(x, sh) / Phi_d(-0.5 * sh);
     s = -2.0 * Phi_inv_d((bmax - beta) / ch);
   }
   if (region) *region = reg;
@@ -636,7 +745,7 @@ static double lbr_otm(double beta, double x, int n_iter, int* region) {
     if (reg == 0) {
       /* g = 1/ln b - 1/ln beta */
       double L, qb;
-      nb_log_d(x, s, &L, &qb);
+      ev->nb_log(x, s, &L, &qb);
       if (!isfinite(L)) { /* b = 0 even in binary128: s far too small */
         s *= 1.5;
         continue;
@@ -649,7 +758,7 @@ static double lbr_otm(double beta, double x, int n_iter, int* region) {
       h3 = h2 * h2 + du - (qb * u - qb * qb) * k1 + 2.0 * qb * qb / (L * L);
     } else if (reg == 3) {
       /* g = ln((b_max - beta)/(b_max - b)) */
-      const double cb = nbc_d(x, s);
+      const double cb = ev->nbc(x, s);
       const double w = bp / cb;
       const double g = log(c_beta / cb);
       nu = -g / w;
@@ -657,7 +766,7 @@ static double lbr_otm(double beta, double x, int n_iter, int* region) {
       h3 = h2 * h2 + du + w * h2;
     } else {
       /* g = b - beta */
-      const double b = nb_d(x, s);
+      const double b = ev->nb(x, s);
       nu = -(b - beta) / bp;
       h2 = u;
       h3 = u * u + du;
@@ -688,7 +797,7 @@ static void lbr_range(void* c_, int64_t i0, int64_t i1) {
       continue;
     }
     int reg = -1;
-    double s = lbr_otm(d.beta_otm, d.x_otm, c->n_iter, &reg);
+    double s = lbr_otm(d.beta_otm, d.x_otm, c->n_iter, &reg, c->ev);
     if (c->region) c->region[i] = (int8_t)reg;
     c->out[i] = s / sqrt(c->T[i]);
   }
@@ -709,7 +818,49 @@ void or_iv_lbr(int model, const double* P, const double* S_or_F, const double* K
   c.status = status;
   c.region = region;
   c.n_iter = n_iter;
+  c.ev = &NB_BINARY128;
   parallel_for(n, nthreads, lbr_range, &c);
+}
+
+void or_iv_lbr_f64(int model, const double* P, const double* S_or_F, const double* K,
+                   const double* T, const double* r, const double* q, const int8_t* flag,
+                   int64_t n, int n_iter, double* sigma, uint8_t* status, int8_t* region,
+                   int nthreads) {
+  ctx_t c = {0};
+  c.model = model;
+  c.P = P;
+  c.SF = S_or_F;
+  c.K = K;
+  c.T = T;
+  c.r = r;
+  c.q = (model == ORC_BSM) ? q : NULL;
+  c.flag = flag;
+  c.out = sigma;
+  c.status = status;
+  c.region = region;
+  c.n_iter = n_iter;
+  c.ev = &NB_FP64;
+  parallel_for(n, nthreads, lbr_range, &c);
+}
+
+static void nb_f64_range(void* c_, int64_t i0, int64_t i1) {
+  ctx_t* c = (ctx_t*)c_;
+  for (int64_t i = i0; i < i1; i++) {
+    const double x = c->x[i], s = c->s[i];
+    const int th = c->flag[i] >= 0 ? 1 : -1;
+    /* intrinsic part and the reduced call: b(x,s,th) = iota + b(-|x|, s) */
+    const double iota = th * x > 0 ? 2.0 * sinh(0.5 * fabs(x)) : 0.0;
+    c->out[i] = s > 0 ? iota + nb_f64(-fabs(x), s) : iota;
+  }
+}
+void or_normalised_black_f64(const double* x, const double* s, const int8_t* theta, int64_t n,
+                             double* out, int nthreads) {
+  ctx_t c = {0};
+  c.x = x;
+  c.s = s;
+  c.flag = theta;
+  c.out = out;
+  parallel_for(n, nthreads, nb_f64_range, &c);
 }
 
 /* ------------------------------------------------------------------------- */

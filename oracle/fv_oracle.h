@@ -98,6 +98,21 @@ void or_iv_lbr(int model, const double* P, const double* S_or_F, const double* K
                const int8_t* flag, int64_t n, int n_iter, double* sigma,
                uint8_t* status, int8_t* region, int nthreads);
 
+/* The same LBR steps with the normalised Black function evaluated in plain
+ * FP64 by the oracle's own routine (erfcx difference with a continued-
+ * fraction erfcx, the small-t odd series of the Mills ratio, the CDF-direct
+ * form past the inflection point): an FP64 CPU implementation of the whole
+ * solver, the CPU baseline of the benchmark. */
+void or_iv_lbr_f64(int model, const double* P, const double* S_or_F, const double* K,
+                   const double* T, const double* r, const double* q, const int8_t* flag,
+                   int64_t n, int n_iter, double* sigma, uint8_t* status, int8_t* region,
+                   int nthreads);
+
+/* That FP64 normalised Black b(x, s, theta) (intrinsic part plus the reduced
+ * call), exported so that it can be pinned against the binary128 one. */
+void or_normalised_black_f64(const double* x, const double* s, const int8_t* theta, int64_t n,
+                             double* out, int nthreads);
+
 /* Halley x8 from the Brenner-Subrahmanyam guess, bisection fallback on the
  * quotes that fail the convergence test; fallback (may be NULL) flags them. */
 void or_iv_halley(int model, const double* P, const double* S_or_F,

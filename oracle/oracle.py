@@ -42,6 +42,9 @@ def _load():
         lib.or_iv.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _U8, _INT]
         lib.or_conditioning.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _D, _N, _D, _D, _INT]
         lib.or_iv_lbr.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _INT, _D, _U8, _I8, _INT]
+        lib.or_iv_lbr_f64.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _INT, _D, _U8, _I8,
+                                      _INT]
+        lib.or_normalised_black_f64.argtypes = [_D, _D, _I8, _N, _D, _INT]
         lib.or_iv_halley.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _U8, _U8, _INT]
         lib.or_greeks.argtypes = [_INT, _D, _D, _D, _D, _D, _D, _I8, _N, _D, _D, _D, _D, _D, _INT]
         lib.or_iv_grad.argtypes = [_INT, _D, _D, _D, _D, _D, _I8, _D, _U8, _D, _N,
@@ -83,6 +86,16 @@ def normalised_black(x, s, theta=1, nthreads=0):
     out = np.empty(n, np.float64)
     _load().or_normalised_black(keep[0][1], keep[1][1], keep[2][1], n, out.ctypes.data_as(_D),
                                 nthreads)
+    return out
+
+
+def normalised_black_f64(x, s, theta=1, nthreads=0):
+    """The oracle's own FP64 evaluation of the normalised Black function."""
+    n = _len(x, s, theta)
+    keep = [_f64(x, n), _f64(s, n), _i8(theta, n)]
+    out = np.empty(n, np.float64)
+    _load().or_normalised_black_f64(keep[0][1], keep[1][1], keep[2][1], n, out.ctypes.data_as(_D),
+                                    nthreads)
     return out
 
 
@@ -158,6 +171,13 @@ def iv_lbr(model, P, S_or_F, K, T, r, q, flag, n_iter=3, nthreads=0):
                       nthreads=nthreads, aux=np.int8)
 
 
+def iv_lbr_f64(model, P, S_or_F, K, T, r, q, flag, n_iter=3, nthreads=0):
+    """The LBR steps with the oracle's FP64 normalised Black (the CPU
+    baseline); returns sigma, status, region."""
+    return _iv_common(_load().or_iv_lbr_f64, model, P, S_or_F, K, T, r, q, flag, extra=(n_iter,),
+                      nthreads=nthreads, aux=np.int8)
+
+
 def iv_halley(model, P, S_or_F, K, T, r, q, flag, nthreads=0):
     """FP64 Halley x8 + bisection fallback; returns sigma, status, fallback flag."""
     return _iv_common(_load().or_iv_halley, model, P, S_or_F, K, T, r, q, flag, nthreads=nthreads,
@@ -199,7 +219,8 @@ def iv_grad(model, S_or_F, K, T, r, q, flag, sigma, status_, grad_sigma, nthread
 
 
 __all__ = ["BLACK76", "BLACK_SCHOLES", "BSM", "OK", "BELOW_INTRINSIC", "ABOVE_MAX", "INVALID",
-           "normalised_black", "price", "price_f64", "status", "iv", "iv_lbr", "iv_halley", "conditioning",
+           "normalised_black", "normalised_black_f64", "price", "price_f64", "status", "iv", "iv_lbr",
+           "iv_lbr_f64", "iv_halley", "conditioning",
            "greeks", "iv_grad", "num_threads"]
 
 if os.environ.get("FV_ORACLE_EAGER"):

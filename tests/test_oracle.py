@@ -412,6 +412,54 @@ def test_lbr_reaches_machine_precision_in_two_iterations(grid_truth, n_iter):
     assert rel[gate].max() <= 1e-12
 
 
+def test_fp64_normalised_black_against_binary128():
+    # the oracle's own FP64 evaluation (erfcx difference with a continued-
+    # fraction erfcx, small-t Mills-ratio series, CDF-direct past the
+    # inflection point) against the binary128 definition
+    xs = np.concatenate([-np.logspace(-8, np.log10(40), 60), [0.0], np.logspace(-8, np.log10(40), 60)])
+    ss = np.logspace(-4, np.log10(50), 90)
+    X, S = np.meshgrid(xs, ss, indexing="ij")
+    X, S = X.ravel(), S.ravel()
+    for th in (1, -1):
+        ref = orc.normalised_black(X, S, th)
+        got = orc.normalised_black_f64(X, S, th)
+        m = ref > 1e-300
+        rel = np.abs(got[m] - ref[m]) / ref[m]
+        h = np.abs(X[m]) / S[m]
+        # |h| <= 10: the series and the erfcx difference both keep 13 digits
+        # (a few hundred ulp at most, the recurrence's and the exponent's loss)
+        assert rel[h <= 10].max() <= 1e-13, rel[h <= 10].max()
+        # beyond, the erfcx difference loses log10(|h|/2t) digits for small t
+        assert rel.max() <= 2e-10, rel.max()
+    # at the money b = erf(s / (2 sqrt 2)) (series below t = 0.1, CDF-direct above)
+    for s_ in (1e-4, 0.05, 0.199, 0.2, 1.0, 4.0, 20.0):
+        got = orc.normalised_black_f64(0.0, s_, 1)[0]
+        assert got == pytest.approx(float(mp.erf(mp.mpf(s_) / (2 * mp.sqrt(2)))), rel=2e-15), s_
+    # the erfcx difference on both sides of the erfcx switch at z = 2: t = 1/2
+    # and -(h + t)/sqrt2 = z, so the first erfcx argument crosses 2
+    zs = np.array([1.5, 1.999999, 2.0, 2.000001, 2.5, 6.0, 30.0])
+    h = -np.sqrt(2.0) * zs - 0.5
+    x, s_ = 2.0 * h * 0.5, np.full(zs.size, 1.0)
+    ref = orc.normalised_black(x, s_, 1)
+    got = orc.normalised_black_f64(x, s_, 1)
+    m = ref > 1e-300
+    assert np.all(np.abs(got[m] - ref[m]) <= 1e-13 * ref[m])
+
+
+def test_fp64_lbr_against_the_definition(grid_truth):
+    # the FP64 CPU solver (the benchmark's CPU baseline): the LBR steps with
+    # the FP64 normalised Black reach the definition within 16 eps (1 + kappa)
+    w, sig, st, v, kap, solved = grid_truth
+    sl, st2, reg = orc.iv_lbr_f64(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"],
+                                  n_iter=3)
+    assert np.array_equal(st, st2)
+    assert set(np.unique(reg[solved])) == {0, 1, 2, 3}
+    rel = np.abs(sl[solved] - sig[solved]) / sig[solved]
+    gate = (v[solved] > 1e-8) & (kap[solved] <= 1e3)
+    assert rel[gate].max() <= 1e-12
+    assert np.all(rel[v[solved] > 1e-8] <= 16 * EPS * (1 + kap[solved][v[solved] > 1e-8]))
+
+
 def test_lbr_one_iteration_is_not_enough(grid_truth):
     w, sig, st, v, kap, solved = grid_truth
     sl, _, _ = orc.iv_lbr(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"], n_iter=1)

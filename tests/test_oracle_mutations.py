@@ -85,6 +85,22 @@ MUTANTS = [
      "    if (nb_q_e(x, mid, 1, ep, em) > beta)\n      lo = mid;"),
     ("definition: intrinsic value not removed in the money",
      "q128 beta_otm = ((q128)th * x > 0) ? beta - iota : beta;", "q128 beta_otm = beta;"),
+    # the oracle's FP64 normalised Black (the CPU baseline's evaluation)
+    ("FP64 normalised Black: Mills-ratio recurrence with k for k + 1",
+     "const double R3 = (k + 1) * Rk + h * R2;", "const double R3 = k * Rk + h * R2;"),
+    ("FP64 erfcx: continued fraction with partial numerators k for k/2",
+     "const double a = 0.5 * k;", "const double a = 1.0 * k;"),
+    ("FP64 normalised Black: CDF-direct form with the wrong sign",
+     "if (cdf_direct(h, t)) return exp(0.5 * x) * Phi_d(h + t) - exp(-0.5 * x) * Phi_d(h - t);",
+     "if (cdf_direct(h, t)) return exp(0.5 * x) * Phi_d(h + t) + exp(-0.5 * x) * Phi_d(h - t);"),
+    ("FP64 normalised Black: ln b with +ln sqrt(2 pi)",
+     "*L = log(D) - 0.5 * (h * h + t * t) - LN_SQRT_2PI;",
+     "*L = log(D) - 0.5 * (h * h + t * t) + LN_SQRT_2PI;"),
+    ("FP64 erfcx: exp(-z^2) for exp(z^2)",
+     "if (z < 2.0) return exp(z * z) * erfc(z);", "if (z < 2.0) return exp(-z * z) * erfc(z);"),
+    ("FP64 complement: wrong sign in the second tail",
+     "return exp(0.5 * x) * Phi_d(-(h + t)) + exp(-0.5 * x) * Phi_d(h - t);",
+     "return exp(0.5 * x) * Phi_d(-(h + t)) + exp(-0.5 * x) * Phi_d(t - h);"),
     # Let's Be Rational, step by step
     ("LBR: normalised vega with t^2 of the wrong sign",
      "return exp(-0.5 * (h * h + t * t)) * INV_SQRT_2PI;", "return exp(-0.5 * (h * h - t * t)) * INV_SQRT_2PI;"),
