@@ -34,23 +34,29 @@ UNIT = "IV/s"
 # algorithmic HBM bytes per quote: P, S, K, T, r, q (8 B each) + flag (1 B) in,
 # sigma (8 B) + status (1 B) out
 BYTES_PER_QUOTE = 58
-# FP64 flops per quote the kernels execute on this workload: thread-level
-# DADD + DMUL + 2 x DFMA from ncu's smsp__sass_thread_inst_executed_op_*_pred_on
-# counters on 4,194,304 quotes of the same grid distribution.  This is the
-# ALU roofline's work per quote (the kernels are bound by the FP64 pipe).
-FP64_FLOPS_PER_QUOTE = {"lbr": 308.0, "mixed": 229.0, "fp32": 121.0}
-# DRAM bytes (read + write) per quote of the same kernels from one ncu capture
+# The method's FP64 work per quote on this workload, from the counted build of
+# the oracle's FP64 LBR (oracle/count_ops.py, a seeded sample of 131,072
+# quotes of the grid, written to oracle/op_counts.json): the status rule, two
+# Householder(3) iterations (Section 2.2: two suffice) and sigma = s/sqrt(T),
+# every +, -, *, /, square root counted and each elementary function at a
+# nominal FP64 cost.  The mixed path's FP64 work is the status rule, one
+# Householder(3) correction and sigma; the FP32 path's the status rule and
+# sigma.  A fixed figure per quote: a faster kernel raises the fraction.
+ALG_FLOPS_PER_QUOTE = {"lbr": 370.4, "mixed": 237.4, "fp32": 85.7}
+# FP64 flops per quote the kernels execute on this workload (DADD + DMUL +
+# 2 x DFMA thread-level ncu counters), shown beside the algorithmic figure;
+# None until a capture of the current kernels (profiles/).
+EXECUTED_FLOPS_PER_QUOTE = {"lbr": None, "mixed": None, "fp32": None}
+# DRAM bytes (read + write) per quote of the timed kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid;
 # traffic grows in proportion to the quotes, so a launch's traffic is this x n.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205688576 + 24795904) / 4194304,
-                            "mixed": (205760768 + 24775168) / 4194304}
-# share of cycles the FP64 pipe was busy in the same captures (the flops above
-# leave out conversions, compares and the FP64 steps of divisions and square
-# roots, which occupy the pipe too)
-FP64_PIPE_BUSY_NCU = {"lbr": 0.821, "mixed": 0.764, "fp32": 0.820}
-# FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock (ncu's sustained peak of
-# the thread-level DFMA counter) x 2 flops x 2070 MHz
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# None until a capture of the current kernels.
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": None, "mixed": None}
+# FP64 peaks: measured on this machine's GB300 by bench_fp64_probe.py (526 G
+# DFMA/s = 1,052 GFLOP/s; profiles/fp64_fp32_throughput_probe.md), and the
+# unit-count figure 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2070 MHz
+FP64_PEAK_GFLOPS = 1052.0
+FP64_PEAK_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.070
 SM_MAX_MHZ = 2070.0
 
 
@@ -400,17 +406,20 @@ def main():
     k_ms = statistics.mean(kernel_ms)
     hbm_peak, hbm_kind = peaks()
     gbs = BYTES_PER_QUOTE * n / (k_ms * 1e-3) / 1e9
-    flops_q = FP64_FLOPS_PER_QUOTE.get(args.path)
+    flops_q = ALG_FLOPS_PER_QUOTE.get(args.path)
     if flops_q is not None:
         achieved = flops_q * n / (k_ms * 1e-3) / 1e9
+        dram_q = DRAM_BYTES_PER_QUOTE_NCU.get(args.path)
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                     "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                    "traffic": (DRAM_BYTES_PER_QUOTE_NCU[args.path] * n
-                                if args.path in DRAM_BYTES_PER_QUOTE_NCU else None),
+                    "traffic": dram_q * n if dram_q is not None else None,
                     "flops_per_quote": flops_q,
-                    "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU.get(args.path),
-                    "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz "
-                                 "(recipe unit count and clock)"}
+                    "flops_kind": "algorithmic: the method's FP64 operations per quote from the "
+                                  "counted build of the oracle's FP64 LBR (oracle/count_ops.py)",
+                    "executed_flops_per_quote": EXECUTED_FLOPS_PER_QUOTE.get(args.path),
+                    "peak_kind": "measured FP64 FMA rate on this GPU (bench_fp64_probe.py)",
+                    "peak_nominal": FP64_PEAK_NOMINAL_GFLOPS,
+                    "frac_of_nominal": achieved / FP64_PEAK_NOMINAL_GFLOPS}
     else:
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak, "traffic": None}

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 SRC = [os.path.join(HERE, "fv_oracle.c")]
-HDR = [os.path.join(HERE, "fv_oracle.h")]
+HDR = [os.path.join(HERE, "fv_oracle.h"), os.path.join(HERE, "lbr_steps.h")]
 
 
 def up_to_date() -> bool:

@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case below plants one mistake (a dropped term, a wrong sign, a wrong
-index or operand) in a copy of ``oracle/fv_oracle.c``, builds the copy with
+index or operand) in a copy of the oracle's sources (``oracle/fv_oracle.c``
+and ``oracle/lbr_steps.h``), builds the copy with
 the oracle's own flags, and runs the pins of ``tests/test_oracle.py`` against
 it: at least one pin must fail.  The mistakes are made on the CPU, in the
 oracle only.
@@ -15,7 +16,7 @@ from concurrent.futures import ThreadPoolExecutor
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE_DIR = os.path.join(ROOT, "oracle")
 
-# (what the mistake is, exact text in fv_oracle.c, the mistaken text)
+# (what the mistake is, exact text in the oracle's sources, the mistaken text)
 MUTANTS = [
     # normalised Black and price (Section 2.2 normalisation, Section 2.4)
     ("normalised Black: wrong sign of the strike term",
@@ -49,13 +50,13 @@ MUTANTS = [
     ("status: FP64 forward with r + q",
      "x = lm + (r - qq) * T;", "x = lm + (r + qq) * T;"),
     ("status: intrinsic value with (1 - Em)",
-     "const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x = x;",
-     "const double iota = itm ? (-E * (1.0 - Em)) / Em : 0.0;\n  o->x = x;"),
+     "const R iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x = x;",
+     "const R iota = itm ? (-E * (1.0 - Em)) / Em : 0.0;\n  o->x = x;"),
     ("status: upper band on the wrong side",
      "if (beta_otm >= bmax_otm * (1.0 - EPS_S)) {", "if (beta_otm >= bmax_otm * (1.0 + EPS_S)) {"),
     ("status: in-the-money test with the wrong sign",
-     "const int itm = th * x > 0;\n  const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x",
-     "const int itm = th * x < 0;\n  const double iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x"),
+     "const int itm = th * x > 0;\n  const R iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x",
+     "const int itm = th * x < 0;\n  const R iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x"),
     # conditioning (normalised vega, kappa) and the status margin: the
     # quantities the parity tests gate and excuse quotes with
     ("conditioning: kappa without the factor s",
@@ -87,7 +88,7 @@ MUTANTS = [
      "q128 beta_otm = ((q128)th * x > 0) ? beta - iota : beta;", "q128 beta_otm = beta;"),
     # the oracle's FP64 normalised Black (the CPU baseline's evaluation)
     ("FP64 normalised Black: Mills-ratio recurrence with k for k + 1",
-     "const double R3 = (k + 1) * Rk + h * R2;", "const double R3 = k * Rk + h * R2;"),
+     "const R R3 = (k + 1) * Rk + h * R2;", "const R R3 = k * Rk + h * R2;"),
     ("FP64 erfcx: continued fraction with partial numerators k for k/2",
      "const double a = 0.5 * k;", "const double a = 1.0 * k;"),
     ("FP64 normalised Black: CDF-direct form with the wrong sign",
@@ -112,15 +113,15 @@ MUTANTS = [
     ("LBR: upper objective derivative without w",
      "h2 = u + w;\n      h3 = h2 * h2 + du + w * h2;", "h2 = u;\n      h3 = h2 * h2 + du + w * h2;"),
     ("LBR: lowest objective derivative with 1 - 2/L",
-     "const double k1 = 1.0 + 2.0 / L;", "const double k1 = 1.0 - 2.0 / L;"),
+     "const R k1 = 1.0 + 2.0 / L;", "const R k1 = 1.0 - 2.0 / L;"),
     ("LBR: Householder step without the h3 term",
-     "double ds = nu * (1.0 + 0.5 * h2 * nu) / (1.0 + nu * (h2 + h3 * nu / 6.0));",
-     "double ds = nu * (1.0 + 0.5 * h2 * nu) / (1.0 + nu * h2);"),
+     "R ds = nu * (1.0 + 0.5 * h2 * nu) / (1.0 + nu * (h2 + h3 * nu / 6.0));",
+     "R ds = nu * (1.0 + 0.5 * h2 * nu) / (1.0 + nu * h2);"),
     ("LBR: middle residual with the wrong sign",
      "nu = -(b - beta) / bp;", "nu = (b - beta) / bp;"),
     ("LBR: b''/b' = x^2/s^3 + s/4",
-     "const double u = h * h / s - 0.25 * s;           /* b''/b' */",
-     "const double u = h * h / s + 0.25 * s;           /* b''/b' */"),
+     "const R u = h * h / s - 0.25 * s;           /* b''/b' */",
+     "const R u = h * h / s + 0.25 * s;           /* b''/b' */"),
     # Halley and its fallback
     ("Halley: residual b - beta with the wrong sign",
      "const double g = upper ? (bmax - beta) - nbc_d(x, s) : nb_d(x, s) - beta;",
@@ -145,14 +146,22 @@ MUTANTS = [
 ]
 
 
+# the oracle's sources; a mistake is planted in the one that holds its text
+SOURCES = ("fv_oracle.c", "lbr_steps.h")
+
+
 def _pins_fail_with(what, old, new, workdir):
     """Build the oracle with one mistake planted; True when a pin fails."""
     from oracle import build as obuild
-    src = open(os.path.join(ORACLE_DIR, "fv_oracle.c")).read()
-    assert src.count(old) == 1, "the text to mutate must occur exactly once: %r" % old
+    srcs = {name: open(os.path.join(ORACLE_DIR, name)).read() for name in SOURCES}
+    hits = [name for name in SOURCES if old in srcs[name]]
+    assert len(hits) == 1 and srcs[hits[0]].count(old) == 1, \
+        "the text to mutate must occur exactly once: %r" % old
+    srcs[hits[0]] = srcs[hits[0]].replace(old, new)
     os.makedirs(workdir)
-    with open(os.path.join(workdir, "fv_oracle.c"), "w") as f:
-        f.write(src.replace(old, new))
+    for name, text in srcs.items():
+        with open(os.path.join(workdir, name), "w") as f:
+            f.write(text)
     shutil.copy(os.path.join(ORACLE_DIR, "fv_oracle.h"), workdir)
     lib = os.path.join(workdir, "liboracle_mutant.so")
     obuild.compile_library([os.path.join(workdir, "fv_oracle.c")], lib)
