@@ -44,14 +44,16 @@ BYTES_PER_QUOTE = 58
 # sigma.  A fixed figure per quote: a faster kernel raises the fraction.
 ALG_FLOPS_PER_QUOTE = {"lbr": 370.4, "mixed": 237.4, "fp32": 85.7}
 # FP64 flops per quote the kernels execute on this workload (DADD + DMUL +
-# 2 x DFMA thread-level ncu counters), shown beside the algorithmic figure;
-# None until a capture of the current kernels (profiles/).
-EXECUTED_FLOPS_PER_QUOTE = {"lbr": None, "mixed": None, "fp32": None}
+# 2 x DFMA thread-level ncu counters on 4,194,304 quotes of the grid;
+# profiles/iv_lbr_bsm_grid_4m.md, profiles/kernels_counters_4m.md), shown
+# beside the algorithmic figure.
+EXECUTED_FLOPS_PER_QUOTE = {"lbr": 308.5, "mixed": 228.9, "fp32": 121.0}
 # DRAM bytes (read + write) per quote of the timed kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid;
-# traffic grows in proportion to the quotes, so a launch's traffic is this x n.
-# None until a capture of the current kernels.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": None, "mixed": None}
+# (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid
+# (profiles/iv_lbr_bsm_grid_4m.md); traffic grows in proportion to the quotes,
+# so a launch's traffic is this x n.
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205.817856e6 + 24.801536e6) / 4194304,
+                            "mixed": (205.779200e6 + 24.751360e6) / 4194304}
 # FP64 peaks: measured on this machine's GB300 by bench_fp64_probe.py (526 G
 # DFMA/s = 1,052 GFLOP/s; profiles/fp64_fp32_throughput_probe.md), and the
 # unit-count figure 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2070 MHz
