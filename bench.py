@@ -232,6 +232,45 @@ def time_steps(torch, fn, steps, warmup, world_size):
     return total_ms, kernel_ms
 
 
+def small_batch_latency(fv, torch, dev, reps=200):
+    """Latency of the FP64 LBR on the 4,096 Black-76 quotes of the small
+    configuration (F = 100, K = F e^k, k ~ U[-1/2, 1/2], T ~ U[0.02, 2],
+    r = 0.03, alternating flags): microseconds per call, and per replay of the
+    call captured in a CUDA graph (launch overhead out).  Inputs priced by the
+    library's own pricing kernel."""
+    w = wl.black76_quotes(4096, seed=0)
+    t = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in ("S_or_F", "K", "T", "r", "flag")}
+    sig = torch.from_numpy(w["sigma_true"]).to(dev)
+    P = fv.fv_price(fv.FV_BLACK76, t["flag"], t["S_or_F"], t["K"], t["T"], t["r"], None, sig)
+    out = torch.empty(4096, dtype=torch.float64, device=dev)
+    st = torch.empty(4096, dtype=torch.uint8, device=dev)
+    call = lambda: fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR, P, t["S_or_F"], t["K"], t["T"], t["r"],
+                                     None, t["flag"], out, st)
+
+    def per_rep_us(fn):
+        for _ in range(20):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / reps
+
+    call_us = per_rep_us(call)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=side):
+        call()
+    torch.cuda.current_stream().wait_stream(side)
+    graph_us = per_rep_us(g.replay)
+    return {"quotes": 4096, "workload": "Black-76 4,096 quotes", "call_us": call_us, "graph_us": graph_us,
+            "path": "lbr"}
+
+
 E2E_CHUNK = 1 << 20
 
 
@@ -438,6 +477,7 @@ def main():
                          "ms_per_step": tm / k,
                          "hbm_frac": BYTES_PER_QUOTE * n / (statistics.mean(km) * 1e-3) / 1e9 / hbm_peak}
         extras.setdefault("halley", {})["fallback_fraction"] = halley_fallback_fraction(fv, torch, t)
+        extras["small_batch"] = small_batch_latency(fv, torch, dev)
         # pricing and Greeks on the same grid
         sig = t["P"].new_tensor(w["sigma_true"])
         for name, fn in (("price", lambda: fv.fv_price(fv.FV_BSM, t["flag"], t["S_or_F"], t["K"],

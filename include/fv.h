@@ -39,6 +39,10 @@
  *    returns FV_ERR_CUDA.  fv_last_error() describes the last error of the
  *    calling thread.
  *  - n = 0 is valid and launches nothing.
+ *  - Every entry point opens an NVTX range named after itself for the call's
+ *    duration (visible to Nsight tools; without one attached it costs
+ *    nothing).  With the environment variable FV_LOG=1 each call prints its
+ *    name and batch size, and each error its message, to stderr.
  */
 #ifndef FV_H
 #define FV_H

@@ -3,6 +3,7 @@
 // Argument checks happen here, before any launch; the kernels live in
 // fv_kernels.cu.  Nothing here synchronises except plan creation.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <unistd.h>
 
@@ -23,11 +24,32 @@ namespace {
 
 thread_local char g_last_error[512] = "no error";
 
+// FV_LOG=1 in the environment: every entry point prints its name and batch
+// size, and every error its message, to stderr (read once per process)
+bool log_on() {
+  static const bool on = [] {
+    const char* v = getenv("FV_LOG");
+    return v != nullptr && v[0] != 0 && !(v[0] == '0' && v[1] == 0);
+  }();
+  return on;
+}
+
+// An NVTX range named after the entry point for the call's duration (seen by
+// Nsight tools; without one attached NVTX does nothing), and the FV_LOG line.
+struct Trace {
+  Trace(const char* fn, int64_t n) {
+    nvtxRangePushA(fn);
+    if (log_on()) fprintf(stderr, "fv: %s n=%lld\n", fn, (long long)n);
+  }
+  ~Trace() { nvtxRangePop(); }
+};
+
 fv_err fail(fv_err e, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
   va_end(ap);
+  if (log_on()) fprintf(stderr, "fv: error %d: %s\n", (int)e, g_last_error);
   return e;
 }
 
@@ -78,6 +100,7 @@ fv_err run_iv(const char* fn, int model, int solver, int prec, bool f32, const v
               const void* SF, const void* K, const void* T, const void* r, const void* q,
               const int8_t* flag, int64_t n, double* sigma, uint8_t* status, void* ws,
               size_t ws_bytes, bool ws_path, void* stream, const int64_t* strides = nullptr) {
+  Trace tr(fn, n);
   fv_err e = check_iv_args(fn, model, solver, P, SF, K, T, r, q, flag, n, sigma, status);
   if (e != FV_SUCCESS || n == 0) return e;
   if (strides)
@@ -355,6 +378,7 @@ fv_err fv_price(fv_model model, const int8_t* flag, const double* S_or_F, const 
                 const double* T, const double* r, const double* q, const double* sigma, int64_t n,
                 double* out_price, void* stream) {
   const char* fn = "fv_price";
+  Trace tr(fn, n);
   if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
   if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
   if (n == 0) return FV_SUCCESS;
@@ -429,6 +453,7 @@ fv_err fv_greeks(fv_model model, const int8_t* flag, const double* S_or_F, const
                  int64_t n, double* delta, double* gamma, double* vega, double* theta,
                  double* rho, void* stream) {
   const char* fn = "fv_greeks";
+  Trace tr(fn, n);
   if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
   if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
   if (n == 0) return FV_SUCCESS;
@@ -454,6 +479,7 @@ fv_err fv_iv_adjoint(fv_model model, const double* price, const double* S_or_F, 
                      int64_t n, double* gP, double* gS, double* gK, double* gT, double* gr,
                      double* gq, void* stream) {
   const char* fn = "fv_iv_adjoint";
+  Trace tr(fn, n);
   if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
   if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
   if (n == 0) return FV_SUCCESS;
@@ -480,6 +506,7 @@ fv_err fv_iv_adjoint(fv_model model, const double* price, const double* S_or_F, 
 fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta, int64_t n,
                            double* out, void* stream) {
   const char* fn = "fv_normalised_black";
+  Trace tr(fn, n);
   if (n < 0) return fail(FV_ERR_ARG, "%s: n = %lld < 0", fn, (long long)n);
   if (n == 0) return FV_SUCCESS;
   FV_REQUIRE(x, "x", fn);
@@ -494,6 +521,7 @@ fv_err fv_normalised_black(const double* x, const double* s, const int8_t* theta
 
 fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* stream) {
   const char* fn = "fv_math";
+  Trace tr(fn, n);
   if (which != FV_MATH_ERFCX && which != FV_MATH_LOG && which != FV_MATH_EXP &&
       which != FV_MATH_EXPM1 && which != FV_MATH_LOG1P && which != FV_MATH_ERFCX_SQRT2)
     return fail(FV_ERR_ARG, "%s: unknown function %d", fn, (int)which);
@@ -510,6 +538,7 @@ fv_err fv_math(fv_math_fn which, const double* z, int64_t n, double* out, void* 
 fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* chains,
                              int64_t n_chains, int autotune, void* stream, fv_chains_plan** plan) {
   const char* fn = "fv_chains_plan_create";
+  Trace tr(fn, n_chains);
   FV_REQUIRE(plan, "plan", fn);
   *plan = nullptr;
   if (!model_ok(model)) return fail(FV_ERR_ARG, "%s: unknown model %d", fn, (int)model);
@@ -659,6 +688,7 @@ fv_err fv_chains_plan_create(fv_model model, fv_solver solver, const fv_chain* c
 
 fv_err fv_implied_vol_chains(fv_chains_plan* plan, void* stream) {
   const char* fn = "fv_implied_vol_chains";
+  Trace tr(fn, plan ? plan->n_quotes : 0);
   FV_REQUIRE(plan, "plan", fn);
   if (plan->n_tiles == 0) return FV_SUCCESS;
   fv_err e = pending_error(fn);
@@ -668,6 +698,7 @@ fv_err fv_implied_vol_chains(fv_chains_plan* plan, void* stream) {
 
 fv_err fv_implied_vol_chains_direct(fv_chains_plan* plan, void* stream) {
   const char* fn = "fv_implied_vol_chains_direct";
+  Trace tr(fn, plan ? plan->n_quotes : 0);
   FV_REQUIRE(plan, "plan", fn);
   if (plan->n_tiles == 0) return FV_SUCCESS;
   fv_err e = pending_error(fn);
@@ -761,6 +792,7 @@ fv_err fv_stream_plan_destroy(fv_stream_plan* p) {
 
 fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan) {
   const char* fn = "fv_stream_plan_create";
+  Trace tr(fn, chunk_quotes);
   FV_REQUIRE(plan, "plan", fn);
   *plan = nullptr;
   if (chunk_quotes <= 0) return fail(FV_ERR_ARG, "%s: chunk_quotes must be positive", fn);
@@ -812,6 +844,7 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
                            const void* q, const int8_t* flag, int64_t n, double* out_sigma,
                            uint8_t* status, void* stream) {
   const char* fn = "fv_implied_vol_host";
+  Trace tr(fn, n);
   FV_REQUIRE(plan, "plan", fn);
   if (precision != FV_FP64 && precision != FV_MIXED && precision != FV_FP32)
     return fail(FV_ERR_ARG, "%s: unknown precision %d", fn, (int)precision);

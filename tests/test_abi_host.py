@@ -143,3 +143,24 @@ def test_autotune_cache_round_trip(tmp_path):
             fv.fv_autotune_cache_put(path, bad, 256, 2, 1, 1.0)
     with pytest.raises(fv.FvError):
         fv.fv_autotune_cache_put(path, "k", 0, 2, 1, 1.0)
+
+
+def test_fv_log_reports_calls_and_errors():
+    # FV_LOG=1: the entry point's name and batch size, and the argument error,
+    # on stderr (argument errors precede any CUDA call, so no GPU is needed)
+    import subprocess
+    import sys
+    code = ("import ctypes; from paper_2604_27210_gb300 import build; "
+            "lib = ctypes.CDLL(build.build()); p = ctypes.c_void_p(0x1000); "
+            "rc = lib.fv_implied_vol(0, 0, p, None, p, p, p, None, p, ctypes.c_int64(4), p, p, None); "
+            "print(rc)")
+    env = dict(os.environ, FV_LOG="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.stdout.strip() == "-1", r.stderr
+    assert "fv: fv_implied_vol n=4" in r.stderr
+    assert "fv: error -1: fv_implied_vol: S_or_F is NULL" in r.stderr
+    env["FV_LOG"] = "0"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert "fv:" not in r.stderr
