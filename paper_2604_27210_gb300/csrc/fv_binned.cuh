@@ -29,11 +29,16 @@ constexpr int kBinKeys = 8;  // 4 regions x {small t, not}
 template <int THREADS, int Q>
 struct BinSmem {
   static constexpr int N = THREADS * Q;
-  double beta[N], x[N], bmax[N], lnb[N], T[N];
+  double beta[N], cbeta[N], x[N], bmax[N], lnb[N], T[N];
   float s32[N];
   unsigned char reg[N];
-  unsigned short perm[N];
-  int cnt[kBinKeys], off[kBinKeys + 1];
+  union {
+    // the quotes whose reduced price is refined in double-double (their place
+    // in the tile, bit 15 set in the money), consumed before perm is written
+    unsigned short fix[N];
+    unsigned short perm[N];  // the sorted order of the solving quotes
+  };
+  int cnt[kBinKeys], off[kBinKeys + 1], nfix;
 };
 
 // One tile of up to THREADS * Q quotes (THREADS = blockDim.x).  `load(li, P, SF, K, T, r, q,
@@ -45,6 +50,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
                                                 double* sigma, uint8_t* status, int64_t out0) {
   const int tid = threadIdx.x;
   if (tid < kBinKeys) sm.cnt[tid] = 0;
+  if (tid == 0) sm.nfix = 0;
   __syncthreads();
   unsigned char key[Q];
   unsigned short rank[Q];
@@ -61,7 +67,10 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
       if (nq.status == Q_OK && nq.solve) {
         const Reduced<double> q64 = reduced64(nq);
         sm.beta[li] = q64.beta;
+        sm.cbeta[li] = q64.c_beta;
         sm.x[li] = q64.x;
+        if (needs_refine(nq))
+          sm.fix[atomicAdd(&sm.nfix, 1)] = (unsigned short)(li | (nq.iota > 0.0 ? 0x8000 : 0));
         sm.bmax[li] = q64.bmax;
         sm.lnb[li] = q64.ln_beta;
         sm.T[li] = T;
@@ -86,6 +95,17 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     }
   }
   __syncthreads();
+  // the tile's ill-conditioned quotes, every thread of the block taking one:
+  // their reduced price and its distance to the bound in double-double (the
+  // sort key above came from the FP64 values, which seed the guess only)
+  for (int j = tid; j < sm.nfix; j += THREADS) {
+    const int li = sm.fix[j] & 0x7fff;
+    double P, SF, K, T, r, q;
+    int flag;
+    load(li, P, SF, K, T, r, q, flag);
+    refine_reduced(model, P, SF, K, T, r, q, flag, (sm.fix[j] & 0x8000) != 0, sm.beta[li],
+                   sm.cbeta[li]);
+  }
   if (tid == 0) {
     int acc = 0;
     for (int k = 0; k < kBinKeys; k++) {
@@ -106,7 +126,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     q.beta = sm.beta[li];
     q.x = sm.x[li];
     q.bmax = sm.bmax[li];
-    q.c_beta = q.bmax - q.beta;
+    q.c_beta = sm.cbeta[li];
     q.ln_beta = sm.lnb[li];
     q.inv_ln_beta = 0.0;
     q.ln_c_beta = 0.0;

@@ -20,13 +20,14 @@ namespace fvk {
 namespace {
 
 // at most 64 registers a thread (1024 / THREADS blocks of THREADS threads on
-// an SM's 65,536), and tiles of at most 1,024 quotes (48 KB of static shared
-// memory)
+// an SM's 65,536); the tile's binning storage (up to ~56 KB for 1,024-quote
+// tiles) is dynamic shared memory, opted in per variant
 template <int THREADS, int Q>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_chains(int model, const ChainDesc* __restrict__ chains, const Tile* __restrict__ tiles,
              int64_t n_tiles, unsigned long long* counter) {
-  __shared__ BinSmem<THREADS, Q> sm;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BinSmem<THREADS, Q>& sm = *reinterpret_cast<BinSmem<THREADS, Q>*>(smem_raw);
   __shared__ unsigned long long s_tile;
   for (;;) {
     __syncthreads();  // the previous tile's readers of s_tile are done
@@ -60,20 +61,37 @@ using ChainsKernel = void (*)(int, const ChainDesc*, const Tile*, int64_t, unsig
 struct Variant {
   int block, qpt;
   ChainsKernel fn;
+  int smem;  // dynamic shared memory of a block
 };
 
+#define FV_CHAINS_VARIANT(B, Q) {B, Q, k_chains<B, Q>, (int)sizeof(BinSmem<B, Q>)}
 const Variant kVariants[] = {
-    {64, 1, k_chains<64, 1>},   {64, 2, k_chains<64, 2>},   {64, 4, k_chains<64, 4>},
-    {128, 1, k_chains<128, 1>}, {128, 2, k_chains<128, 2>}, {128, 4, k_chains<128, 4>},
-    {256, 1, k_chains<256, 1>}, {256, 2, k_chains<256, 2>}, {256, 4, k_chains<256, 4>},
-    {512, 1, k_chains<512, 1>}, {512, 2, k_chains<512, 2>},
+    FV_CHAINS_VARIANT(64, 1),  FV_CHAINS_VARIANT(64, 2),  FV_CHAINS_VARIANT(64, 4),
+    FV_CHAINS_VARIANT(128, 1), FV_CHAINS_VARIANT(128, 2), FV_CHAINS_VARIANT(128, 4),
+    FV_CHAINS_VARIANT(256, 1), FV_CHAINS_VARIANT(256, 2), FV_CHAINS_VARIANT(256, 4),
+    FV_CHAINS_VARIANT(512, 1), FV_CHAINS_VARIANT(512, 2),
 };
+#undef FV_CHAINS_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 const Variant* find(int block, int qpt) {
   for (const Variant& v : kVariants)
     if (v.block == block && v.qpt == qpt) return &v;
   return nullptr;
+}
+
+// allow the variant's dynamic shared memory on the current device (once per
+// device and variant; a host call, not a stream operation)
+cudaError_t opt_in(const Variant* v) {
+  static bool done[64][kNumVariants] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int k = (int)(v - kVariants);
+  if (dev >= 0 && dev < 64 && done[dev][k]) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v->smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev][k] = true;
+  return e;
 }
 
 }  // namespace
@@ -88,8 +106,9 @@ void chains_variant(int k, int* block, int* qpt) {
 int chains_max_blocks_per_sm(int block, int qpt) {
   const Variant* v = find(block, qpt);
   int b = 0;
-  if (v == nullptr ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v->fn, block, 0) != cudaSuccess || b <= 0) {
+  if (v == nullptr || opt_in(v) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v->fn, block, v->smem) != cudaSuccess ||
+      b <= 0) {
     cudaGetLastError();
     b = 1;
   }
@@ -101,9 +120,11 @@ cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles,
                           cudaStream_t st) {
   const Variant* v = find(block, qpt);
   if (v == nullptr || grid <= 0) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  cudaError_t e = opt_in(v);
   if (e != cudaSuccess) return e;
-  v->fn<<<grid, block, 0, st>>>(model, chains, tiles, n_tiles, counter);
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  v->fn<<<grid, block, v->smem, st>>>(model, chains, tiles, n_tiles, counter);
   return cudaGetLastError();
 }
 

@@ -392,6 +392,7 @@ struct Norm {
   double beta_otm;  // beta - iota for in-the-money quotes, else beta
   double x_otm;     // -|x|
   double bmax;      // e^{x_otm/2}: upper bound of the reduced call
+  double c_beta;    // bmax - beta_otm (the reduced price's distance to its bound)
   double ln_beta;   // ln beta when beta < 1e-280 (else 0: take log(beta_otm))
 };
 
@@ -456,6 +457,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   o.solve = false;
   o.x = o.beta = o.iota = o.beta_otm = o.x_otm = o.ln_beta = 0.0;
   o.bmax = 1.0;
+  o.c_beta = 1.0;
   if (!bits_finite(P) || !inputs_valid(model, SF, K, T, r, q, flag)) return o;
   const double qq = model == M_BSM ? q : 0.0;
   const double x = model_x(model, SF, K, T, r, qq);
@@ -499,8 +501,133 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   o.beta_otm = beta_otm;
   o.x_otm = -fabs(x);
   o.bmax = bmax;
+  o.c_beta = __dsub_rn(bmax, beta_otm);
   o.solve = beta_otm > __dmul_rn(iota, kEpsS);
   return o;
+}
+
+// ---------------------------------------------------------------------------
+// Double-double refinement of the reduced price of ill-conditioned quotes
+//
+// The inputs are FP64 numbers and the implied volatility is the exact root
+// for them, but beta, the intrinsic value iota and the bound b_max above each
+// carry a few ulp.  In the money beta_otm = beta - iota cancels, and near the
+// upper bound b_max - beta_otm does: sigma moves by ~eps beta/beta_otm (or
+// eps b_max/(b_max - beta_otm)) times the quote's own sensitivity, far beyond
+// 1e-12 for deep quotes whose normalised vega still exceeds 1e-8.  Both are
+// differences of undiscounted prices divided by sqrt(F K):
+//   beta_otm sqrt(F K)          = p - theta (F - K)    (in the money),
+//   (b_max - beta_otm) sqrt(F K) = bound - p,  bound = F (call) or K (put),
+// with p = P e^{rT} and F = S e^{(r-q)T} (Black-76: F given).  Those two
+// products are taken in double-double (head + tail), the differences formed
+// exactly, and only the final division by sqrt(F K) rounds.
+// ---------------------------------------------------------------------------
+struct dd {
+  double hi, lo;
+};
+// a + b = s + e exactly (Knuth)
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  return {s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+// a * b = p + e exactly (one FMA)
+__device__ __forceinline__ dd two_prod(double a, double b) {
+  const double p = __dmul_rn(a, b);
+  return {p, fma(a, b, -p)};
+}
+__device__ __forceinline__ dd dd_norm(double hi, double lo) {
+  const double s = __dadd_rn(hi, lo);
+  return {s, __dsub_rn(lo, __dsub_rn(s, hi))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const dd s = two_sum(a.hi, b.hi);
+  const dd t = two_sum(a.lo, b.lo);
+  dd u = dd_norm(s.hi, __dadd_rn(s.lo, t.hi));
+  return dd_norm(u.hi, __dadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const dd p = two_prod(a.hi, b.hi);
+  return dd_norm(p.hi, fma(a.hi, b.lo, fma(a.lo, b.hi, p.lo)));
+}
+
+// e^a for a double-double a (|a| < 700): the table reduction of exp64,
+// a = k ln2/128 + r with |r| <= ln2/256 (k ln2_hi exact, a_hi - k ln2_hi
+// exact), expm1(r) = r + r^2/2 in double-double plus the rest of its Taylor
+// series (below 3.3e-9 of the result) in FP64, then 2^m (T_hi + T_lo)(1 +
+// expm1(r)): relative error ~1e-25, limited by ln2/128's two-part constant.
+__device__ __forceinline__ dd exp_dd(dd a) {
+  const double t = fma(a.hi, FV_EXP_INV_LN2_N, 6755399441055744.0);
+  const int k = __double2loint(t);
+  const double kd = t - 6755399441055744.0;
+  const double r0 = fma(kd, -FV_EXP_LN2_N_HI, a.hi);
+  const dd r = two_sum(r0, fma(kd, -FV_EXP_LN2_N_LO, a.lo));
+  const dd r2 = dd_mul(r, r);
+  const double rh = r.hi;
+  double tail = fma(rh, 1.0 / 40320.0, 1.0 / 5040.0);
+  tail = fma(tail, rh, 1.0 / 720.0);
+  tail = fma(tail, rh, 1.0 / 120.0);
+  tail = fma(tail, rh, 1.0 / 24.0);
+  tail = fma(tail, rh, 1.0 / 6.0);
+  tail = tail * rh * r2.hi;  // r^3/6 + r^4/24 + ... + r^10/10!
+  const dd em1 = dd_add(r, dd_add({0.5 * r2.hi, 0.5 * r2.lo}, {tail, 0.0}));
+  const double2 tj = __ldg(reinterpret_cast<const double2*>(kExpTable) + (k & (FV_EXP_N - 1)));
+  const dd T = {tj.x, tj.y};
+  const dd e = dd_add(T, dd_mul(T, em1));
+  const double sc = __hiloint2double(((k >> 7) + 1023) << 20, 0);  // 2^m, exact scaling
+  return {e.hi * sc, e.lo * sc};
+}
+
+// The reduced quote needs the refinement where the cancellation costs more
+// than a factor 64: in the money with beta_otm < beta / 64, or any quote with
+// b_max - beta_otm < b_max / 64.
+__device__ __forceinline__ bool needs_refine(const Norm& n) {
+  return n.solve && ((n.iota > 0.0 && n.beta_otm < 0.015625 * n.beta) ||
+                     n.c_beta < 0.015625 * n.bmax);
+}
+
+// beta_otm (in the money) and c_beta of a quote that needs_refine, from its
+// inputs (model, flag as in decide)
+static __device__ __noinline__ void refine_reduced(int model, double P, double SF, double K, double T,
+                                            double r, double q, int flag, bool itm,
+                                            double& beta_otm, double& c_beta) {
+  // p = P e^{rT}; F and 1/sqrt(F K)
+  const dd p = dd_mul(exp_dd(two_prod(r, T)), {P, 0.0});
+  dd F = {SF, 0.0};
+  double inv_sqrt_fk;
+  if (model == M_BLACK76) {
+    inv_sqrt_fk = rsqrt(__dmul_rn(SF, K));
+  } else {
+    const double qq = model == M_BSM ? q : 0.0;
+    const dd rq = two_sum(r, -qq);                       // r - q exactly
+    const dd g = dd_add(two_prod(rq.hi, T), two_prod(rq.lo, T));  // (r - q) T
+    F = dd_mul(exp_dd(g), {SF, 0.0});
+    inv_sqrt_fk = __dmul_rn(rsqrt(__dmul_rn(SF, K)), exp64(-half64(g.hi)));
+  }
+  // A refined value replaces the FP64 one only where it is positive: a quote
+  // the FP64 status rule keeps (within a few ulp of a threshold) may be
+  // exactly at its bound or at its intrinsic value, and then keeps the FP64
+  // values it was decided with.
+  const dd mK = {-K, 0.0};
+  if (itm) {
+    // p - theta (F - K)
+    const dd fk = dd_add(F, mK);
+    const dd num = dd_add(p, flag > 0 ? dd{-fk.hi, -fk.lo} : fk);
+    const double b = __dmul_rn(num.hi + num.lo, inv_sqrt_fk);
+    if (b > 0.0) beta_otm = b;
+  }
+  // bound - p
+  const dd bound = flag > 0 ? F : dd{K, 0.0};
+  const dd cnum = dd_add(bound, dd{-p.hi, -p.lo});
+  const double c = __dmul_rn(cnum.hi + cnum.lo, inv_sqrt_fk);
+  if (c > 0.0) c_beta = c;
+}
+
+// decide, then the refinement where the quote needs it
+__device__ __forceinline__ void refine_if_needed(int model, double P, double SF, double K,
+                                                 double T, double r, double q, int flag, Norm& n) {
+  if (needs_refine(n))
+    refine_reduced(model, P, SF, K, T, r, q, flag, n.iota > 0.0, n.beta_otm, n.c_beta);
 }
 
 // ---------------------------------------------------------------------------
@@ -943,7 +1070,7 @@ __device__ __forceinline__ Reduced<double> reduced64(const Norm& n) {
   q.beta = n.beta_otm;
   // out of the money, beta_otm = beta and the logarithm of P applies
   q.ln_beta = (n.ln_beta != 0.0 && n.beta_otm == n.beta) ? n.ln_beta : 0.0;
-  q.c_beta = n.bmax - n.beta_otm;
+  q.c_beta = n.c_beta;
   q.x = n.x_otm;
   q.bmax = n.bmax;
   q.inv_ln_beta = 0.0;
@@ -1005,9 +1132,9 @@ struct HalleyOut {
 // beta > b_max/2: b_max - b then comes from the cancellation-free complement,
 // so g carries an error relative to b_max - b instead of to b_max (the same
 // function, with the same Halley step).
-__device__ __forceinline__ HalleyOut halley_solve(double beta, double x, double bmax) {
+__device__ __forceinline__ HalleyOut halley_solve(double beta, double c_beta, double x,
+                                                 double bmax) {
   const bool upper = beta > 0.5 * bmax;
-  const double c_beta = bmax - beta;
   double s = kSqrt2Pi * beta;  // Brenner-Subrahmanyam: b ~ s/sqrt(2 pi) at the money
   double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
   for (int k = 0; k < kHalleySteps; k++) {

@@ -168,7 +168,10 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
     double P, SF, K, T, r, q;
     int flag;
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
-    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    // FP64 and mixed: the ill-conditioned quotes' reduced price in
+    // double-double (the FP32 path's 1e-5 does not need it)
+    if (PREC != P_FP32) refine_if_needed(a.model, P, SF, K, T, r, q, flag, nq);
     double sigma = qnan();
     if (nq.status == Q_OK) {
       if (!nq.solve) {
@@ -280,13 +283,13 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
 //    kernel appends the failures to a compacted list in a device workspace
 //    and a second kernel runs the fallback over the whole list.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ Reduced<double> reduced_of(double beta, double x, double bmax,
-                                                      double ln_beta) {
+__device__ __forceinline__ Reduced<double> reduced_of(double beta, double c_beta, double x,
+                                                      double bmax, double ln_beta) {
   Reduced<double> q;
   q.beta = beta;
   q.x = x;
   q.bmax = bmax;
-  q.c_beta = bmax - beta;
+  q.c_beta = c_beta;
   q.ln_beta = ln_beta;
   q.inv_ln_beta = 0.0;
   q.ln_c_beta = 0.0;
@@ -297,8 +300,8 @@ template <int THREADS, int Q>
 struct HalleySmem {
   // the tile's quotes that failed the convergence test: reduced quote,
   // maturity, the sweeps' bracket and the quote's place in the tile
-  double beta[THREADS * Q], x[THREADS * Q], bmax[THREADS * Q], lnb[THREADS * Q], T[THREADS * Q],
-      lo[THREADS * Q], hi[THREADS * Q];
+  double beta[THREADS * Q], cbeta[THREADS * Q], x[THREADS * Q], bmax[THREADS * Q],
+      lnb[THREADS * Q], T[THREADS * Q], lo[THREADS * Q], hi[THREADS * Q];
   unsigned short li[THREADS * Q];
   int n;
 };
@@ -317,20 +320,22 @@ __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled
       double P, SF, K, T, r, q;
       int flag;
       load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
-      const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+      Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+      refine_if_needed(a.model, P, SF, K, T, r, q, flag, nq);
       a.status[i] = (uint8_t)nq.status;
       double sigma = qnan();
       if (nq.status == Q_OK) {
         if (!nq.solve) {
           sigma = 0.0;
         } else {
-          const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax);
+          const HalleyOut h = halley_solve(nq.beta_otm, nq.c_beta, nq.x_otm, nq.bmax);
           if (h.converged) {
             sigma = h.s * rsqrt(T);
           } else {
             const Reduced<double> q64 = reduced64(nq);
             const int j = atomicAdd(&sm.n, 1);
             sm.beta[j] = q64.beta;
+            sm.cbeta[j] = q64.c_beta;
             sm.x[j] = q64.x;
             sm.bmax[j] = q64.bmax;
             sm.lnb[j] = q64.ln_beta;
@@ -347,8 +352,8 @@ __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled
     __syncthreads();
     const int nf = sm.n;
     for (int j = threadIdx.x; j < nf; j += THREADS) {
-      const double s = halley_fallback64(reduced_of(sm.beta[j], sm.x[j], sm.bmax[j], sm.lnb[j]),
-                                         sm.lo[j], sm.hi[j]);
+      const double s = halley_fallback64(
+          reduced_of(sm.beta[j], sm.cbeta[j], sm.x[j], sm.bmax[j], sm.lnb[j]), sm.lo[j], sm.hi[j]);
       a.sigma[base + sm.li[j]] = s * rsqrt(sm.T[j]);
     }
     __syncthreads();
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(THREADS) k_iv_halley32_tiled(IvArgs a, TileSch
         if (!nq.solve) {
           sigma = 0.0;
         } else {
-          const float b32 = (float)nq.beta_otm, c32 = (float)(nq.bmax - nq.beta_otm),
+          const float b32 = (float)nq.beta_otm, c32 = (float)nq.c_beta,
                       x32 = (float)nq.x_otm;
           const Halley32Out h = halley32_solve(b32, c32, x32);
           if (h.converged) {
@@ -506,7 +511,8 @@ __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
     double P, SF, K, T, r, q;
     int flag;
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
-    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    refine_if_needed(a.model, P, SF, K, T, r, q, flag, nq);
     double sigma = qnan();
     bool fallback = false;
     double lo = 0.0, hi = 0.0;
@@ -514,7 +520,7 @@ __global__ void __launch_bounds__(256) k_iv_halley(IvArgs a, HalleyWs w) {
       if (!nq.solve) {
         sigma = 0.0;
       } else {
-        const HalleyOut h = halley_solve(nq.beta_otm, nq.x_otm, nq.bmax);
+        const HalleyOut h = halley_solve(nq.beta_otm, nq.c_beta, nq.x_otm, nq.bmax);
         if (h.converged) {
           sigma = h.s * rsqrt(T);
         } else {
@@ -539,7 +545,8 @@ __global__ void __launch_bounds__(256) k_halley_fallback(IvArgs a, HalleyWs w) {
     double P, SF, K, T, r, q;
     int flag;
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
-    const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+    refine_if_needed(a.model, P, SF, K, T, r, q, flag, nq);
     const double s = halley_fallback64(reduced64(nq), w.lo[k], w.hi[k]);
     a.sigma[i] = s * rsqrt(T);
   }
@@ -560,7 +567,7 @@ __global__ void __launch_bounds__(256) k_iv_halley32(IvArgs a, HalleyWs w) {
       if (!nq.solve) {
         sigma = 0.0;
       } else {
-        const Halley32Out h = halley32_solve((float)nq.beta_otm, (float)(nq.bmax - nq.beta_otm),
+        const Halley32Out h = halley32_solve((float)nq.beta_otm, (float)nq.c_beta,
                                              (float)nq.x_otm);
         if (h.converged) {
           sigma = (double)h.s * rsqrt(T);
@@ -587,7 +594,7 @@ __global__ void __launch_bounds__(256) k_halley32_fallback(IvArgs a, HalleyWs w)
     int flag;
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     const Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
-    const float s = bisect32_fallback((float)nq.beta_otm, (float)(nq.bmax - nq.beta_otm),
+    const float s = bisect32_fallback((float)nq.beta_otm, (float)nq.c_beta,
                                       (float)nq.x_otm, (float)w.lo[k], (float)w.hi[k]);
     a.sigma[i] = (double)s * rsqrt(T);
   }

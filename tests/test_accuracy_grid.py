@@ -57,7 +57,9 @@ def test_accuracy_grid_all_paths():
     amb = orc.status(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])[3] <= 16.0
     assert amb.mean() <= 1e-3
     solved = (st == orc.OK) & (ref > 0) & ~amb
-    gate = solved & (v > 1e-8) & (kap <= 1e3)
+    # FP64 paths: every quote with b' > 1e-8; FP32 paths: kappa <= 1e3 too
+    gate64 = solved & (v > 1e-8)
+    gate32 = gate64 & (kap <= 1e3)
     otm = solved & (w["flag"] * X <= 0)
     rows, bars = [], []
     for name, fn in paths.items():
@@ -67,13 +69,13 @@ def test_accuracy_grid_all_paths():
         assert np.all(np.isfinite(s_gpu[(st == orc.OK) & amb]) & (s_gpu[(st == orc.OK) & amb] >= 0))
         rel = np.where(solved, np.abs(s_gpu - ref) / np.where(solved, ref, 1.0), 0.0)
         ulp = rel / (EPS * (1.0 + np.nan_to_num(kap, nan=0.0)))
-        rows.append((name, rel[gate].max(), np.median(rel[gate]), rel[otm & (v > 1e-8)].max(),
-                     rel[solved].max(), np.max(ulp[solved])))
-        bar = 1e-12
+        bar, gate = 1e-12, gate64
         if "FP32" in name and "mixed" not in name:
             # the plain-Phi residual cancels in FP32 where s is small: the
             # paper's throughput path carries a looser bound than LBR FP32
-            bar = 1e-3 if "plain" in name else 1e-5
+            bar, gate = (1e-3 if "plain" in name else 1e-5), gate32
+        rows.append((name, rel[gate].max(), np.median(rel[gate]), rel[otm & (v > 1e-8)].max(),
+                     rel[solved].max(), np.max(ulp[solved])))
         bars.append((name, rel[gate].max(), bar))
     path = os.environ.get("FV_ACCURACY_REPORT")
     if path:
@@ -82,8 +84,9 @@ def test_accuracy_grid_all_paths():
                     "max rel, all solved | max rel / (eps (1+kappa)) |\n|---|---:|---:|---:|---:|---:|\n")
             for r in rows:
                 f.write("| %s | %.2e | %.2e | %.2e | %.2e | %.3g |\n" % r)
-            f.write("\n%d quotes (%d x-values x %d s-values x call/put), %d solved, %d in the gate "
-                    "(b' > 1e-8, kappa <= 1e3)\n" % (X.size, 121, 120, solved.sum(), gate.sum()))
+            f.write("\n%d quotes (%d x-values x %d s-values x call/put), %d solved; gated: %d with "
+                    "b' > 1e-8 (FP64 paths), %d of them with kappa <= 1e3 (FP32 paths)\n"
+                    % (X.size, 121, 120, solved.sum(), gate64.sum(), gate32.sum()))
     for name, got, bar in bars:
         assert got <= bar, (name, got, bar)
 
@@ -134,7 +137,9 @@ def test_extreme_grid_all_paths():
         assert np.all(s_gpu[(st == orc.OK) & (ref == 0) & ~amb] == 0), name
         chk = solved & normal & np.isfinite(ref)
         rel = np.abs(s_gpu[chk] - ref[chk]) / ref[chk]
-        gate = (v[chk] > 1e-8) & (kap[chk] <= 1e3)
+        gate = v[chk] > 1e-8
+        if tol_gate > 1e-12:
+            gate &= kap[chk] <= 1e3
         assert rel[gate].max() <= tol_gate, (name, rel[gate].max())
         if tol_rest is not None:
             bound = tol_rest + 16 * EPS * (1 + np.nan_to_num(kap[chk], nan=np.inf))

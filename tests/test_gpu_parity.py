@@ -2,11 +2,12 @@
 
 Floating-point tolerances (the target accuracy, read with the conditioning
 of each quote):
-  - sigma, FP64 paths: relative error <= 1e-12 where the normalised vega
-    b' > 1e-8 and kappa = beta / (s b') <= 1e3; elsewhere (solved quotes) the
-    error is bounded by 1e-12 + 16 eps (1 + kappa), the rounding of the FP64
-    inputs amplified by the conditioning.
-  - sigma, pure FP32 path: relative error <= 1e-5 on the same gate.
+  - sigma, FP64 paths (LBR, Halley, mixed): relative error <= 1e-12 wherever
+    the normalised vega b' > 1e-8; elsewhere (solved quotes) the error is
+    bounded by 1e-12 + 16 eps (1 + kappa), kappa = beta / (s b').
+  - sigma, pure FP32 paths: relative error <= 1e-5 (FP32 LBR) or 1e-4 (the
+    plain-Phi FP32 Halley) where b' > 1e-8 and kappa <= 1e3 (their FP32 solve
+    keeps the FP64 reduced price's rounding, amplified by kappa).
   - price round trip: relative <= 1e-13 where b' > 1e-8.
   - status: bit-identical for every quote.
 """
@@ -78,7 +79,11 @@ def _check_sigma(got, ref, st, v, kap, tol_gate=1e-12, tol_rest=None, name=""):
     assert np.all(np.isnan(got[(st != orc.OK) & (st != 255)])), name
     assert np.all(np.isfinite(got[solved]) & (got[solved] > 0)), name
     rel = np.abs(got[solved] - ref[solved]) / ref[solved]
-    gate = (v[solved] > 1e-8) & (kap[solved] <= 1e3)
+    # FP64 paths: every quote with b' > 1e-8 (their ill-conditioned quotes'
+    # reduced price is refined in double-double); FP32 paths: kappa <= 1e3 too
+    gate = v[solved] > 1e-8
+    if tol_gate > 1e-12:
+        gate &= kap[solved] <= 1e3
     if gate.any():
         assert rel[gate].max() <= tol_gate, "%s: gated max rel %.3g" % (name, rel[gate].max())
     if tol_rest is not None:
