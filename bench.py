@@ -43,17 +43,20 @@ BYTES_PER_QUOTE = 58
 # Householder(3) correction and sigma; the FP32 path's the status rule and
 # sigma.  A fixed figure per quote: a faster kernel raises the fraction.
 ALG_FLOPS_PER_QUOTE = {"lbr": 370.4, "mixed": 237.4, "fp32": 85.7}
-# FP64 flops per quote the kernels execute on this workload (DADD + DMUL +
-# 2 x DFMA thread-level ncu counters on 4,194,304 quotes of the grid;
-# profiles/iv_lbr_bsm_grid_4m.md, profiles/kernels_counters_4m.md), shown
-# beside the algorithmic figure.
-EXECUTED_FLOPS_PER_QUOTE = {"lbr": 308.5, "mixed": 228.9, "fp32": 121.0}
-# DRAM bytes (read + write) per quote of the timed kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304 quotes of the grid
-# (profiles/iv_lbr_bsm_grid_4m.md); traffic grows in proportion to the quotes,
-# so a launch's traffic is this x n.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205.817856e6 + 24.801536e6) / 4194304,
-                            "mixed": (205.779200e6 + 24.751360e6) / 4194304}
+# FP64 flops per quote the step's kernels execute on this workload (DADD +
+# DMUL + 2 x DFMA thread-level ncu counters on 4,194,304 quotes of the grid:
+# the solver, plus 4.2 per quote in the refinement pass over the quotes it
+# marked; profiles/iv_lbr_bsm_grid_4m.md, profiles/kernels_counters_4m.md),
+# shown beside the algorithmic figure.
+EXECUTED_FLOPS_PER_QUOTE = {"lbr": 307.2 + 4.2, "mixed": 228.2 + 4.2, "fp32": 121.0}
+# DRAM bytes (read + write) per quote of the step's kernels from one ncu
+# capture each (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304
+# quotes of the grid (profiles/iv_lbr_bsm_grid_4m.md): the solver, then the
+# refinement pass (13.70 MB: the status bytes and the marked quotes' inputs;
+# the same scan and the same marked quotes in both precisions).  Traffic grows
+# in proportion to the quotes, so a step's traffic is this x n.
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205.79e6 + 24.73e6 + 13.70e6) / 4194304,
+                            "mixed": (206.29e6 + 24.51e6 + 13.70e6) / 4194304}
 # FP64 peaks: measured on this machine's GB300 by bench_fp64_probe.py (526 G
 # DFMA/s = 1,052 GFLOP/s; profiles/fp64_fp32_throughput_probe.md), and the
 # unit-count figure 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2070 MHz
@@ -189,7 +192,10 @@ def run_path(fv, t, path, out, st):
         raise ValueError(path)
 
 
-LAUNCHES_PER_STEP = {"lbr": 1, "mixed": 1, "fp32": 1, "halley": 1}
+# kernels per step on the grid: the LBR solver, then the refinement kernel
+# over the ill-conditioned quotes it marked (the FP32 path has none; Halley
+# refines inside its one kernel)
+LAUNCHES_PER_STEP = {"lbr": 2, "mixed": 2, "fp32": 1, "halley": 1}
 
 
 def halley_fallback_fraction(fv, torch, t):
@@ -443,7 +449,8 @@ def main():
     clocks = clk.summary()
     ms_step, value = aggregate(n, total_ms / args.steps, ws)
 
-    # kernel-level roofline of the dominant (only) kernel of the step
+    # roofline of the step's kernels: the solver (97 % of the step's device
+    # time on the grid) and its refinement pass
     k_ms = statistics.mean(kernel_ms)
     hbm_peak, hbm_kind = peaks()
     gbs = BYTES_PER_QUOTE * n / (k_ms * 1e-3) / 1e9

@@ -29,28 +29,24 @@ constexpr int kBinKeys = 8;  // 4 regions x {small t, not}
 template <int THREADS, int Q>
 struct BinSmem {
   static constexpr int N = THREADS * Q;
-  double beta[N], cbeta[N], x[N], bmax[N], lnb[N], T[N];
+  double beta[N], x[N], bmax[N], lnb[N], T[N];
   float s32[N];
   unsigned char reg[N];
-  union {
-    // the quotes whose reduced price is refined in double-double (their place
-    // in the tile, bit 15 set in the money), consumed before perm is written
-    unsigned short fix[N];
-    unsigned short perm[N];  // the sorted order of the solving quotes
-  };
-  int cnt[kBinKeys], off[kBinKeys + 1], nfix;
+  unsigned short perm[N];  // the sorted order of the solving quotes
+  int cnt[kBinKeys], off[kBinKeys + 1];
 };
 
 // One tile of up to THREADS * Q quotes (THREADS = blockDim.x).  `load(li, P, SF, K, T, r, q,
 // flag)` returns false past the tile's end; `out(li)` gives the index of the
 // quote's sigma / status.  LATE32: the mixed path's FP32 iterations run in
 // phase 2 (phase 1 only evaluates the FP32 guess that gives the sort key).
+// An ill-conditioned quote (needs_refine) is not solved here: its status is
+// written with kRefineMark and the refinement kernel solves it.
 template <int PREC, int THREADS, int Q, bool LATE32, typename Load>
 __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int model, const Load& load,
                                                 double* sigma, uint8_t* status, int64_t out0) {
   const int tid = threadIdx.x;
   if (tid < kBinKeys) sm.cnt[tid] = 0;
-  if (tid == 0) sm.nfix = 0;
   __syncthreads();
   unsigned char key[Q];
   unsigned short rank[Q];
@@ -63,14 +59,12 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     int flag;
     if (load(li, P, SF, K, T, r, q, flag)) {
       const Norm nq = decide(model, P, SF, K, T, r, q, flag);
-      status[out0 + li] = (uint8_t)nq.status;
-      if (nq.status == Q_OK && nq.solve) {
+      const bool refine = needs_refine(nq);
+      status[out0 + li] = (uint8_t)nq.status | (refine ? kRefineMark : 0);
+      if (nq.status == Q_OK && nq.solve && !refine) {
         const Reduced<double> q64 = reduced64(nq);
         sm.beta[li] = q64.beta;
-        sm.cbeta[li] = q64.c_beta;
         sm.x[li] = q64.x;
-        if (needs_refine(nq))
-          sm.fix[atomicAdd(&sm.nfix, 1)] = (unsigned short)(li | (nq.iota > 0.0 ? 0x8000 : 0));
         sm.bmax[li] = q64.bmax;
         sm.lnb[li] = q64.ln_beta;
         sm.T[li] = T;
@@ -89,23 +83,12 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
                             (reg != 0 || series_in_log_space<float>(q32.x, sg));
         key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
         rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
-      } else {
+      } else if (!refine) {
         sigma[out0 + li] = nq.status == Q_OK ? 0.0 : qnan();
       }
     }
   }
   __syncthreads();
-  // the tile's ill-conditioned quotes, every thread of the block taking one:
-  // their reduced price and its distance to the bound in double-double (the
-  // sort key above came from the FP64 values, which seed the guess only)
-  for (int j = tid; j < sm.nfix; j += THREADS) {
-    const int li = sm.fix[j] & 0x7fff;
-    double P, SF, K, T, r, q;
-    int flag;
-    load(li, P, SF, K, T, r, q, flag);
-    refine_reduced(model, P, SF, K, T, r, q, flag, (sm.fix[j] & 0x8000) != 0, sm.beta[li],
-                   sm.cbeta[li]);
-  }
   if (tid == 0) {
     int acc = 0;
     for (int k = 0; k < kBinKeys; k++) {
@@ -126,7 +109,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     q.beta = sm.beta[li];
     q.x = sm.x[li];
     q.bmax = sm.bmax[li];
-    q.c_beta = sm.cbeta[li];
+    q.c_beta = q.bmax - q.beta;
     q.ln_beta = sm.lnb[li];
     q.inv_ln_beta = 0.0;
     q.ln_c_beta = 0.0;
@@ -148,6 +131,24 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     sigma[out0 + li] = s * rsqrt(sm.T[li]);
   }
   __syncthreads();
+}
+
+// The FP64 LBR or mixed solve of one quote from its (refined) reduced
+// values, the arithmetic phase 1 and phase 2 above apply to a tile's quote.
+template <int PREC>
+__device__ __forceinline__ double lbr_solve_quote(const Reduced<double>& q64) {
+  Reduced<float> q32 = reduced32(q64);
+  int reg = 1;
+  if (PREC == P_FP64) {
+    const float g = lbr_guess<float>(q32, reg);
+    return lbr_solve64(q64, g, reg);
+  }
+  const float g = lbr_guess<float>(q32, reg);
+  Reduced<float> f = reduced32(q64);
+  wing_logs<float>(f, reg);
+  float s32 = g;
+  for (int it = 0; it < 2; it++) s32 = guarded<float>(s32, hh3_step<float>(objective<float>(f, s32, reg)));
+  return hh3_correction(q64, f64_of(s32), reg);
 }
 
 }  // namespace fvk

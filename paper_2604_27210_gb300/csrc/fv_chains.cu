@@ -12,6 +12,8 @@
 // the variants below and keeps the fastest.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fv_binned.cuh"
 #include "fv_internal.h"
 
@@ -53,6 +55,58 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     // sigma / status of the chain, indexed from the tile's offset
     lbr_binned_tile<P_FP64, THREADS, Q, false>(sm, model, load, c.sigma + tl.offset,
                                                c.status + tl.offset, 0);
+  }
+}
+
+// The chains' ill-conditioned quotes, which the kernel above marked
+// (status | kRefineMark): the blocks scan the tiles (tile t to block t mod
+// grid), append the marked quotes to a shared-memory list, and solve the list
+// with every thread of the block from the quotes' double-double refined
+// reduced price when it could not take another tile, and at the end.
+constexpr int kRefThreads = 256, kRefList = 2048;
+
+__device__ __forceinline__ void chains_refine_solve(int model, const ChainDesc& c, int64_t k) {
+  const double P = c.P[k], K = c.K[k];
+  const int flag = c.flag[k];
+  Norm nq = decide(model, P, c.SF, K, c.T, c.r, c.q, flag);
+  refine_reduced(model, P, c.SF, K, c.T, c.r, c.q, flag, positive64(nq.iota), nq.beta_otm, nq.c_beta);
+  const double s = lbr_solve_quote<P_FP64>(reduced64(nq));
+  c.sigma[k] = s * rsqrt(c.T);
+  c.status[k] = (uint8_t)nq.status;
+}
+
+__global__ void __launch_bounds__(kRefThreads, 4)
+    k_chains_refine(int model, const ChainDesc* __restrict__ chains, const Tile* __restrict__ tiles,
+                    int64_t n_tiles, int tile_quotes) {
+  // a marked quote: its tile (bits 10..63) and its place in the tile (< 1,024)
+  __shared__ uint64_t list[kRefList];
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int64_t t = blockIdx.x;; t += gridDim.x) {
+    const bool more = t < n_tiles;
+    if (more) {
+      const Tile tl = tiles[t];
+      const ChainDesc& c = chains[tl.chain];
+      const int count = (int)min((int64_t)tile_quotes, c.n - tl.offset);
+      for (int li = threadIdx.x; li < count; li += kRefThreads)
+        if (c.status[tl.offset + li] & kRefineMark)
+          list[atomicAdd(&cnt, 1)] = ((uint64_t)t << 10) | (uint64_t)li;
+    }
+    __syncthreads();
+    const int m = cnt;
+    __syncthreads();  // every thread has read m: the decision below is the block's
+    if (m > kRefList - tile_quotes || (!more && m > 0)) {
+      for (int j = threadIdx.x; j < m; j += kRefThreads) {
+        const uint64_t e = list[j];
+        const Tile tl = tiles[e >> 10];
+        chains_refine_solve(model, chains[tl.chain], tl.offset + (int64_t)(e & 1023));
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) cnt = 0;
+      __syncthreads();
+    }
+    if (!more) break;
   }
 }
 
@@ -125,6 +179,9 @@ cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles,
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   v->fn<<<grid, block, v->smem, st>>>(model, chains, tiles, n_tiles, counter);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int rgrid = (int)std::min<int64_t>((int64_t)sm_count() * 4, n_tiles);
+  k_chains_refine<<<rgrid, kRefThreads, 0, st>>>(model, chains, tiles, n_tiles, block * qpt);
   return cudaGetLastError();
 }
 

@@ -580,11 +580,17 @@ __device__ __forceinline__ dd exp_dd(dd a) {
 
 // The reduced quote needs the refinement where the cancellation costs more
 // than a factor 64: in the money with beta_otm < beta / 64, or any quote with
-// b_max - beta_otm < b_max / 64.
+// b_max - beta_otm < b_max / 64.  The test takes FP32 views (integer unit,
+// FP32 compares): the factor is a threshold, not a result.
 __device__ __forceinline__ bool needs_refine(const Norm& n) {
-  return n.solve && ((n.iota > 0.0 && n.beta_otm < 0.015625 * n.beta) ||
-                     n.c_beta < 0.015625 * n.bmax);
+  if (!n.solve) return false;
+  const bool itm = positive64(n.iota);
+  return (itm && f32_trunc(n.beta_otm) < 0.015625f * f32_trunc(n.beta)) ||
+         f32_trunc(n.c_beta) < 0.015625f * f32_trunc(n.bmax);
 }
+// Status bit of a quote the large-batch LBR kernels (flat and chains) leave
+// to their refinement kernel (set between the two launches only).
+constexpr uint8_t kRefineMark = 0x80;
 
 // beta_otm (in the money) and c_beta of a quote that needs_refine, from its
 // inputs (model, flag as in decide)

@@ -29,11 +29,13 @@ int grid_for(int64_t n, int block, int per_sm);
 
 // LBR: batches of kSmallBatch quotes or more run the region-binned kernel with
 // dynamic tiles, whose counters are the first two sigma outputs (zeroed on
-// `st` before the launch)
+// `st` before the launch), then the refinement kernel over the quotes it
+// marked; smaller ones one unbinned kernel
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
 
-// Halley x8 with the fallback inside the same kernel (tile-local compaction
-// in shared memory): no workspace.  Large batches zero the first two sigma
+// Halley x8 with the fallback and the double-double refinement of
+// ill-conditioned quotes inside the same kernel (tile-local compaction in
+// shared memory): no workspace.  Large batches zero the first two sigma
 // outputs on `st` before the launch (the dynamic tile counters).
 cudaError_t launch_iv_halley(const IvArgs& a, cudaStream_t st);
 // Halley x8 in FP32 on the plain-Phi residual, the same arrangement
@@ -85,7 +87,8 @@ int chains_variant_count();
 void chains_variant(int k, int* block, int* quotes_per_thread);
 // resident blocks of a variant on one SM (1 if the variant does not exist)
 int chains_max_blocks_per_sm(int block, int quotes_per_thread);
-// zero `counter` on `st`, then launch the variant over the tile table
+// zero `counter` on `st`, launch the variant over the tile table, then the
+// refinement kernel over the quotes it marked
 cudaError_t launch_chains(int model, const ChainDesc* chains, const Tile* tiles, int64_t n_tiles,
                           unsigned long long* counter, int block, int qpt, int grid,
                           cudaStream_t st);

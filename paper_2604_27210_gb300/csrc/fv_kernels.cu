@@ -202,6 +202,66 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
 
 constexpr int kBinThreads = 256;
 
+// ---------------------------------------------------------------------------
+// The refinement kernel: the ill-conditioned quotes a large-batch LBR kernel
+// marked (status | kRefineMark) are solved here from their double-double
+// refined reduced price.  The blocks scan the status bytes in 256-quote
+// chunks (chunk c to block c mod grid), append the marked quotes to a
+// shared-memory list, and solve the list with every thread of the block when
+// it could not take another chunk, and at the end: so a block solves up to
+// 1,024 quotes at once however sparse they are (about 1 % of the benchmark
+// grid's quotes, 8 % where half the quotes are in the money).  It runs on the
+// same stream right after the kernel that marked them, in that kernel's
+// precision PREC (FP64 or mixed).
+// ---------------------------------------------------------------------------
+constexpr int kRefThreads = 256, kRefList = 1024;
+
+template <typename InT, int PREC>
+__device__ __forceinline__ void refine_solve(const IvArgs& a, int64_t i) {
+  double P, SF, K, T, r, q;
+  int flag;
+  load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
+  Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
+  refine_reduced(a.model, P, SF, K, T, r, q, flag, positive64(nq.iota), nq.beta_otm, nq.c_beta);
+  const double s = lbr_solve_quote<PREC>(reduced64(nq));
+  a.sigma[i] = s * rsqrt(T);
+  a.status[i] = (uint8_t)nq.status;
+}
+
+template <typename InT, int PREC>
+__global__ void __launch_bounds__(kRefThreads, 4) k_refine(IvArgs a) {
+  __shared__ int64_t list[kRefList];
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const int64_t chunks = (a.n + kRefThreads - 1) / kRefThreads;
+  for (int64_t c = blockIdx.x;; c += gridDim.x) {
+    const bool more = c < chunks;
+    if (more) {
+      const int64_t i = c * kRefThreads + threadIdx.x;
+      if (i < a.n && (a.status[i] & kRefineMark)) list[atomicAdd(&cnt, 1)] = i;
+    }
+    __syncthreads();
+    const int m = cnt;
+    __syncthreads();  // every thread has read m: the decision below is the block's
+    // solve when the list could not take another chunk, and at the end
+    if (m > kRefList - kRefThreads || (!more && m > 0)) {
+      for (int j = threadIdx.x; j < m; j += kRefThreads) refine_solve<InT, PREC>(a, list[j]);
+      __syncthreads();
+      if (threadIdx.x == 0) cnt = 0;
+      __syncthreads();
+    }
+    if (!more) break;
+  }
+}
+
+template <typename InT, int PREC>
+static cudaError_t launch_refine(const IvArgs& a, cudaStream_t st) {
+  constexpr auto kernel = k_refine<InT, PREC>;
+  kernel<<<persistent_grid<kernel>(a.n, kRefThreads, kRefThreads), kRefThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename InT, int PREC, int Q, int MINB, bool LATE32>
 __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, TileSched ts) {
   __shared__ BinSmem<kBinThreads, Q> sm;
@@ -226,7 +286,9 @@ static cudaError_t launch_binned(const IvArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int grid = persistent_grid<kernel>(a.n, kBinThreads * Q, kBinThreads);
   kernel<<<grid, kBinThreads, 0, st>>>(a, ts);
-  return cudaGetLastError();
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return le;
+  return launch_refine<InT, PREC>(a, st);
 }
 
 // Tile shapes measured on GB300 (16.8 M quotes of the BSM grid, one resident
