@@ -317,6 +317,68 @@ def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
     return ms, h2d, d2h
 
 
+def other_configs(fv, torch, dev, steps=3):
+    """The remaining workloads of the benchmark set, timed beside the headline
+    (N = 1 only; inputs priced by the library's own pricing kernel):
+      - 67,108,864 Black-76 quotes with FP32 inputs (F, K, T, r, price): the
+        mixed, FP64 and FP32 paths on the FP32 arrays, and the FP64 path on the
+        same quotes widened to FP64;
+      - 10,000 option chains (74.0 M quotes, lengths log-uniform in 8..65,536):
+        the tuned persistent kernel replayed from its CUDA graph, one flat
+        launch over the concatenated quotes, and one launch per chain;
+      - 8,388,608 BSM quotes: the FP64 LBR, the IV adjoint and the Greeks.
+    Each figure: quotes / mean CUDA-event time per step after one warm-up."""
+    import bench_kernels as bk
+    res = {}
+
+    def timed(fn, n, k=steps):
+        tm, _ = time_steps(torch, fn, k, 1, 1)
+        return {"value": n / (tm / k * 1e-3), "unit": "quotes/s", "ms_per_step": tm / k}
+
+    # FP32 inputs: the price of the FP32 values widened to FP64, rounded to FP32
+    w = wl.black76_fp32(1 << 26, seed=2)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    t = {k: T(w[k]) for k in ("S_or_F", "K", "T", "r", "flag")}
+    P = fv.fv_price(w["model"], t["flag"], t["S_or_F"].double(), t["K"].double(),
+                    t["T"].double(), t["r"].double(), None, T(w["sigma_true"]))
+    t["P"], t["q"] = P.float(), None
+    n = t["P"].numel()
+    cfg = {"quotes": n}
+    for name, kern in (("mixed", "mixed"), ("fp64", "lbr"), ("fp32", "fp32")):
+        cfg[name] = timed(bk.runner(fv, torch, kern, w, t), n)
+    t64 = {k: (v.double() if v is not None and v.dtype == torch.float32 else v) for k, v in t.items()}
+    del t, P
+    cfg["fp64_fp64_inputs"] = timed(bk.runner(fv, torch, "lbr", w, t64), n)
+    res["black76_fp32_inputs_67m"] = cfg
+    del t64, w
+    torch.cuda.empty_cache()
+
+    w, t = bk.make(fv, torch, dev, "chains", 10000, 3)
+    n = t["P"].numel()
+    cfg = {"chains": 10000, "quotes": n}
+    fn, plan, _ = bk.chains_runner(fv, torch, w, t, "graph")
+    cfg["persistent_graph"] = timed(fn, n)
+    cfg["persistent_graph"]["plan"] = plan.info()
+    del fn, plan
+    cfg["flat_launch"] = timed(bk.runner(fv, torch, "lbr", w, t), n)
+    fn, _, _ = bk.chains_runner(fv, torch, w, t, "separate")
+    cfg["launch_per_chain"] = timed(fn, n, 2)
+    del fn
+    res["chains_10k"] = cfg
+    del t, w
+    torch.cuda.empty_cache()
+
+    w, t = bk.make(fv, torch, dev, "bsm", 1 << 23, 4)
+    n = t["P"].numel()
+    res["bsm_8m"] = {"quotes": n,
+                     "iv_fp64": timed(bk.runner(fv, torch, "lbr", w, t), n),
+                     "adjoint": timed(bk.runner(fv, torch, "adjoint", w, t), n),
+                     "greeks": timed(bk.runner(fv, torch, "greeks", w, t), n)}
+    del t, w
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(w_host, P_host, n_sample, seed=123):
     """The oracle's FP64 LBR (its own FP64 normalised Black, as it stands) on
     the workload (all of it, or a seeded sample of n_sample quotes), all host
@@ -423,6 +485,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 30, help="quotes of the CPU baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the selected path (for profiler runs)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (FP32 inputs, chains, BSM adjoint)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -512,6 +576,12 @@ def main():
         torch.cuda.synchronize()
         errors = error_stats(w, P_host, idx, out.cpu().numpy(), st.cpu().numpy(), sig_cpu, st_cpu)
 
+    configs = None
+    if ws == 1 and not args.no_extras and not args.no_configs:
+        del t, out, st
+        torch.cuda.empty_cache()
+        configs = other_configs(fv, torch, dev)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -531,7 +601,7 @@ def main():
                 "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP[args.path] * args.steps,
                 "e2e": {"value": ws * n / (e2e_ms * 1e-3), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "cpu_baseline": cpu, "errors": errors, "paths": extras}
+                "cpu_baseline": cpu, "errors": errors, "paths": extras, "configs": configs}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
     Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     // FP64 and mixed: the ill-conditioned quotes' reduced price in
     // double-double (the FP32 path's 1e-5 does not need it)
-    if (PREC != P_FP32) refine_if_needed(a.model, P, SF, K, T, r, q, flag, nq);
+    if (PREC != P_FP32) refine_if_needed<true>(a.model, P, SF, K, T, r, q, flag, nq);
     double sigma = qnan();
     if (nq.status == Q_OK) {
       if (!nq.solve) {
@@ -390,7 +390,10 @@ __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled
         if (!nq.solve) {
           sigma = 0.0;
         } else {
-          const HalleyOut h = halley_solve(nq.beta_otm, nq.c_beta, nq.x_otm, nq.bmax);
+          // the handoff test from the first sweep on (large batches) or the
+          // second (the 64-thread small-batch tiles)
+          const HalleyOut h =
+              halley_solve(nq.beta_otm, nq.c_beta, nq.x_otm, nq.bmax, THREADS == 64 ? 1 : 0);
           if (h.converged) {
             sigma = h.s * rsqrt(T);
           } else {
