@@ -913,7 +913,7 @@ def test_full_size_fp32_inputs_mixed(fv, torch_dev):
 
 
 def test_full_size_chains(fv, torch_dev):
-    # 10,000 chains (74.0 M quotes), the plan tuned on them (every shape timed)
+    # 10,000 chains (72.8 M quotes), the plan tuned on them (every shape timed)
     c = wl.fill_prices(wl.chains(10000, seed=3), orc.price)
     chains = _chain_tensors(torch_dev, c)
     plan = fv.fv_chains_plan_create(fv.FV_BLACK76, chains, autotune=True)
