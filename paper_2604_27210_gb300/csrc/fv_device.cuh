@@ -1151,51 +1151,85 @@ struct HalleyOut {
   bool converged;
 };
 
-// The residual g = b - beta is evaluated as (b_max - beta) - (b_max - b) when
+// One quote's sweeps so far: the iterate, the bracket [lo, hi], the last
+// Newton distance relative to s, and whether the sweeps have ended (the root,
+// the handoff test, or the last sweep).
+struct HalleyState {
+  double s, lo, hi, nerr;
+  bool done;
+};
+
+__device__ __forceinline__ HalleyState halley_start(double beta) {
+  HalleyState h;
+  h.s = kSqrt2Pi * beta;  // Brenner-Subrahmanyam: b ~ s/sqrt(2 pi) at the money
+  h.lo = 0.0;
+  h.hi = __longlong_as_double(0x7ff0000000000000LL);
+  h.nerr = h.hi;
+  h.done = false;
+  return h;
+}
+
+// Sweeps k0 .. k1 - 1 of the eight, from the state h.  The residual
+// g = b - beta is evaluated as (b_max - beta) - (b_max - b) when
 // beta > b_max/2: b_max - b then comes from the cancellation-free complement,
 // so g carries an error relative to b_max - b instead of to b_max (the same
-// function, with the same Halley step).
-__device__ __forceinline__ HalleyOut halley_solve(double beta, double c_beta, double x,
-                                                 double bmax, int first_check = 0) {
+// function, with the same Halley step).  Running 0..8 at once or in pieces
+// gives the same result bit for bit.
+__device__ __forceinline__ void halley_sweeps(double beta, double c_beta, double x, double bmax,
+                                              HalleyState& h, int k0, int k1, int first_check) {
   const bool upper = beta > 0.5 * bmax;
-  double s = kSqrt2Pi * beta;  // Brenner-Subrahmanyam: b ~ s/sqrt(2 pi) at the money
-  double lo = 0.0, hi = __longlong_as_double(0x7ff0000000000000LL), nerr = hi;
-  for (int k = 0; k < kHalleySteps; k++) {
+  for (int k = k0; k < k1; k++) {
     NB<double> v;
-    nb_eval<double, false>(x, s, upper, v, true, bmax);
+    nb_eval<double, false>(x, h.s, upper, v, true, bmax);
     const double g = upper ? c_beta - v.e * v.B : v.b - beta;
     if (g < 0.0) {
-      lo = s;
+      h.lo = h.s;
     } else if (g > 0.0) {
-      hi = s;
+      h.hi = h.s;
     } else {
       // g == 0 is the root; a NaN residual leaves the quote unconverged
-      nerr = (g == 0.0) ? 0.0 : hi;
-      break;
+      h.nerr = (g == 0.0) ? 0.0 : h.hi;
+      h.done = true;
+      return;
     }
     // Newton step nu = g/b' = g sqrt(2 pi)/e (e^-1 as in the Householder step)
     // and its distance to the root relative to s (the convergence test)
     const double nu = g * (kSqrt2Pi * inv_e(v.e));
-    nerr = fabs(nu) * v.inv_s;
-    if (k >= first_check && k < kHalleySteps - 1 && !(nerr <= kHalleyReach[k])) break;
+    h.nerr = fabs(nu) * v.inv_s;
+    if (k >= first_check && k < kHalleySteps - 1 && !(h.nerr <= kHalleyReach[k])) {
+      h.done = true;
+      return;
+    }
     // Halley: ds = -2 g g' / (2 g'^2 - g g'') = -nu / (1 - nu u / 2), u = b''/b';
     // the factor 1 / (1 - nu u / 2) only shapes the step (its rounding enters at
     // order nu^2), so it is formed in FP32
-    const float hf = f32_trunc(v.h), sf = f32_trunc(s);
+    const float hf = f32_trunc(v.h), sf = f32_trunc(h.s);
     const float u = hf * hf * __frcp_rn(sf) - 0.25f * sf;
     const double step = -nu * f64_of(1.0f / (1.0f - 0.5f * f32_trunc(nu) * u));
-    double sn = s + step;
+    double sn = h.s + step;
     // lo <= sn <= hi, sn finite: lo, hi >= 0, so on the signed patterns
     const long long bn = __double_as_longlong(sn);
-    if (!(bn >= __double_as_longlong(lo) && bn <= __double_as_longlong(hi) && bits_finite(sn)))
-      sn = bits_finite(hi) ? 0.5 * (lo + hi) : 2.0 * s;
-    s = sn;
+    if (!(bn >= __double_as_longlong(h.lo) && bn <= __double_as_longlong(h.hi) && bits_finite(sn)))
+      sn = bits_finite(h.hi) ? 0.5 * (h.lo + h.hi) : 2.0 * h.s;
+    h.s = sn;
   }
+  if (k1 >= kHalleySteps) h.done = true;
+}
+
+__device__ __forceinline__ bool halley_converged(const HalleyState& h) {
+  return isfinite(h.s) && h.s > 0.0 && h.nerr <= kHalleyConvTol;
+}
+
+// All eight sweeps at once
+__device__ __forceinline__ HalleyOut halley_solve(double beta, double c_beta, double x,
+                                                 double bmax, int first_check = 0) {
+  HalleyState h = halley_start(beta);
+  halley_sweeps(beta, c_beta, x, bmax, h, 0, kHalleySteps, first_check);
   HalleyOut o;
-  o.s = s;
-  o.lo = lo;
-  o.hi = hi;
-  o.converged = isfinite(s) && s > 0.0 && nerr <= kHalleyConvTol;
+  o.s = h.s;
+  o.lo = h.lo;
+  o.hi = h.hi;
+  o.converged = halley_converged(h);
   return o;
 }
 
@@ -1266,22 +1300,23 @@ __device__ __forceinline__ double bisect_fallback(double ln_beta, double beta, d
 // remaining error is far below an ulp) or when the bracket has shrunk to a
 // few ulp: two or three evaluations from the guess, against ~50 halvings of
 // a plain bisection.
-__device__ __forceinline__ double halley_fallback64(Reduced<double> q, double lo, double hi) {
-  int reg = 1;
-  double s;
-  {
-    // region and guess as the FP64 LBR solver takes them: FP32 where FP32
-    // holds the quote's scales, FP64 otherwise
-    Reduced<float> q32 = reduced32(q);
-    int reg32 = 1;
-    const float g32 = lbr_guess<float>(q32, reg32);
-    if (q.bmax > 1e-20 && g32 > 1e-30f && g32 < 1e30f) {
-      s = f64_of(g32);
-      reg = reg32;
-    } else {
-      s = lbr_guess<double>(q, reg);
-    }
+// The fallback's start: region and guess as the FP64 LBR solver takes them,
+// FP32 where FP32 holds the quote's scales, FP64 otherwise
+__device__ __forceinline__ double halley_fallback_guess(Reduced<double> q, int& reg) {
+  reg = 1;
+  Reduced<float> q32 = reduced32(q);
+  int reg32 = 1;
+  const float g32 = lbr_guess<float>(q32, reg32);
+  if (q.bmax > 1e-20 && g32 > 1e-30f && g32 < 1e30f) {
+    reg = reg32;
+    return f64_of(g32);
   }
+  return lbr_guess<double>(q, reg);
+}
+
+// The fallback's bracketed Householder(3) steps from the guess s of region reg
+__device__ __forceinline__ double halley_fallback_steps(Reduced<double> q, double s, int reg,
+                                                        double lo, double hi) {
   const bool has_hi = bits_finite(hi);
   if (!(s > lo && s < hi)) s = has_hi ? 0.5 * (lo + hi) : 2.0 * fmax(lo, 0.5 * s);
   wing_logs<double>(q, reg);
@@ -1305,6 +1340,12 @@ __device__ __forceinline__ double halley_fallback64(Reduced<double> q, double lo
     if (done) break;
   }
   return s;
+}
+
+__device__ __forceinline__ double halley_fallback64(const Reduced<double>& q, double lo, double hi) {
+  int reg;
+  const double s = halley_fallback_guess(q, reg);
+  return halley_fallback_steps(q, s, reg, lo, hi);
 }
 
 // ---------------------------------------------------------------------------

@@ -360,19 +360,40 @@ __device__ __forceinline__ Reduced<double> reduced_of(double beta, double c_beta
 
 template <int THREADS, int Q>
 struct HalleySmem {
-  // the tile's quotes that failed the convergence test: reduced quote,
-  // maturity, the sweeps' bracket and the quote's place in the tile
-  double beta[THREADS * Q], cbeta[THREADS * Q], x[THREADS * Q], bmax[THREADS * Q],
-      lnb[THREADS * Q], T[THREADS * Q], lo[THREADS * Q], hi[THREADS * Q];
-  unsigned short li[THREADS * Q];
-  int n;
+  // per quote of the tile, at its place li: the reduced quote, the maturity
+  // and the sweeps' state (iterate and bracket); then the two compacted lists
+  // of places: the quotes still sweeping after their first sweep, and the
+  // quotes for the fallback
+  static constexpr int N = THREADS * Q;
+  double beta[N], cbeta[N], x[N], bmax[N], lnb[N], T[N], s[N], lo[N], hi[N];
+  unsigned short sweep[N], fall[N];
+  unsigned char reg[N];  // the fallback's start region
+  int n_sweep, n_fall;
+  int cnt[kBinKeys], off[kBinKeys + 1];  // the fallback's counting sort
 };
 
+// A block solves a tile in three phases, each over packed lanes:
+//   1. every quote: status, refinement where needed, the first sweep;
+//   2. the quotes the first sweep left sweeping, compacted: the other seven;
+//   3. the quotes that did not converge, compacted and sorted by the region
+//      and small-t class of their start (the key of the binned LBR tile):
+//      the fallback.
+// On the benchmark grid 80 % of the quotes leave after the first sweep and
+// about 10 % sweep on, so phase 2 keeps the long sweeps of the few converging
+// quotes from holding warps whose other lanes are done.  The arithmetic of
+// every quote is that of halley_solve and halley_fallback64.
 template <typename InT, int THREADS, int Q>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled(IvArgs a, TileSched ts) {
   __shared__ HalleySmem<THREADS, Q> sm;
+  // the handoff test from the first sweep on (large batches) or the second
+  // (the 64-thread small-batch tiles)
+  constexpr int kFirstCheck = THREADS == 64 ? 1 : 0;
   for_each_tile(ts, THREADS * Q, a.n, [&](int64_t base, int count) {
-    if (threadIdx.x == 0) sm.n = 0;
+    if (threadIdx.x == 0) {
+      sm.n_sweep = 0;
+      sm.n_fall = 0;
+    }
+    if (threadIdx.x < kBinKeys) sm.cnt[threadIdx.x] = 0;
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < Q; k++) {
@@ -390,36 +411,95 @@ __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled
         if (!nq.solve) {
           sigma = 0.0;
         } else {
-          // the handoff test from the first sweep on (large batches) or the
-          // second (the 64-thread small-batch tiles)
-          const HalleyOut h =
-              halley_solve(nq.beta_otm, nq.c_beta, nq.x_otm, nq.bmax, THREADS == 64 ? 1 : 0);
-          if (h.converged) {
+          const Reduced<double> q64 = reduced64(nq);
+          HalleyState h = halley_start(q64.beta);
+          halley_sweeps(q64.beta, q64.c_beta, q64.x, q64.bmax, h, 0, 1, kFirstCheck);
+          if (h.done && halley_converged(h)) {
             sigma = h.s * rsqrt(T);
           } else {
-            const Reduced<double> q64 = reduced64(nq);
-            const int j = atomicAdd(&sm.n, 1);
-            sm.beta[j] = q64.beta;
-            sm.cbeta[j] = q64.c_beta;
-            sm.x[j] = q64.x;
-            sm.bmax[j] = q64.bmax;
-            sm.lnb[j] = q64.ln_beta;
-            sm.T[j] = T;
-            sm.lo[j] = h.lo;
-            sm.hi[j] = h.hi;
-            sm.li[j] = (unsigned short)li;
-            continue;  // sigma comes from the fallback
+            sm.beta[li] = q64.beta;
+            sm.cbeta[li] = q64.c_beta;
+            sm.x[li] = q64.x;
+            sm.bmax[li] = q64.bmax;
+            sm.lnb[li] = q64.ln_beta;
+            sm.T[li] = T;
+            sm.s[li] = h.s;
+            sm.lo[li] = h.lo;
+            sm.hi[li] = h.hi;
+            if (h.done)
+              sm.fall[atomicAdd(&sm.n_fall, 1)] = (unsigned short)li;
+            else
+              sm.sweep[atomicAdd(&sm.n_sweep, 1)] = (unsigned short)li;
+            continue;  // sigma comes from phase 2 or 3
           }
         }
       }
       a.sigma[i] = sigma;
     }
     __syncthreads();
-    const int nf = sm.n;
+    const int nsw = sm.n_sweep;
+    for (int j = threadIdx.x; j < nsw; j += THREADS) {
+      const int li = sm.sweep[j];
+      HalleyState h;
+      h.s = sm.s[li];
+      h.lo = sm.lo[li];
+      h.hi = sm.hi[li];
+      h.nerr = __longlong_as_double(0x7ff0000000000000LL);
+      h.done = false;
+      halley_sweeps(sm.beta[li], sm.cbeta[li], sm.x[li], sm.bmax[li], h, 1, kHalleySteps,
+                    kFirstCheck);
+      if (halley_converged(h)) {
+        a.sigma[base + li] = h.s * rsqrt(sm.T[li]);
+      } else {
+        sm.lo[li] = h.lo;
+        sm.hi[li] = h.hi;
+        sm.fall[atomicAdd(&sm.n_fall, 1)] = (unsigned short)li;
+      }
+    }
+    __syncthreads();
+    const int nf = sm.n_fall;
+    unsigned char key[Q];
+    unsigned short rank[Q];
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+      const int j = k * THREADS + threadIdx.x;
+      key[k] = 0xff;
+      rank[k] = 0;
+      if (j < nf) {
+        const int li = sm.fall[j];
+        int reg;
+        const double g = halley_fallback_guess(
+            reduced_of(sm.beta[li], sm.cbeta[li], sm.x[li], sm.bmax[li], sm.lnb[li]), reg);
+        sm.s[li] = g;
+        sm.reg[li] = (unsigned char)reg;
+        const float gf = f32_trunc(g);
+        const bool series = 0.5f * gf < (float)fvd::Prec<double>::t_small &&
+                            (reg != 0 || series_in_log_space<float>(f32_trunc(sm.x[li]), gf));
+        key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
+        rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int k = 0; k < kBinKeys; k++) {
+        sm.off[k] = acc;
+        acc += sm.cnt[k];
+      }
+      sm.off[kBinKeys] = acc;
+    }
+    __syncthreads();
+    // the sorted order of the fallback's quotes, in place of the sweep list
+#pragma unroll
+    for (int k = 0; k < Q; k++)
+      if (key[k] != 0xff) sm.sweep[sm.off[key[k]] + rank[k]] = sm.fall[k * THREADS + threadIdx.x];
+    __syncthreads();
     for (int j = threadIdx.x; j < nf; j += THREADS) {
-      const double s = halley_fallback64(
-          reduced_of(sm.beta[j], sm.cbeta[j], sm.x[j], sm.bmax[j], sm.lnb[j]), sm.lo[j], sm.hi[j]);
-      a.sigma[base + sm.li[j]] = s * rsqrt(sm.T[j]);
+      const int li = sm.sweep[j];
+      const double s = halley_fallback_steps(
+          reduced_of(sm.beta[li], sm.cbeta[li], sm.x[li], sm.bmax[li], sm.lnb[li]), sm.s[li],
+          sm.reg[li], sm.lo[li], sm.hi[li]);
+      a.sigma[base + li] = s * rsqrt(sm.T[li]);
     }
     __syncthreads();
   });
