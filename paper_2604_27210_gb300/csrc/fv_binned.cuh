@@ -113,9 +113,8 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     q.ln_beta = sm.lnb[li];
     q.inv_ln_beta = 0.0;
     q.ln_c_beta = 0.0;
-    double s;
     if (PREC == P_FP64) {
-      s = lbr_solve64(q, sm.s32[li], sm.reg[li]);
+      sigma[out0 + li] = lbr_solve64(q, sm.s32[li], sm.reg[li]) * rsqrt(sm.T[li]);
     } else {
       int reg = sm.reg[li];
       float s32 = sm.s32[li];
@@ -126,9 +125,8 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
         for (int it = 0; it < 2; it++)
           s32 = guarded<float>(s32, hh3_step<float>(objective<float>(q32, s32, reg)));
       }
-      s = hh3_correction(q, f64_of(s32), reg);
+      sigma[out0 + li] = mixed_sigma(q, s32, reg, sm.T[li]);
     }
-    sigma[out0 + li] = s * rsqrt(sm.T[li]);
   }
   __syncthreads();
 }

@@ -34,6 +34,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "fv_df32.cuh"
 #include "fv_fp64_tables.h"
 
 namespace fvd {
@@ -971,6 +972,21 @@ __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double 
 __device__ __forceinline__ double hh3_correction(Reduced<double> q, double s, int reg) {
   wing_logs<double>(q, reg);
   return guarded<double>(s, hh3_ds_mixed(q, s, reg));
+}
+
+// The mixed solver's correction of its FP32 iterate s32 and sigma = s/sqrt(T):
+// the Householder(3) step with the residual in double-float
+// (fvdf::hh3_correction_df) where the quote's scales fit FP32's exponent
+// range, else the FP64 step above.
+// The FP64 step is out of line: it is rare here, and its code would otherwise
+// sit in the hot loop's instruction stream.
+static __device__ __noinline__ double mixed_sigma_fp64(Reduced<double> q, float s32, int reg, double T) {
+  return hh3_correction(q, f64_of(s32), reg) * rsqrt(T);
+}
+__device__ __forceinline__ double mixed_sigma(const Reduced<double>& q, float s32, int reg, double T) {
+  double sigma;
+  if (fvdf::hh3_correction_df(q.beta, q.c_beta, q.x, q.ln_beta, T, s32, reg, sigma)) return sigma;
+  return mixed_sigma_fp64(q, s32, reg, T);
 }
 
 // Boundaries (six normalised-Black values: b and b' at s_l, s_c, s_h, of which

@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
     load_quote<InT>(a, i, P, SF, K, T, r, q, flag);
     Norm nq = decide(a.model, P, SF, K, T, r, q, flag);
     // FP64 and mixed: the ill-conditioned quotes' reduced price in
-    // double-double (the FP32 path's 1e-5 does not need it)
+    // double-double (the FP32 path's 1e-5 does not need it); the mixed path
+    // takes their correction in FP64
+    const bool ill = PREC == P_MIXED && needs_refine(nq);
     if (PREC != P_FP32) refine_if_needed<true>(a.model, P, SF, K, T, r, q, flag, nq);
     double sigma = qnan();
     if (nq.status == Q_OK) {
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
         const Reduced<double> q64 = reduced64(nq);
         int reg = 1;
         double s;
+        float s32 = 0.0f;
         if (PREC == P_FP64) {
           // two Householder(3) steps, a third where the second still moved s
           // by more than 2^-17 (quartic convergence: a smaller second step
@@ -188,11 +191,13 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
           const float g = lbr_guess<float>(q32, reg);
           s = lbr_solve64(q64, g, reg);
         } else {
-          const float s32 = lbr_solve<float>(reduced32(q64), 2, 2, 0.0f, reg);
+          s32 = lbr_solve<float>(reduced32(q64), 2, 2, 0.0f, reg);
           s = (double)s32;
-          if (PREC == P_MIXED) s = hh3_correction(q64, s, reg);
+          if (PREC == P_MIXED && ill) s = hh3_correction(q64, s, reg);
         }
-        sigma = s * rsqrt(T);  // sigma = s / sqrt(T) within 1.5 ulp, one FP64 step fewer
+        // sigma = s / sqrt(T) within 1.5 ulp, one FP64 step fewer; the mixed
+        // path's well-conditioned quotes take the double-float correction
+        sigma = (PREC == P_MIXED && !ill) ? mixed_sigma(q64, s32, reg, T) : s * rsqrt(T);
       }
     }
     a.sigma[i] = sigma;
