@@ -131,6 +131,205 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The mixed solver's tile: the status rule and reduction in double-float
+//
+// On this GPU the FP64 status rule (logarithm, exponentials, reciprocal
+// square root) takes more time than the mixed solver's FP32 iterations and
+// double-float correction together.  Pass A decides each quote with the
+// double-float rule (fvdf::decide_df), which leaves to the FP64 rule the
+// quotes it cannot decide with certainty: in the money (the intrinsic value
+// cancels), within its guard band of a threshold, BSM log-moneyness that
+// cancels, scales outside FP32's range.  Those go to a shared-memory list,
+// and pass B applies the FP64 rule to the list with every thread of the block
+// (packed lanes whatever the tile's mix).  Statuses are the FP64 rule's.
+// Pass C evaluates the FP32 guess and the sort key of every solving quote;
+// phase 2 is the binned tile's, with the reduced quote as double-float.
+// ---------------------------------------------------------------------------
+template <int THREADS, int Q>
+struct BinSmemMixed {
+  static constexpr int N = THREADS * Q;
+  fvdf::df beta[N], x[N], bmax[N], cbeta[N], lnb[N];
+  double T[N];
+  float s32[N];
+  unsigned char reg[N];
+  unsigned char state[N];  // 0: no root to solve here, 1: solve, 2: solve from ln beta
+  unsigned short perm[N], list[N];
+  int cnt[kBinKeys], off[kBinKeys + 1];
+  int nlist;
+};
+
+__device__ __forceinline__ Reduced<float> reduced32_df(const fvdf::df& beta, const fvdf::df& cbeta,
+                                                       const fvdf::df& x, const fvdf::df& bmax,
+                                                       const fvdf::df& lnb, bool tiny) {
+  Reduced<float> f;
+  f.beta = tiny ? 0.0f : beta.h;
+  f.ln_beta = tiny ? lnb.h : 0.0f;
+  f.c_beta = cbeta.h;
+  f.x = x.h;
+  f.bmax = bmax.h;
+  f.inv_ln_beta = 0.0f;
+  f.ln_c_beta = 0.0f;
+  return f;
+}
+
+// the mixed FP64 solve of one quote (the refinement pass's arithmetic), out of
+// line: only quotes whose scales leave FP32's range take it
+template <int PREC>
+__device__ __forceinline__ double lbr_solve_quote(const Reduced<double>& q64);
+static __device__ __noinline__ double mixed_solve_fp64(Reduced<double> q64, double T) {
+  return lbr_solve_quote<P_MIXED>(q64) * rsqrt(T);
+}
+
+template <int THREADS, int Q, typename Load>
+__device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& sm, int model,
+                                                      const Load& load, double* sigma,
+                                                      uint8_t* status, int64_t out0) {
+  using fvdf::df;
+  const int tid = threadIdx.x;
+  if (tid < kBinKeys) sm.cnt[tid] = 0;
+  if (tid == 0) sm.nlist = 0;
+  __syncthreads();
+  // pass A: the double-float status rule
+#pragma unroll 1
+  for (int k = 0; k < Q; k++) {
+    const int li = k * THREADS + tid;
+    sm.state[li] = 0;
+    double P, SF, K, T, r, q;
+    int flag;
+    if (!load(li, P, SF, K, T, r, q, flag)) continue;
+    const fvdf::NormDF d = fvdf::decide_df(model, P, SF, K, T, r, q, flag);
+    if (d.fp64) {
+      sm.list[atomicAdd(&sm.nlist, 1)] = (unsigned short)li;
+      continue;
+    }
+    // out of the money: ill-conditioned where b_max - beta < b_max/64
+    const bool refine = d.solve && d.c_beta.h < 0.015625f * d.bmax.h;
+    status[out0 + li] = (uint8_t)d.status | (refine ? kRefineMark : 0);
+    if (d.solve && !refine) {
+      sm.beta[li] = d.beta;
+      sm.x[li] = d.x;
+      sm.bmax[li] = d.bmax;
+      sm.cbeta[li] = d.c_beta;
+      sm.lnb[li] = d.ln_beta;
+      sm.T[li] = T;
+      sm.state[li] = d.tiny ? 2 : 1;
+    } else if (!refine) {
+      sigma[out0 + li] = d.status == Q_OK ? 0.0 : qnan();
+    }
+  }
+  __syncthreads();
+  // pass B: the FP64 rule on the list, packed
+  const int nl = sm.nlist;
+  for (int j = tid; j < nl; j += THREADS) {
+    const int li = sm.list[j];
+    double P, SF, K, T, r, q;
+    int flag;
+    load(li, P, SF, K, T, r, q, flag);
+    const Norm nq = decide(model, P, SF, K, T, r, q, flag);
+    const bool refine = needs_refine(nq);
+    status[out0 + li] = (uint8_t)nq.status | (refine ? kRefineMark : 0);
+    if (nq.status == Q_OK && nq.solve && !refine) {
+      const Reduced<double> q64 = reduced64(nq);
+      df b, x, bm, cb, T2, lb = fvdf::mk(0.0f);
+      bool tiny = false, ok = fvdf::df_of0(q64.x, x) && fvdf::df_of(q64.bmax, bm) &&
+                              fvdf::df_of(q64.c_beta, cb) && fvdf::df_of(T, T2);
+      if (ok && !fvdf::df_of(q64.beta, b)) {
+        // beta below the double-float range: carried as ln beta
+        tiny = true;
+        b = fvdf::mk(0.0f);
+        if (q64.ln_beta != 0.0) ok = fvdf::df_of(q64.ln_beta, lb);
+        else lb = fvdf::dlog_of(q64.beta);
+      }
+      if (ok) {
+        sm.beta[li] = b;
+        sm.x[li] = x;
+        sm.bmax[li] = bm;
+        sm.cbeta[li] = cb;
+        sm.lnb[li] = lb;
+        sm.T[li] = T;
+        sm.state[li] = tiny ? 2 : 1;
+      } else {
+        // scales outside FP32's range: the whole mixed solve in FP64 here
+        sigma[out0 + li] = mixed_solve_fp64(q64, T);
+      }
+    } else if (!refine) {
+      sigma[out0 + li] = nq.status == Q_OK ? 0.0 : qnan();
+    }
+  }
+  __syncthreads();
+  // pass C: the FP32 guess (the sort key) of every solving quote
+  unsigned char key[Q];
+  unsigned short rank[Q];
+#pragma unroll
+  for (int k = 0; k < Q; k++) {
+    const int li = k * THREADS + tid;
+    key[k] = 0xff;
+    rank[k] = 0;
+    const int stt = sm.state[li];
+    if (stt != 0) {
+      Reduced<float> q32 = reduced32_df(sm.beta[li], sm.cbeta[li], sm.x[li], sm.bmax[li], sm.lnb[li],
+                                        stt == 2);
+      int reg = 1;
+      const float sg = lbr_guess<float>(q32, reg);
+      sm.s32[li] = sg;
+      sm.reg[li] = (unsigned char)reg;
+      const bool series = 0.5f * sg < (float)fvd::Prec<double>::t_small &&
+                          (reg != 0 || series_in_log_space<float>(q32.x, sg));
+      key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
+      rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int k = 0; k < kBinKeys; k++) {
+      sm.off[k] = acc;
+      acc += sm.cnt[k];
+    }
+    sm.off[kBinKeys] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < Q; k++)
+    if (key[k] != 0xff) sm.perm[sm.off[key[k]] + rank[k]] = (unsigned short)(k * THREADS + tid);
+  __syncthreads();
+  // phase 2: the FP32 iterations and the double-float correction
+  const int ns = sm.off[kBinKeys];
+  for (int j = tid; j < ns; j += THREADS) {
+    const int li = sm.perm[j];
+    const bool tiny = sm.state[li] == 2;
+    const df beta = sm.beta[li], x = sm.x[li], bmax = sm.bmax[li], cbeta = sm.cbeta[li],
+             lnb = sm.lnb[li];
+    const double T = sm.T[li];
+    int reg = sm.reg[li];
+    float s32 = sm.s32[li];
+    Reduced<float> q32 = reduced32_df(beta, cbeta, x, bmax, lnb, tiny);
+    wing_logs<float>(q32, reg);
+#pragma unroll 1
+    for (int it = 0; it < 2; it++)
+      s32 = guarded<float>(s32, hh3_step<float>(objective<float>(q32, s32, reg)));
+    df Td;
+    double sig;
+    if (!(fvdf::df_of(T, Td) &&
+          fvdf::hh3_correction_dfv(beta, cbeta, x, lnb, tiny, Td, s32, reg, sig))) {
+      // the FP64 correction from the double-float values (rare)
+      const double lb = tiny ? fvdf::to_double(lnb) : 0.0;
+      Reduced<double> q64;
+      q64.beta = tiny ? exp(lb) : fvdf::to_double(beta);
+      q64.x = fvdf::to_double(x);
+      q64.bmax = fvdf::to_double(bmax);
+      q64.c_beta = fvdf::to_double(cbeta);
+      q64.ln_beta = lb;
+      q64.inv_ln_beta = 0.0;
+      q64.ln_c_beta = 0.0;
+      sig = mixed_sigma_fp64(q64, s32, reg, T);
+    }
+    sigma[out0 + li] = sig;
+  }
+  __syncthreads();
+}
+
 // The FP64 LBR or mixed solve of one quote from its (refined) reduced
 // values, the arithmetic phase 1 and phase 2 above apply to a tile's quote.
 template <int PREC>

@@ -288,19 +288,25 @@ FV_DF_FN df dexp(df a) {
 // r - r^2/2 in double-float plus r^3/3 - ... - r^6/6 in FP32 (|r| <= 2^-8:
 // absolute error below 2^-49), m ln2 from three parts (the first two
 // products exact for |m| < 2^11).
+// log1p(r) for |r| <= 2^-7: r - r^2/2 + r^3/3 in double-float, -r^4/4 + r^5/5 -
+// r^6/6 in FP32 (below 2^-30 of r: their rounding is below 2^-54 of the
+// result, which stays within 2^-47 relative for any such r)
+FV_DF_FN df log1p_small(df r) {
+  const df r2 = dsqr(r);
+  const df r3 = dmul(r2, r);
+  const float rh = r.h;
+  const float poly = fma_(fma_(rh, -1.0f / 6.0f, 0.2f), rh, -0.25f);
+  const float tail = mul(mul(r2.h, r2.h), poly);
+  const df t3 = dmul(r3, df{FV_DF_THIRD_HI, FV_DF_THIRD_LO});
+  return dadd(r, dadd_fast(dscale(neg(r2), 0.5f), dadd_fast(t3, mk(tail))));
+}
 FV_DF_FN df dlog_core(int m, float fh, float fl) {
   const float jf = sub(fma_(fh, 128.0f, 12582784.0f), 12582912.0f);  // round((f - 1) 128)
   const int j = (int)jf;
   const f4 row = ld4(kLogDf + 4 * (j - FV_DF_LOG_J0));
   const df p = two_prod(fh, row.x);
   const df r = two_sum(sub(p.h, 1.0f), fma_(fl, row.x, p.l));
-  const df r2 = dsqr(r);
-  const float rh = r.h;
-  float poly = fma_(rh, -1.0f / 6.0f, 0.2f);
-  poly = fma_(poly, rh, -0.25f);
-  poly = fma_(poly, rh, 1.0f / 3.0f);
-  const float tail = mul(mul(mul(rh, rh), rh), poly);
-  const df l1p = dadd(r, dadd_fast(dscale(neg(r2), 0.5f), mk(tail)));
+  const df l1p = log1p_small(r);
   const float mf = (float)m;
   const df mln2 = dadd(two_sum(mul(mf, FV_DF_LN2_1), mul(mf, FV_DF_LN2_2)), mk(mul(mf, FV_DF_LN2_3)));
   return dadd(dadd(mln2, df{row.y, row.z}), l1p);
@@ -344,6 +350,20 @@ FV_DF_FN df dlog_of(double d) {
   float fh, fl;
   log_arg_of(d, m, fh, fl);
   return dlog_core(m, fh, fl);
+}
+
+// log1p(u) for -1/2 <= u <= 1 (a double-float u) with the error of u's own
+// precision (~2^-47 relative): the table row j = round(128 u) gives
+// ln(1 + u) = -ln c_j + log1p(r), r = c_j (1 + u) - 1 = (c_j - 1) + c_j u with
+// c_j - 1 exact (Sterbenz) and c_j u_h a two-product, so 1 + u is never
+// rounded; j = 0 (|u| < 1/256) leaves r = u.
+FV_DF_FN df dlog1p(df u) {
+  const int j = (int)sub(fma_(u.h, 128.0f, 12582912.0f), 12582912.0f);
+  const f4 row = ld4(kLogDf + 4 * (j - FV_DF_LOG_J0));
+  const df a = two_prod(row.x, u.h);
+  const df s = two_sum(sub(row.x, 1.0f), a.h);
+  const df r = two_sum(s.h, add(add(s.l, a.l), mul(row.x, u.l)));
+  return dadd(df{row.y, row.z}, log1p_small(r));
 }
 
 // erfcx(z) = exp(z^2) erfc(z) for z >= 0.  Below 128: the piecewise Chebyshev
@@ -497,20 +517,14 @@ FV_DF_FN bool nb_df(df x, float s, int reg, NBdf& o) {
 //                 inflection point sqrt(2 pi) (C - c_beta e^E)
 //   region 0:     nu = (ln beta - ln b) ln b / ln beta * b/b',  ln b = ln B - E
 //   region 3:     nu = -(ln c_beta - ln(b_max - b)) (b_max - b)/b'
-// beta, c_beta = b_max - beta, x and T are the FP64 reduced quote (ln_beta its
-// preset logarithm or 0).  Writes sigma = (s + ds)/sqrt(T) and returns true;
-// returns false, writing nothing, where the quote's scales leave the range
-// this evaluation covers (the caller then takes the FP64 correction).
-FV_DF_FN bool hh3_correction_df(double beta, double c_beta, double x, double ln_beta, double T,
-                                float s, int reg, double& sigma) {
-  if (!(s > 1e-30f && s < 1e30f)) return false;
-  df xd, Td;
-  if (x == 0.0) {
-    xd = mk(0.0f);
-  } else if (!df_of(x, xd)) {
-    return false;
-  }
-  if (!df_of(T, Td) || !(Td.h > 1e-30f)) return false;
+// on the reduced quote as double-float numbers: beta, c_beta = b_max - beta,
+// x <= 0, T, and ln beta where has_ln (beta below the double-float range,
+// given as 0).  Writes sigma = (s + ds)/sqrt(T) and returns true; returns
+// false, writing nothing, where the quote's scales leave the range this
+// evaluation covers (the caller then takes the FP64 correction).
+FV_DF_FN bool hh3_correction_dfv(df beta, df c_beta, df xd, df ln_beta, bool has_ln, df Td, float s,
+                                 int reg, double& sigma) {
+  if (!(s > 1e-30f && s < 1e30f) || !(Td.h > 1e-30f && Td.h < 1e30f)) return false;
   NBdf v;
   if (!nb_df(xd, s, reg, v)) return false;
   df nu;
@@ -519,27 +533,25 @@ FV_DF_FN bool hh3_correction_df(double beta, double c_beta, double x, double ln_
   if (reg == 1 || reg == 2) {
     // e^E times the reduced price (or its distance to the bound); E <= 80
     // keeps e^E and the products normal FP32 numbers
-    if (!(v.E.h <= 80.0f)) return false;
-    df p;
-    if (!df_of(v.via_comp ? c_beta : beta, p) || !(p.h > 1e-26f)) return false;
+    const df p = v.via_comp ? c_beta : beta;
+    if (!(v.E.h <= 80.0f) || !(p.h > 1e-26f)) return false;
     const df pe = dmul(p, dexp(v.E));
     nu = dmul(s2pi, v.via_comp ? dsub(v.B, pe) : dsub(pe, v.B));
   } else {
     if (!(v.B.h > 1e-30f) || !(v.E.h < 1e30f)) return false;
-    // ln B (or ln C), and ln beta (region 0, unless preset) or ln c_beta
+    // ln B (or ln C), and ln beta (region 0, unless given) or ln c_beta
     // (region 3), through one loop body of the logarithm
-    const double d = reg == 0 ? beta : c_beta;
-    if (!(d > 0.0)) return false;
-    const bool preset = reg == 0 && ln_beta != 0.0;
-    df L1 = mk(0.0f);
-    if (preset && !df_of(ln_beta, L1)) return false;
+    const df d = reg == 0 ? beta : c_beta;
+    const bool given = reg == 0 && has_ln;
+    if (!given && !(d.h > 1e-37f)) return false;
+    df L1 = given ? ln_beta : mk(0.0f);
     int m0, m1;
     float fh0, fl0, fh1, fl1;
     log_arg(v.B, m0, fh0, fl0);
-    log_arg_of(d, m1, fh1, fl1);
+    log_arg(given ? v.B : d, m1, fh1, fl1);
     df L0 = mk(0.0f);
 #pragma unroll 1
-    for (int i = 0; i < (preset ? 1 : 2); i++) {
+    for (int i = 0; i < (given ? 1 : 2); i++) {
       const df l = dlog_core(i == 0 ? m0 : m1, i == 0 ? fh0 : fh1, i == 0 ? fl0 : fl1);
       if (i == 0) L0 = l;
       else L1 = l;
@@ -580,6 +592,189 @@ FV_DF_FN bool hh3_correction_df(double beta, double c_beta, double x, double ln_
   if (sn.h <= 0.25f * s) sn = mk(0.25f * s);
   sigma = to_double(dmul(sn, drsqrt(Td)));
   return true;
+}
+
+// the same from the FP64 reduced quote (ln_beta its preset logarithm or 0)
+FV_DF_FN bool hh3_correction_df(double beta, double c_beta, double x, double ln_beta, double T,
+                                float s, int reg, double& sigma) {
+  df xd, Td, bd = mk(0.0f), cd = mk(0.0f), lb = mk(0.0f);
+  if (x == 0.0) {
+    xd = mk(0.0f);
+  } else if (!df_of(x, xd)) {
+    return false;
+  }
+  if (!df_of(T, Td)) return false;
+  bool has_ln = ln_beta != 0.0;
+  if (has_ln && !df_of(ln_beta, lb)) return false;
+  if (!has_ln && beta > 0.0 && !df_of(beta, bd)) {
+    // beta below the double-float range: the lowest region works with ln beta
+    if (reg != 0) return false;
+    lb = dlog_of(beta);
+    has_ln = true;
+  }
+  if (c_beta > 0.0 && !df_of(c_beta, cd)) return false;
+  return hh3_correction_dfv(bd, cd, xd, lb, has_ln, Td, s, reg, sigma);
+}
+
+// ---------------------------------------------------------------------------
+// The status rule and the reduction to an out-of-the-money call (Section
+// 2.2's shared preprocessing) in double-float, for the mixed solver
+// ---------------------------------------------------------------------------
+// Status codes of the FP64 rule (fv.h's fv_quote_status)
+enum { DF_Q_OK = 0, DF_Q_BELOW = 1, DF_Q_ABOVE = 2, DF_Q_INVALID = 3 };
+
+struct NormDF {
+  int status;     // the FP64 rule's status (when !fp64)
+  bool solve;     // a positive root exists
+  bool fp64;      // not decided here: the quote takes the FP64 rule
+  bool tiny;      // beta below the double-float range; ln_beta holds ln beta
+  df beta, x, bmax, c_beta, ln_beta;  // x = -|ln(F/K)|, c_beta = b_max - beta
+};
+
+FV_DF_FN bool finite64(double v) {
+  return (dbits(v) & 0x7fffffffffffffffULL) < 0x7ff0000000000000ULL;
+}
+FV_DF_FN bool pos_finite64(double v) {
+  const uint64_t b = dbits(v);
+  return b != 0 && b < 0x7ff0000000000000ULL;  // sign clear, nonzero, finite
+}
+FV_DF_FN double dsub64(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+// a double-float for d = 0 or 2^-100 <= |d| < 2^127
+FV_DF_FN bool df_of0(double d, df& out) {
+  if (d == 0.0) {
+    out = mk(0.0f);
+    return true;
+  }
+  return df_of(d, out);
+}
+// within [2^-60, 2^60]: products and quotients of two such stay normal FP32
+FV_DF_FN bool mid_range(float v) { return v >= 8.673617379884035e-19f && v <= 1.152921504606847e18f; }
+
+// The decision and the reduced quote of one quote, where the double-float
+// evaluation can take them with certainty; otherwise fp64 = true and the
+// caller applies the FP64 rule (its status then decides).
+//  - Validity: the FP64 rule's tests (non-finite inputs, F, K, T <= 0, flag
+//    not +-1: INVALID).
+//  - x = ln(F/K): near the money (K/2 <= F <= 2K) log1p((F - K)/K) with F - K
+//    exact in FP64 (Sterbenz) and log1p on the unrounded 1 + u; else ln of
+//    the ratio.  Black-Scholes / BSM add (r - q) T; where that sum cancels to
+//    below 1/8 of its terms the quote takes the FP64 rule (x's error, ~2^-46
+//    of the larger term, moves sigma by about that error over max(|x|, s):
+//    below 2^-43 relative with the guard).
+//  - In the money (theta x > 0) the intrinsic value beta - iota cancels: the
+//    FP64 rule.
+//  - Out of the money iota = 0: BELOW exactly where P < 0; ABOVE where
+//    beta >= b_max (1 - 2^-46), decided here only farther than 2^-42 b_max
+//    from that threshold (the two evaluations carry ~2^-45 and the FP64
+//    rule's roundings a few ulp), else the FP64 rule.
+//  - beta = P e^{rate}/sqrt(F K) (rate = r T, or (r + q) T/2 with S); below
+//    2^-90 the reduced price is carried as ln beta = ln P + rate - ln(F K)/2
+//    (FP64 keeps beta itself down to its subnormals: quotes where it would
+//    underflow take the FP64 rule).
+// Scales outside the double-float range take the FP64 rule.
+FV_DF_FN NormDF decide_df(int model, double P, double SF, double K, double T, double r,
+                          double q, int flag) {
+  NormDF o;
+  o.status = DF_Q_INVALID;
+  o.solve = false;
+  o.fp64 = false;
+  o.tiny = false;
+  o.beta = o.x = o.c_beta = o.ln_beta = mk(0.0f);
+  o.bmax = mk(1.0f);
+  const bool bsm = model == 2;
+  if (!(flag == 1 || flag == -1) || !finite64(P) || !pos_finite64(SF) || !pos_finite64(K) ||
+      !pos_finite64(T) || !finite64(r) || (bsm && !finite64(q)))
+    return o;
+  const double qq = bsm ? q : 0.0;
+  df Sd, Kd, Td, rd, qd;
+  if (!df_of(SF, Sd) || !df_of(K, Kd) || !df_of(T, Td) || !df_of0(r, rd) || !df_of0(qq, qd) ||
+      !mid_range(Sd.h) || !mid_range(Kd.h) || !mid_range(Td.h) || !(rd.h <= 1e6f && rd.h >= -1e6f) ||
+      !(qd.h <= 1e6f && qd.h >= -1e6f)) {
+    o.fp64 = true;
+    return o;
+  }
+  // x = ln(F/K) (+ (r - q) T)
+  df x;
+  const uint64_t bs = dbits(SF), bk = dbits(K), one = 1ULL << 52;
+  const bool near = bs + one >= bk && bs <= bk + one;  // K/2 <= SF <= 2K (normal SF, K)
+  if (near) {
+    const double d = dsub64(SF, K);  // exact
+    df dd;
+    if (!df_of0(d, dd)) {
+      o.fp64 = true;
+      return o;
+    }
+    x = dlog1p(dmul(dd, drcp(Kd)));
+  } else {
+    x = dlog(dmul(Sd, drcp(Kd)));
+  }
+  if (model != 0) {
+    const df g = dmul(dsub(rd, qd), Td);
+    const float big = fmaxf(fabsf(x.h), fabsf(g.h));
+    x = dadd(x, g);
+    if (fabsf(x.h) < 0.125f * big) {
+      o.fp64 = true;
+      return o;
+    }
+  }
+  const df rate = model == 0 ? dmul(rd, Td) : dscale(dmul(dadd(rd, qd), Td), 0.5f);
+  // in the money, or scales beyond the exponentials' range: the FP64 rule
+  const bool itm = flag > 0 ? x.h > 0.0f : x.h < 0.0f;
+  if (itm || !(fabsf(x.h) <= 120.0f) || !(fabsf(rate.h) <= 60.0f)) {
+    o.fp64 = true;
+    return o;
+  }
+  const df xo = x.h > 0.0f ? neg(x) : x;
+  o.x = xo;
+  o.bmax = dexp(dscale(xo, 0.5f));
+  if (P < 0.0) {
+    o.status = DF_Q_BELOW;
+    return o;
+  }
+  o.status = DF_Q_OK;
+  if (P == 0.0) return o;  // beta = 0: at the intrinsic value, sigma = 0
+  df Pd;
+  df beta = mk(0.0f);
+  if (df_of(P, Pd)) beta = dmul(dmul(Pd, dexp(rate)), drsqrt(dmul(Sd, Kd)));
+  if (beta.h >= 8.077935669463161e-28f) {  // 2^-90
+    // ABOVE: beta >= b_max (1 - 2^-46), with a guard band of 2^-42 b_max
+    const df lim = dsub(o.bmax, dscale(o.bmax, 1.4210854715202004e-14f));
+    const df t = dsub(beta, lim);
+    if (fabsf(t.h) <= 2.2737367544323206e-13f * o.bmax.h) {
+      o.fp64 = true;
+      return o;
+    }
+    if (t.h >= 0.0f) {
+      o.status = DF_Q_ABOVE;
+      return o;
+    }
+    o.solve = true;
+    o.beta = beta;
+    o.c_beta = dsub(o.bmax, beta);
+    return o;
+  }
+  // beta below 2^-90: ln beta from the logarithms of P, F and K
+  if (P < 2.2250738585072014e-308 || P > 1e30) {
+    o.fp64 = true;
+    return o;
+  }
+  const df lnb = dsub(dadd(dlog_of(P), rate), dscale(dadd(dlog_of(SF), dlog_of(K)), 0.5f));
+  // FP64 beta stays normal (its own rule then solves), and far below b_max
+  if (!(lnb.h > -700.0f) || !(lnb.h < 0.5f * xo.h - 1.0f)) {
+    o.fp64 = true;
+    return o;
+  }
+  o.solve = true;
+  o.tiny = true;
+  o.ln_beta = lnb;
+  o.c_beta = o.bmax;
+  return o;
 }
 
 }  // namespace fvdf

@@ -269,7 +269,9 @@ static cudaError_t launch_refine(const IvArgs& a, cudaStream_t st) {
 
 template <typename InT, int PREC, int Q, int MINB, bool LATE32>
 __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, TileSched ts) {
-  __shared__ BinSmem<kBinThreads, Q> sm;
+  using Smem = typename std::conditional<PREC == P_MIXED, BinSmemMixed<kBinThreads, Q>,
+                                         BinSmem<kBinThreads, Q>>::type;
+  __shared__ Smem sm;
   for_each_tile(ts, kBinThreads * Q, a.n, [&](int64_t base, int count) {
     auto load = [&](int li, double& P, double& SF, double& K, double& T, double& r, double& q,
                     int& flag) {
@@ -277,7 +279,10 @@ __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, T
       load_quote<InT>(a, base + li, P, SF, K, T, r, q, flag);
       return true;
     };
-    lbr_binned_tile<PREC, kBinThreads, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
+    if constexpr (PREC == P_MIXED)
+      lbr_binned_tile_mixed<kBinThreads, Q>(sm, a.model, load, a.sigma, a.status, base);
+    else
+      lbr_binned_tile<PREC, kBinThreads, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
   });
 }
 

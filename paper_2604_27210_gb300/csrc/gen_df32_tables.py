@@ -26,7 +26,9 @@ log: Tang's table-driven method (ACM TOMS 16(4), 1990) on a 1/128 grid:
 y = 2^m f, f in [1/sqrt2, sqrt2), F_j = 1 + j/128 nearest f (j = -38..53),
 c_j = 1/F_j rounded to FP32, r = f c_j - 1 (f_hi c_j exact as a two-product),
     ln y = m ln2 + L_j + log1p(r),   L_j = -ln(c_j) as a double-float pair,
-|r| <= 2^-8; ln2 in three FP32 parts of 12, 12 and 24 bits.
+|r| <= 2^-7.5; ln2 in three FP32 parts of 12, 12 and 24 bits.  log1p(u) for
+u in [-1/2, 1] takes the same rows (j = -64..128) with r = (c_j - 1) + c_j u,
+c_j - 1 exact (Sterbenz), so that 1 + u is never rounded.
 
 Run:  python gen_df32_tables.py   (needs mpmath)
 """
@@ -44,7 +46,7 @@ DF_TERMS = 5      # coefficients of degree 0..4 as double-float pairs
 STRIDE = 16       # floats per erfcx piece: c, 5 pairs, 4 singles, pad (64 bytes)
 EXP_N = 128
 LOG_N = 128
-LOG_J = range(-38, 54)
+LOG_J = range(-64, 129)   # [1/sqrt2, sqrt2) for log, 1 + u on [1/2, 2] for log1p
 
 
 def f32(v):

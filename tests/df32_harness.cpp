@@ -68,3 +68,30 @@ int h_corr(double beta, double c_beta, double x, double ln_beta, double T, float
   return fvdf::hh3_correction_df(beta, c_beta, x, ln_beta, T, s, reg, *sigma) ? 1 : 0;
 }
 }
+
+extern "C" {
+// the double-float status rule: out = {status, solve, fp64, tiny}, vals = the
+// reduced quote (beta, x, bmax, c_beta, ln_beta as hi, lo pairs)
+void h_decide(int model, const double* P, const double* SF, const double* K, const double* T,
+              const double* r, const double* q, const signed char* flag, long n, int* out,
+              float* vals) {
+  for (long i = 0; i < n; i++) {
+    const fvdf::NormDF d = fvdf::decide_df(model, P[i], SF[i], K[i], T[i], r[i], q[i], flag[i]);
+    out[4 * i] = d.status;
+    out[4 * i + 1] = d.solve;
+    out[4 * i + 2] = d.fp64;
+    out[4 * i + 3] = d.tiny;
+    const df v[5] = {d.beta, d.x, d.bmax, d.c_beta, d.ln_beta};
+    for (int k = 0; k < 5; k++) {
+      vals[10 * i + 2 * k] = v[k].h;
+      vals[10 * i + 2 * k + 1] = v[k].l;
+    }
+  }
+}
+
+void h_dlog1p(float uh, float ul, float* out) {
+  const df r = fvdf::dlog1p(df{uh, ul});
+  out[0] = r.h;
+  out[1] = r.l;
+}
+}

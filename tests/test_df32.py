@@ -49,6 +49,9 @@ def lib(tmp_path_factory):
     L.h_nb.restype = i
     L.h_corr.argtypes = [d, d, d, d, d, f, i, ctypes.POINTER(ctypes.c_double)]
     L.h_corr.restype = i
+    L.h_dlog1p.argtypes = [f, f, fp]
+    vp = ctypes.c_void_p
+    L.h_decide.argtypes = [i, vp, vp, vp, vp, vp, vp, vp, ctypes.c_long, vp, vp]
     return L
 
 
@@ -277,3 +280,108 @@ def test_committed_tables_are_the_generators_output(tmp_path):
     spec.loader.exec_module(gen)
     out = gen.write(str(tmp_path / "fv_df32_tables.h"))
     assert open(out).read() == open(os.path.join(CSRC, "fv_df32_tables.h")).read()
+
+
+def test_log1p_keeps_the_relative_precision_of_u(lib):
+    g = np.random.default_rng(7)
+    worst = 0.0
+    us = np.concatenate([g.uniform(-0.5, 1.0, 2000), g.uniform(-1e-2, 1e-2, 500),
+                         np.sign(g.uniform(-1, 1, 500)) * 10.0 ** g.uniform(-12, -3, 500),
+                         [k / 128 for k in range(-64, 129)], [0.0]])
+    for u in us:
+        uh, ul = split(mp.mpf(float(u)) * (1 + mp.mpf(g.uniform(-1, 1)) * 1e-8))
+        _, r = call2(lib.h_dlog1p, uh, ul)
+        ref = mp.log1p(val((uh, ul)))
+        if ref == 0:
+            assert val(r) == 0
+            continue
+        worst = max(worst, abs(float((val(r) - ref) / ref)))
+    # -ln c_j and log1p(r) may cancel by a factor ~2 half-way between rows
+    assert worst <= 2.0 ** -45, worst
+
+
+# ---------------------------------------------------------------------------
+# the double-float status rule against the oracle's FP64 rule
+# ---------------------------------------------------------------------------
+def _decide(lib, w):
+    n = len(w["P"])
+    cols = [np.ascontiguousarray(np.asarray(w[k], dtype=np.float64)) for k in
+            ("P", "S_or_F", "K", "T", "r")]
+    q = np.ascontiguousarray(np.zeros(n) if w.get("q") is None else np.asarray(w["q"], np.float64))
+    flag = np.ascontiguousarray(np.asarray(w["flag"], dtype=np.int8))
+    out = np.empty((n, 4), np.int32)
+    vals = np.empty((n, 10), np.float32)
+    lib.h_decide(int(w["model"]), *[c.ctypes.data for c in cols], q.ctypes.data, flag.ctypes.data,
+                 n, out.ctypes.data, vals.ctypes.data)
+    v = vals.astype(np.float64)
+    return out, {k: v[:, 2 * i] + v[:, 2 * i + 1] for i, k in
+                 enumerate(("beta", "x", "bmax", "c_beta", "ln_beta"))}
+
+
+def _workloads():
+    from oracle import oracle as orc
+    from paper_2604_27210_gb300 import workloads as wl
+    out = []
+    g = wl.fill_prices(wl.bsm_grid(512, 256, seed=1), orc.price)
+    out.append(("bsm grid", g))
+    out.append(("black76", wl.fill_prices(wl.black76_quotes(50000, seed=3), orc.price)))
+    out.append(("bsm quotes", wl.fill_prices(wl.bsm_quotes(50000, seed=4), orc.price)))
+    return out
+
+
+@pytest.mark.parametrize("name", ["bsm grid", "black76", "bsm quotes"])
+def test_status_rule_in_double_float_matches_the_fp64_rule(lib, name):
+    from oracle import oracle as orc
+    w = dict(_workloads())[name]
+    n = len(w["P"])
+    out, v = _decide(lib, w)
+    st, x, beta, margin = orc.status(w["model"], *[w[k] for k in ("P", "S_or_F", "K", "T", "r",
+                                                                     "q", "flag")])
+    dec = out[:, 2] == 0
+    # every quote the double-float rule decides has the FP64 rule's status
+    assert np.array_equal(out[dec, 0], st[dec]), (out[dec, 0] != st[dec]).sum()
+    # in-the-money quotes always take the FP64 rule; out of the money most are
+    # decided here
+    itm = (np.asarray(w["flag"]) * x > 0) & (st != orc.INVALID)
+    assert not np.any(dec & itm)
+    otm = ~itm & (st != orc.INVALID)
+    assert dec[otm].mean() > 0.97, dec[otm].mean()
+    # the reduced quote of the solved ones, against the FP64 rule's values
+    solve = dec & (out[:, 1] == 1)
+    assert solve.sum() > 0.3 * n
+    norm = solve & (out[:, 3] == 0)
+    rel_x = np.abs(-np.abs(x[norm]) - v["x"][norm]) / np.abs(x[norm])
+    rel_b = np.abs(beta[norm] - v["beta"][norm]) / beta[norm]
+    assert rel_x.max() <= 2.0 ** -42, rel_x.max()
+    assert rel_b.max() <= 2.0 ** -44, rel_b.max()
+    bmax = np.exp(-np.abs(x[norm]) / 2)
+    assert np.all(np.abs(v["bmax"][norm] - bmax) <= 2.0 ** -44 * bmax)
+    assert np.all(np.abs(v["c_beta"][norm] - (bmax - beta[norm])) <= 2.0 ** -43 * bmax)
+    tiny = solve & (out[:, 3] == 1)
+    if tiny.any():
+        assert np.all(np.abs(v["ln_beta"][tiny] - np.log(beta[tiny])) <= 2.0 ** -44 * np.abs(np.log(beta[tiny])))
+
+
+def test_status_rule_in_double_float_edge_cases(lib):
+    from oracle import oracle as orc
+    F, K, T, r = 100.0, 120.0, 0.5, 0.03
+    bmax_price = K * np.exp(-r * T)  # a put's bound: the discounted strike
+    # call out of the money (F < K): bound F e^{-rT}; put in the money
+    P = np.array([0.0, -0.0, -1e-3, 1e-310, 1e-200, 5.0, F * np.exp(-r * T) * (1 - 1e-15),
+                  F * np.exp(-r * T) * (1 + 1e-12), F * np.exp(-r * T) * (1 - 1e-9), np.nan, 5.0,
+                  5.0, 5.0])
+    n = len(P)
+    w = {"model": 0, "P": P, "S_or_F": np.array([F] * 10 + [np.inf, F, F]),
+         "K": np.array([K] * 11 + [-1.0, K]), "T": np.full(n, T), "r": np.full(n, r), "q": None,
+         "flag": np.array([1] * 12 + [2], np.int8)}
+    out, v = _decide(lib, w)
+    st, x, beta, margin = orc.status(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    dec = out[:, 2] == 0
+    assert np.array_equal(out[dec, 0], st[dec])
+    assert list(out[:3, 0]) == [orc.OK, orc.OK, orc.BELOW_INTRINSIC] and list(out[:3, 1]) == [0, 0, 0]
+    assert out[3, 2] == 1  # FP64 beta would be subnormal: the FP64 rule
+    assert out[4, 3] == 1 and out[4, 1] == 1  # tiny price: carried as ln beta
+    assert out[6, 2] == 1  # within the guard band of the bound
+    assert out[7, 0] == orc.ABOVE_MAX and out[8, 0] == orc.OK
+    assert list(out[9:, 0]) == [orc.INVALID] * 4
+    assert bmax_price > 0
