@@ -282,6 +282,34 @@ FV_DF_FN df dexp(df a) {
   return dscale(e, pow2f(k >> 7));
 }
 
+// e^a and expm1(a) for -70 <= a <= 0 from one reduction, e^a to ~2^-46 and
+// expm1(a) to ~2^-44 relative (the table's pair holds 2^(j/128) to 2^-48,
+// against an expm1 down to ~1/200 of it): expm1(r) = r + r^2/2 + r^3/6 in
+// double-float plus r^4/24 + r^5/120
+// + r^6/720 in FP32 (below 2^-28 of r), and
+//   expm1(a) = (2^m T_h - 1) + 2^m (T_l + T expm1(r)),
+// the first term exact for m = 0, -1 (Sterbenz) and the two never cancelling
+// by more than a factor ~1.3; below |a| = 1/200 the reduction is skipped
+// (k = 0, expm1(a) = expm1(r)).
+FV_DF_FN df dexp_em1(df a, df& em1_out) {
+  const bool tiny = fabsf(a.h) < 0.005f;
+  const float t = fma_(a.h, FV_DF_EXP_INV, 12582912.0f);
+  const int k = tiny ? 0 : (int)(fbits(t) - fbits(12582912.0f));
+  const float kd = tiny ? 0.0f : sub(t, 12582912.0f);
+  const float r1 = fma_(-kd, FV_DF_EXP_L2, fma_(-kd, FV_DF_EXP_L1, a.h));
+  const df r = dadd(dsub(two_sum(r1, a.l), two_prod(kd, FV_DF_EXP_L3)), mk(mul(-kd, FV_DF_EXP_L4)));
+  const df r2 = dsqr(r);
+  const df r3 = dmul(r2, r);
+  const float rh = r.h;
+  const float tail = mul(mul(r2.h, r2.h), fma_(fma_(rh, 1.0f / 720.0f, 1.0f / 120.0f), rh, 1.0f / 24.0f));
+  const df em1 = dadd(r, dadd_fast(dscale(r2, 0.5f), dadd_fast(dmul(r3, df{FV_DF_SIXTH_HI, FV_DF_SIXTH_LO}), mk(tail))));
+  const df T = ld2(kExpDf + 2 * (k & (FV_DF_EXP_N - 1)));
+  const float p2 = pow2f(k >> 7);
+  const df Tem1 = dadd(dmul(T, em1), mk(T.l));
+  em1_out = dadd(two_sum(mul(T.h, p2), -1.0f), dscale(Tem1, p2));
+  return dscale(dadd_fast(mk(T.h), Tem1), p2);
+}
+
 // ln(2^m f) for f = fh + fl in [1/sqrt2, sqrt2) (fh with 24 bits): Tang's
 // table-driven method on a 1/128 grid, r = f c_j - 1 exact as a double-float
 // (f_h c_j a two-product, its head minus one exact by Sterbenz), log1p(r) =
@@ -667,12 +695,13 @@ FV_DF_FN bool mid_range(float v) { return v >= 8.673617379884035e-19f && v <= 1.
 //    below 1/8 of its terms the quote takes the FP64 rule (x's error, ~2^-46
 //    of the larger term, moves sigma by about that error over max(|x|, s):
 //    below 2^-43 relative with the guard).
-//  - In the money (theta x > 0) the intrinsic value beta - iota cancels: the
-//    FP64 rule.
-//  - Out of the money iota = 0: BELOW exactly where P < 0; ABOVE where
-//    beta >= b_max (1 - 2^-46), decided here only farther than 2^-42 b_max
-//    from that threshold (the two evaluations carry ~2^-45 and the FP64
+//  - BELOW where beta < iota (1 - 2^-46) (out of the money iota = 0: exactly
+//    where P < 0), ABOVE where the reduced price beta - iota >= b_max
+//    (1 - 2^-46): each decided here only farther than 2^-42 of iota or
+//    b_max from its threshold (the evaluations carry ~2^-45 and the FP64
 //    rule's roundings a few ulp), else the FP64 rule.
+//  - In the money (theta x > 0) the reduced price beta - iota cancels: taken
+//    here where it keeps at least half of beta, else the FP64 rule.
 //  - beta = P e^{rate}/sqrt(F K) (rate = r T, or (r + q) T/2 with S); below
 //    2^-90 the reduced price is carried as ln beta = ln P + rate - ln(F K)/2
 //    (FP64 keeps beta itself down to its subnormals: quotes where it would
@@ -724,24 +753,55 @@ FV_DF_FN NormDF decide_df(int model, double P, double SF, double K, double T, do
     }
   }
   const df rate = model == 0 ? dmul(rd, Td) : dscale(dmul(dadd(rd, qd), Td), 0.5f);
-  // in the money, or scales beyond the exponentials' range: the FP64 rule
-  const bool itm = flag > 0 ? x.h > 0.0f : x.h < 0.0f;
-  if (itm || !(fabsf(x.h) <= 120.0f) || !(fabsf(rate.h) <= 60.0f)) {
+  // scales beyond the exponentials' range: the FP64 rule
+  if (!(fabsf(x.h) <= 120.0f) || !(fabsf(rate.h) <= 60.0f)) {
     o.fp64 = true;
     return o;
   }
+  const bool itm = flag > 0 ? x.h > 0.0f : x.h < 0.0f;
   const df xo = x.h > 0.0f ? neg(x) : x;
   o.x = xo;
-  o.bmax = dexp(dscale(xo, 0.5f));
+  df E;  // expm1(-|x|/2)
+  o.bmax = dexp_em1(dscale(xo, 0.5f), E);
   if (P < 0.0) {
     o.status = DF_Q_BELOW;
     return o;
   }
-  o.status = DF_Q_OK;
-  if (P == 0.0) return o;  // beta = 0: at the intrinsic value, sigma = 0
   df Pd;
   df beta = mk(0.0f);
-  if (df_of(P, Pd)) beta = dmul(dmul(Pd, dexp(rate)), drsqrt(dmul(Sd, Kd)));
+  if (P != 0.0 && df_of(P, Pd)) beta = dmul(dmul(Pd, dexp(rate)), drsqrt(dmul(Sd, Kd)));
+  if (itm) {
+    // iota = e^{|x|/2} - e^{-|x|/2} = -E (1 + b_max)/b_max, the FP64 rule's
+    // form; BELOW where beta < iota (1 - 2^-46), with the guard band 2^-42 iota
+    const df iota = dmul(dmul(neg(E), dadd(mk(1.0f), o.bmax)), drcp(o.bmax));
+    if (P == 0.0) {
+      o.status = DF_Q_BELOW;
+      return o;
+    }
+    if (!(beta.h >= 8.077935669463161e-28f) || !(iota.h > 0.0f)) {
+      o.fp64 = true;
+      return o;
+    }
+    const df tb = dsub(beta, dsub(iota, dscale(iota, 1.4210854715202004e-14f)));
+    if (fabsf(tb.h) <= 2.2737367544323206e-13f * iota.h) {
+      o.fp64 = true;
+      return o;
+    }
+    if (tb.h < 0.0f) {
+      o.status = DF_Q_BELOW;
+      return o;
+    }
+    // the reduced price beta - iota, where it keeps at least half of beta
+    // (its error is then below 3 2^-46 of it); deeper: the FP64 rule
+    const df bo = dsub(beta, iota);
+    if (!(bo.h >= 0.5f * beta.h)) {
+      o.fp64 = true;
+      return o;
+    }
+    beta = bo;
+  }
+  o.status = DF_Q_OK;
+  if (P == 0.0) return o;  // beta = 0 out of the money: at the intrinsic value, sigma = 0
   if (beta.h >= 8.077935669463161e-28f) {  // 2^-90
     // ABOVE: beta >= b_max (1 - 2^-46), with a guard band of 2^-42 b_max
     const df lim = dsub(o.bmax, dscale(o.bmax, 1.4210854715202004e-14f));

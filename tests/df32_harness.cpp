@@ -95,3 +95,12 @@ void h_dlog1p(float uh, float ul, float* out) {
   out[1] = r.l;
 }
 }
+
+extern "C" void h_dexp_em1(float ah, float al, float* out) {
+  df em1;
+  const df e = fvdf::dexp_em1(df{ah, al}, em1);
+  out[0] = e.h;
+  out[1] = e.l;
+  out[2] = em1.h;
+  out[3] = em1.l;
+}
