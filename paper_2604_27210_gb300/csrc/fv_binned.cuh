@@ -132,11 +132,13 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
 }
 
 // ---------------------------------------------------------------------------
-// The mixed solver's tile: the status rule and reduction in double-float
+// The mixed and FP32 solvers' tile: the status rule and reduction in
+// double-float
 //
 // On this GPU the FP64 status rule (logarithm, exponentials, reciprocal
 // square root) takes more time than the mixed solver's FP32 iterations and
-// double-float correction together.  Pass A decides each quote with the
+// double-float correction together, and several times the FP32 solver's
+// whole solve.  Pass A decides each quote with the
 // double-float rule (fvdf::decide_df), which leaves to the FP64 rule the
 // quotes it cannot decide with certainty: in the money (the intrinsic value
 // cancels), within its guard band of a threshold, BSM log-moneyness that
@@ -144,7 +146,9 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
 // and pass B applies the FP64 rule to the list with every thread of the block
 // (packed lanes whatever the tile's mix).  Statuses are the FP64 rule's.
 // Pass C evaluates the FP32 guess and the sort key of every solving quote;
-// phase 2 is the binned tile's, with the reduced quote as double-float.
+// phase 2 is the binned tile's, with the reduced quote as double-float: the
+// FP32 iterations, then (mixed) the double-float correction.  The FP32 path
+// marks nothing for the refinement pass (its 1e-5 does not need it).
 // ---------------------------------------------------------------------------
 template <int THREADS, int Q>
 struct BinSmemMixed {
@@ -181,8 +185,8 @@ static __device__ __noinline__ double mixed_solve_fp64(Reduced<double> q64, doub
   return lbr_solve_quote<P_MIXED>(q64) * rsqrt(T);
 }
 
-template <int THREADS, int Q, typename Load>
-__device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& sm, int model,
+template <int PREC, int THREADS, int Q, typename Load>
+__device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q>& sm, int model,
                                                       const Load& load, double* sigma,
                                                       uint8_t* status, int64_t out0) {
   using fvdf::df;
@@ -203,8 +207,8 @@ __device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& 
       sm.list[atomicAdd(&sm.nlist, 1)] = (unsigned short)li;
       continue;
     }
-    // out of the money: ill-conditioned where b_max - beta < b_max/64
-    const bool refine = d.solve && d.c_beta.h < 0.015625f * d.bmax.h;
+    // ill-conditioned (mixed path) where b_max - beta < b_max/64
+    const bool refine = PREC == P_MIXED && d.solve && d.c_beta.h < 0.015625f * d.bmax.h;
     status[out0 + li] = (uint8_t)d.status | (refine ? kRefineMark : 0);
     if (d.solve && !refine) {
       sm.beta[li] = d.beta;
@@ -227,7 +231,7 @@ __device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& 
     int flag;
     load(li, P, SF, K, T, r, q, flag);
     const Norm nq = decide(model, P, SF, K, T, r, q, flag);
-    const bool refine = needs_refine(nq);
+    const bool refine = PREC == P_MIXED && needs_refine(nq);
     status[out0 + li] = (uint8_t)nq.status | (refine ? kRefineMark : 0);
     if (nq.status == Q_OK && nq.solve && !refine) {
       const Reduced<double> q64 = reduced64(nq);
@@ -249,9 +253,12 @@ __device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& 
         sm.lnb[li] = lb;
         sm.T[li] = T;
         sm.state[li] = tiny ? 2 : 1;
-      } else {
+      } else if (PREC == P_MIXED) {
         // scales outside FP32's range: the whole mixed solve in FP64 here
         sigma[out0 + li] = mixed_solve_fp64(q64, T);
+      } else {
+        int reg = 1;
+        sigma[out0 + li] = (double)lbr_solve<float>(reduced32(q64), 2, 2, 0.0f, reg) * rsqrt(T);
       }
     } else if (!refine) {
       sigma[out0 + li] = nq.status == Q_OK ? 0.0 : qnan();
@@ -294,7 +301,7 @@ __device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& 
   for (int k = 0; k < Q; k++)
     if (key[k] != 0xff) sm.perm[sm.off[key[k]] + rank[k]] = (unsigned short)(k * THREADS + tid);
   __syncthreads();
-  // phase 2: the FP32 iterations and the double-float correction
+  // phase 2: the FP32 iterations and (mixed) the double-float correction
   const int ns = sm.off[kBinKeys];
   for (int j = tid; j < ns; j += THREADS) {
     const int li = sm.perm[j];
@@ -311,6 +318,12 @@ __device__ __forceinline__ void lbr_binned_tile_mixed(BinSmemMixed<THREADS, Q>& 
       s32 = guarded<float>(s32, hh3_step<float>(objective<float>(q32, s32, reg)));
     df Td;
     double sig;
+    if (PREC == P_FP32) {
+      // sigma = s/sqrt(T) with the double-float reciprocal square root
+      sigma[out0 + li] = fvdf::df_of(T, Td) ? fvdf::to_double(fvdf::dmulf(fvdf::drsqrt(Td), s32))
+                                            : (double)s32 * rsqrt(T);
+      continue;
+    }
     if (!(fvdf::df_of(T, Td) &&
           fvdf::hh3_correction_dfv(beta, cbeta, x, lnb, tiny, Td, s32, reg, sig))) {
       // the FP64 correction from the double-float values (rare)

@@ -269,7 +269,7 @@ static cudaError_t launch_refine(const IvArgs& a, cudaStream_t st) {
 
 template <typename InT, int PREC, int Q, int MINB, bool LATE32>
 __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, TileSched ts) {
-  using Smem = typename std::conditional<PREC == P_MIXED, BinSmemMixed<kBinThreads, Q>,
+  using Smem = typename std::conditional<PREC != P_FP64, BinSmemMixed<kBinThreads, Q>,
                                          BinSmem<kBinThreads, Q>>::type;
   __shared__ Smem sm;
   for_each_tile(ts, kBinThreads * Q, a.n, [&](int64_t base, int count) {
@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, T
       load_quote<InT>(a, base + li, P, SF, K, T, r, q, flag);
       return true;
     };
-    if constexpr (PREC == P_MIXED)
-      lbr_binned_tile_mixed<kBinThreads, Q>(sm, a.model, load, a.sigma, a.status, base);
+    if constexpr (PREC != P_FP64)
+      lbr_binned_tile_df<PREC, kBinThreads, Q>(sm, a.model, load, a.sigma, a.status, base);
     else
       lbr_binned_tile<PREC, kBinThreads, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
   });
@@ -298,17 +298,19 @@ static cudaError_t launch_binned(const IvArgs& a, cudaStream_t st) {
   kernel<<<grid, kBinThreads, 0, st>>>(a, ts);
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess) return le;
-  return launch_refine<InT, PREC>(a, st);
+  if constexpr (PREC == P_FP32)
+    return cudaSuccess;  // nothing marked for refinement
+  else
+    return launch_refine<InT, PREC>(a, st);
 }
 
 // Tile shapes measured on GB300 (16.8 M quotes of the BSM grid, one resident
 // wave of blocks): the FP64 solve runs 2 quotes per thread at 4 blocks per SM
 // (9.39 ms; 1 x 4 9.30 ms, 3 x 4 9.32 ms, 2 x 3 9.45 ms: within 1 %, while
-// 5 blocks per SM would cap the registers at 48 and spill); the mixed path
-// 2 quotes per thread, 4 blocks per SM and its FP32 iterations in phase 2,
-// where they interleave with the FP64 correction (1 or 2 quotes per thread at
-// 3 to 5 blocks per SM within 1.2 % when it was tuned).  The FP32 path has
-// no FP64 solve to sort for and stays unbinned.
+// 5 blocks per SM would cap the registers at 48 and spill).  The mixed and
+// FP32 paths run the tile whose status rule is in double-float (2 quotes per
+// thread, 4 blocks per SM; their FP32 iterations in phase 2).  Batches below
+// kSmallBatch take the unbinned kernel with 64-thread blocks.
 
 template <typename InT, int PREC>
 static void launch_flat_prec(const IvArgs& a, int block, cudaStream_t st) {
@@ -327,7 +329,7 @@ static void launch_flat(const IvArgs& a, int prec, int block, cudaStream_t st) {
 }
 
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
-  if (prec == P_FP32 || a.n < kSmallBatch) {
+  if (a.n < kSmallBatch) {
     const int block = a.n < kSmallBatch ? 64 : 256;
     if (a.f32_inputs)
       launch_flat<float>(a, prec, block, st);
@@ -336,10 +338,12 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
     return cudaGetLastError();
   }
   if (a.f32_inputs)
-    return prec == P_FP64 ? launch_binned<float, P_FP64, 2, 4, false>(a, st)
-                          : launch_binned<float, P_MIXED, 2, 4, true>(a, st);
-  return prec == P_FP64 ? launch_binned<double, P_FP64, 2, 4, false>(a, st)
-                        : launch_binned<double, P_MIXED, 2, 4, true>(a, st);
+    return prec == P_FP64    ? launch_binned<float, P_FP64, 2, 4, false>(a, st)
+           : prec == P_MIXED ? launch_binned<float, P_MIXED, 2, 4, true>(a, st)
+                             : launch_binned<float, P_FP32, 2, 4, true>(a, st);
+  return prec == P_FP64    ? launch_binned<double, P_FP64, 2, 4, false>(a, st)
+         : prec == P_MIXED ? launch_binned<double, P_MIXED, 2, 4, true>(a, st)
+                           : launch_binned<double, P_FP32, 2, 4, true>(a, st);
 }
 
 // ---------------------------------------------------------------------------
