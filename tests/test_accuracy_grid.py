@@ -144,3 +144,65 @@ def test_extreme_grid_all_paths():
         if tol_rest is not None:
             bound = tol_rest + 16 * EPS * (1 + np.nan_to_num(kap[chk], nan=np.inf))
             assert np.all(rel <= bound), (name, (rel > bound).sum(), rel[rel > bound].max())
+
+
+def test_both_grids_through_the_large_batch_tiles():
+    # The accuracy and extreme grids above run below 2^17 quotes, where every
+    # path takes the unbinned kernel and its FP64 status rule.  Repeated past
+    # that size they go through the large-batch tiles: the mixed and FP32 paths
+    # then decide each quote with the double-float status rule, which leaves
+    # the quotes it cannot decide with certainty to the FP64 rule.  Their
+    # statuses must be the FP64 LBR's bit for bit (the same FP64 rule decides
+    # wherever double-float does not), every copy must give the same results,
+    # and sigma must meet the bars of the tests above.
+    import torch
+    from paper_2604_27210_gb300 import fv
+
+    w, X, S = _grid()
+    xs = np.concatenate([-np.logspace(-8, np.log10(20.0), 50), [0.0], np.logspace(-8, np.log10(20.0), 50)])
+    ss = np.logspace(-4, np.log10(20.0), 80)
+    X2, S2 = np.meshgrid(xs, ss, indexing="ij")
+    X2, S2 = np.concatenate([X2.ravel(), X2.ravel()]), np.concatenate([S2.ravel(), S2.ravel()])
+    n2 = X2.size
+    flag2 = np.concatenate([np.ones(n2 // 2, np.int8), -np.ones(n2 // 2, np.int8)])
+    P2 = orc.price(0, np.ones(n2), np.exp(-X2), np.ones(n2), np.zeros(n2), None, S2, flag2)
+    one = {"P": np.concatenate([w["P"], P2]), "F": np.concatenate([w["S_or_F"], np.ones(n2)]),
+           "K": np.concatenate([w["K"], np.exp(-X2)]), "flag": np.concatenate([w["flag"], flag2])}
+    m = one["P"].size
+    reps = -(-(1 << 17) // m) + 1
+    n = m * reps
+    P, F, K, flag = (np.tile(one[k], reps) for k in ("P", "F", "K", "flag"))
+    T, r = np.ones(n), np.zeros(n)
+    ref, st = orc.iv(0, one["P"], one["F"], one["K"], np.ones(m), np.zeros(m), None, one["flag"])
+    v, kap = orc.conditioning(0, one["P"], one["F"], one["K"], np.ones(m), np.zeros(m), None,
+                              one["flag"], ref)
+    amb = orc.status(0, one["P"], one["F"], one["K"], np.ones(m), np.zeros(m), None,
+                     one["flag"])[3] <= 16.0
+    dev = torch.device("cuda:0")
+    t = [torch.tensor(a, device=dev) for a in (P, F, K, T, r)]
+    ft = torch.tensor(flag, device=dev)
+    s64, st64 = (a.cpu().numpy() for a in fv.fv_implied_vol(0, fv.FV_LBR, *t, None, ft))
+    assert np.array_equal(st64.reshape(reps, m), np.tile(st64[:m], (reps, 1)))
+    normal = one["P"] >= 1e-290
+    for name, prec, tol_gate, tol_rest in (("mixed", fv.FV_MIXED, 1e-12, 1e-12),
+                                           ("FP32", fv.FV_FP32, 1e-5, None)):
+        s_gpu, st_gpu = (a.cpu().numpy() for a in fv.fv_implied_vol_ex(0, fv.FV_LBR, prec, *t, None, ft))
+        assert np.array_equal(st_gpu, st64), (name, (st_gpu != st64).sum())
+        # every copy gives the same sigma, whatever tile and lane it landed in
+        sg = s_gpu.reshape(reps, m)
+        assert np.array_equal(np.isnan(sg), np.tile(np.isnan(sg[0]), (reps, 1))), name
+        assert np.all((sg == sg[0]) | np.isnan(sg)), name
+        s1, st1 = sg[0], st_gpu[:m]
+        assert np.array_equal(st1[~amb], st[~amb]), name
+        solved = (st == orc.OK) & (ref > 0) & ~amb
+        assert np.all(np.isfinite(s1[solved]) & (s1[solved] > 0)), name
+        assert np.all(s1[(st == orc.OK) & (ref == 0) & ~amb] == 0), name
+        chk = solved & normal & np.isfinite(ref)
+        rel = np.abs(s1[chk] - ref[chk]) / ref[chk]
+        gate = v[chk] > 1e-8
+        if tol_gate > 1e-12:
+            gate &= kap[chk] <= 1e3
+        assert rel[gate].max() <= tol_gate, (name, rel[gate].max())
+        if tol_rest is not None:
+            bound = tol_rest + 16 * EPS * (1 + np.nan_to_num(kap[chk], nan=np.inf))
+            assert np.all(rel <= bound), (name, (rel > bound).sum(), rel[rel > bound].max())
