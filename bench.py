@@ -280,17 +280,23 @@ def small_batch_latency(fv, torch, dev, reps=200):
 E2E_CHUNK = 1 << 20
 
 
-def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
+def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path, transfer):
     """The same metric through the public API from pinned host buffers: each step
-    is one fv_implied_vol_host call, which copies that step's inputs to the
-    device and sigma + status back, in 1M-quote chunks overlapped with the
-    solve on two streams."""
+    is one fv_implied_vol_host call.  Its inputs start in host memory and sigma +
+    status end there; the timed region holds their whole way across the
+    CPU-GPU link.  transfer = FV_TRANSFER_DIRECT: the solver reads the inputs
+    and writes the outputs in host memory itself (one launch, no staging);
+    FV_TRANSFER_STAGED: 1M-quote chunks copied to the device and back,
+    overlapped with the solve on two streams.  Either way every input byte
+    crosses the link once per step (h2d) and every output byte once (d2h).
+    Returns (ms per step, h2d bytes, d2h bytes, the mode taken)."""
     keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
     host = {k: t_dev[k].cpu().pin_memory() for k in keys}
     n = t_dev["P"].numel()
     out_h = torch.empty(n, dtype=torch.float64).pin_memory()
     st_h = torch.empty(n, dtype=torch.uint8).pin_memory()
     plan = fv.fv_stream_plan_create(E2E_CHUNK)
+    plan.set_transfer(transfer)
     solver = fv.FV_HALLEY if path == "halley" else fv.FV_LBR
     prec = {"lbr": fv.FV_FP64, "halley": fv.FV_FP64, "mixed": fv.FV_MIXED, "fp32": fv.FV_FP32}[path]
 
@@ -313,8 +319,9 @@ def e2e_measure(fv, torch, w_host, t_dev, steps, warmup, path):
     ms = max(e0.elapsed_time(e1), 1e3 * wall) / steps
     h2d = sum(host[k].numel() * host[k].element_size() for k in keys)
     d2h = n * 9
+    taken = {fv.FV_TRANSFER_DIRECT: "direct", fv.FV_TRANSFER_STAGED: "staged"}[plan.last_transfer]
     plan.destroy()
-    return ms, h2d, d2h
+    return ms, h2d, d2h, taken
 
 
 def other_configs(fv, torch, dev, steps=3):
@@ -559,8 +566,13 @@ def main():
             extras[name] = {"value": ws * n / (max_over_ranks(tm / 5, ws) * 1e-3), "unit": "quotes/s",
                             "ms_per_step": tm / 5}
 
-    e2e_ms, h2d, d2h = e2e_measure(fv, torch, w, t, max(3, args.steps // 4), 1, args.path)
+    e2e_steps = max(3, args.steps // 4)
+    e2e_ms, h2d, d2h, e2e_mode = e2e_measure(fv, torch, w, t, e2e_steps, 1, args.path,
+                                             fv.FV_TRANSFER_AUTO)
     e2e_ms = max_over_ranks(e2e_ms, ws)
+    # the chunked-copy pipeline on the same buffers, for comparison
+    staged_ms = max_over_ranks(e2e_measure(fv, torch, w, t, e2e_steps, 1, args.path,
+                                           fv.FV_TRANSFER_STAGED)[0], ws)
 
     cpu = None
     errors = None
@@ -600,7 +612,9 @@ def main():
                 "roofline": roofline, "hbm_roofline": hbm,
                 "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP[args.path] * args.steps,
                 "e2e": {"value": ws * n / (e2e_ms * 1e-3), "unit": UNIT,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": e2e_ms, "transfer": e2e_mode,
+                        "staged_value": ws * n / (staged_ms * 1e-3)},
                 "cpu_baseline": cpu, "errors": errors, "paths": extras, "configs": configs}
         print(json.dumps(line))
     if ws > 1:

@@ -297,26 +297,49 @@ fv_err fv_autotune_cache_put(const char* path, const char* key, int block, int q
 
 fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
 
-/* ---- host-resident batches: copies overlapped with the solve ----------- */
+/* ---- host-resident batches ------------------------------------------- */
 /* A stream plan holds device staging for two chunks of up to chunk_quotes
- * quotes (inputs and outputs) and two CUDA streams.
- * Created once (allocates device memory); used by fv_implied_vol_host. */
+ * quotes (inputs and outputs), two CUDA streams and a 16-byte device tile
+ * counter.  Created once (allocates device memory); used by
+ * fv_implied_vol_host.  One call at a time per plan. */
 typedef struct fv_stream_plan fv_stream_plan;
 fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan);
 fv_err fv_stream_plan_destroy(fv_stream_plan* plan);
 
-/* Implied volatility of n quotes whose inputs and outputs are HOST arrays
- * (page-locked memory lets the copies run concurrently with the solve;
- * pageable memory works but serialises them).  The batch is cut into chunks
- * that alternate between the plan's two streams: while chunk k solves, chunk
+/* How fv_implied_vol_host moves a batch between host and GPU.
+ *  - FV_TRANSFER_DIRECT: the solver reads the inputs and writes sigma and
+ *    status in host memory itself, over the CPU-GPU link (NVLink-C2C on a
+ *    Grace-Blackwell node), in one launch on `stream` with no staging copy.
+ *    Every array must be page-locked host memory the GPU maps
+ *    (cudaHostAlloc, cudaHostRegister, torch's pin_memory()); otherwise the
+ *    call fails with FV_ERR_ARG before any work is queued.
+ *  - FV_TRANSFER_STAGED: chunked copies through the plan's device staging,
+ *    overlapped with the solve on the plan's two streams (below).
+ *  - FV_TRANSFER_AUTO (a new plan's mode): DIRECT when every array is such
+ *    page-locked memory, STAGED otherwise (pageable memory).
+ * The solver's per-quote arithmetic is the same in both modes, so are the
+ * results.  set_transfer: FV_ERR_ARG for an unknown mode.  last_transfer:
+ * the mode the plan's last call took (DIRECT or STAGED; AUTO before the first
+ * call), in *mode. */
+typedef enum { FV_TRANSFER_AUTO = 0, FV_TRANSFER_STAGED = 1, FV_TRANSFER_DIRECT = 2 } fv_transfer;
+fv_err fv_stream_plan_set_transfer(fv_stream_plan* plan, int mode);
+fv_err fv_stream_plan_last_transfer(const fv_stream_plan* plan, int* mode);
+
+/* Implied volatility of n quotes whose inputs and outputs are HOST arrays.
+ * Direct mode: one launch of the solver on `stream` over the host arrays
+ * (the dynamic tile counter in the plan's device memory, since the outputs
+ * are not device memory).  Staged mode: the batch is cut into chunks that
+ * alternate between the plan's two streams: while chunk k solves, chunk
  * k+1's inputs travel to the device and chunk k-1's sigma and status travel
- * back.  Chunks hold chunk_quotes quotes except at the ends: the first three
- * ramp up (1/8, 1/4, 1/2 of it) so that the first solve starts after a short
- * copy, and the last ones halve so that the last solve and copy-out are
- * short.  The pipeline starts after the work already queued on `stream`, and
- * `stream` waits for it, so the outputs are in place once `stream` has
- * completed.  Arguments as fv_implied_vol_ex (contiguous arrays, q may be
- * NULL unless FV_BSM); one call at a time per plan. */
+ * back (page-locked memory lets the copies run concurrently with the solve;
+ * pageable memory works but serialises them).  Chunks hold chunk_quotes
+ * quotes except at the ends: the first three ramp up (1/8, 1/4, 1/2 of it)
+ * so that the first solve starts after a short copy, and the last ones halve
+ * so that the last solve and copy-out are short.  The staged pipeline starts
+ * after the work already queued on `stream`, and `stream` waits for it.  In
+ * both modes the outputs are in place once `stream` has completed.
+ * Arguments as fv_implied_vol_ex (contiguous arrays, q may be NULL unless
+ * FV_BSM). */
 fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solver,
                            fv_precision precision, fv_dtype in_dtype, const void* price,
                            const void* S_or_F, const void* K, const void* T, const void* r,

@@ -769,6 +769,9 @@ struct fv_stream_plan {
   uint8_t* status[2];
   cudaStream_t st[2];
   cudaEvent_t ev_start, ev_end[2];
+  unsigned long long* ctr;  // the direct mode's two tile counters
+  int transfer;             // fv_transfer
+  int last_transfer;
 };
 
 extern "C" {
@@ -786,6 +789,7 @@ fv_err fv_stream_plan_destroy(fv_stream_plan* p) {
     if (p->ev_end[b]) cudaEventDestroy(p->ev_end[b]);
   }
   if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ctr) cudaFree(p->ctr);
   delete p;
   return FV_SUCCESS;
 }
@@ -812,16 +816,55 @@ fv_err fv_stream_plan_create(int64_t chunk_quotes, fv_stream_plan** plan) {
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_end[b], cudaEventDisableTiming);
   }
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaMalloc(&p->ctr, 2 * sizeof(unsigned long long));
   if (ce != cudaSuccess) {
     cudaGetLastError();
     fv_stream_plan_destroy(p);
     return fail(FV_ERR_NOMEM, "%s: %s", fn, cudaGetErrorString(ce));
   }
+  p->transfer = FV_TRANSFER_AUTO;
+  p->last_transfer = FV_TRANSFER_AUTO;
   *plan = p;
   return FV_SUCCESS;
 }
 
+fv_err fv_stream_plan_set_transfer(fv_stream_plan* plan, int mode) {
+  const char* fn = "fv_stream_plan_set_transfer";
+  FV_REQUIRE(plan, "plan", fn);
+  if (mode != FV_TRANSFER_AUTO && mode != FV_TRANSFER_STAGED && mode != FV_TRANSFER_DIRECT)
+    return fail(FV_ERR_ARG, "%s: unknown transfer mode %d", fn, mode);
+  plan->transfer = mode;
+  return FV_SUCCESS;
+}
+
+fv_err fv_stream_plan_last_transfer(const fv_stream_plan* plan, int* mode) {
+  const char* fn = "fv_stream_plan_last_transfer";
+  FV_REQUIRE(plan, "plan", fn);
+  FV_REQUIRE(mode, "mode", fn);
+  *mode = plan->last_transfer;
+  return FV_SUCCESS;
+}
+
 }  // extern "C"
+
+// The address at which the GPU reads and writes host memory in place:
+// page-locked memory (cudaHostAlloc, cudaHostRegister) under unified
+// addressing.  nullptr for pageable, managed or device memory.
+static void* mapped_view(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// one solver launch over a batch whose arrays the device addresses
+static cudaError_t launch_solver(const fvk::IvArgs& a, int solver, int precision, cudaStream_t s) {
+  if (solver == FV_LBR) return fvk::launch_iv_lbr(a, precision, s);
+  if (precision == FV_FP32) return fvk::launch_iv_halley32(a, s);
+  return fvk::launch_iv_halley(a, s);
+}
 
 // Quotes in chunk k of a host batch with `remaining` quotes left and chunks of
 // up to C: the first three ramp up (C/8, C/4, C/2) so that the first solve
@@ -858,6 +901,40 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
   const size_t es = in_dtype == FV_DTYPE_F32 ? 4 : 8;
   const void* host_in[6] = {price, S_or_F, K, T, r, model == FV_BSM ? q : nullptr};
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (plan->transfer != FV_TRANSFER_STAGED) {
+    // direct: the solver works on the host arrays in place, if the GPU maps
+    // every one of them
+    void* dv[6] = {};
+    bool mapped = true;
+    for (int j = 0; j < 6 && mapped; j++)
+      if (host_in[j]) mapped = (dv[j] = mapped_view(host_in[j])) != nullptr;
+    void* dflag = mapped ? mapped_view(flag) : nullptr;
+    void* dsig = dflag ? mapped_view(out_sigma) : nullptr;
+    void* dst = dsig ? mapped_view(status) : nullptr;
+    if (dst) {
+      fvk::IvArgs a;
+      a.model = model;
+      a.f32_inputs = in_dtype == FV_DTYPE_F32;
+      a.P = dv[0];
+      a.SF = dv[1];
+      a.K = dv[2];
+      a.T = dv[3];
+      a.r = dv[4];
+      a.q = dv[5];
+      a.flag = static_cast<const int8_t*>(dflag);
+      a.n = n;
+      a.sigma = static_cast<double*>(dsig);
+      a.status = static_cast<uint8_t*>(dst);
+      for (int j = 0; j < 7; j++) a.st[j] = 1;
+      a.ctr = plan->ctr;
+      plan->last_transfer = FV_TRANSFER_DIRECT;
+      return cuda_result(launch_solver(a, solver, precision, caller), fn);
+    }
+    if (plan->transfer == FV_TRANSFER_DIRECT)
+      return fail(FV_ERR_ARG, "%s: FV_TRANSFER_DIRECT needs every array in page-locked host memory",
+                  fn);
+  }
+  plan->last_transfer = FV_TRANSFER_STAGED;
   cudaError_t ce = cudaEventRecord(plan->ev_start, caller);
   for (int b = 0; b < 2 && ce == cudaSuccess; b++) ce = cudaStreamWaitEvent(plan->st[b], plan->ev_start, 0);
   const int64_t C = plan->chunk;
@@ -888,12 +965,7 @@ fv_err fv_implied_vol_host(fv_stream_plan* plan, fv_model model, fv_solver solve
     a.sigma = plan->sigma[b];
     a.status = plan->status[b];
     for (int j = 0; j < 7; j++) a.st[j] = 1;
-    if (solver == FV_LBR)
-      ce = fvk::launch_iv_lbr(a, (int)precision, s);
-    else if (precision == FV_FP32)
-      ce = fvk::launch_iv_halley32(a, s);
-    else
-      ce = fvk::launch_iv_halley(a, s);
+    ce = launch_solver(a, solver, precision, s);
     if (ce == cudaSuccess)
       ce = cudaMemcpyAsync(out_sigma + off, plan->sigma[b], m * 8, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess)

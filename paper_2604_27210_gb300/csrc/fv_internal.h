@@ -21,6 +21,9 @@ struct IvArgs {
   // element strides of P, S_or_F, K, T, r, q, flag (1 = contiguous, 0 = one
   // value broadcast to every quote)
   int64_t st[7];
+  // two 64-bit device counters for the dynamic tile schedule, or nullptr to
+  // keep them in sigma[0..1] (outputs that live in host memory need these)
+  unsigned long long* ctr = nullptr;
 };
 
 // grid sizing: blocks for n quotes, capped at `per_sm` resident blocks per SM
@@ -28,15 +31,15 @@ int sm_count();
 int grid_for(int64_t n, int block, int per_sm);
 
 // LBR: batches of kSmallBatch quotes or more run the region-binned kernel with
-// dynamic tiles, whose counters are the first two sigma outputs (zeroed on
-// `st` before the launch), then the refinement kernel over the quotes it
-// marked; smaller ones one unbinned kernel
+// dynamic tiles, whose counters are a.ctr or else the first two sigma outputs
+// (zeroed on `st` before the launch), then the refinement kernel over the
+// quotes it marked; smaller ones one unbinned kernel
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
 
 // Halley x8 with the fallback and the double-double refinement of
 // ill-conditioned quotes inside the same kernel (tile-local compaction in
-// shared memory): no workspace.  Large batches zero the first two sigma
-// outputs on `st` before the launch (the dynamic tile counters).
+// shared memory): no workspace.  Large batches zero the dynamic tile
+// counters (a.ctr, else the first two sigma outputs) on `st` before the launch.
 cudaError_t launch_iv_halley(const IvArgs& a, cudaStream_t st);
 // Halley x8 in FP32 on the plain-Phi residual, the same arrangement
 cudaError_t launch_iv_halley32(const IvArgs& a, cudaStream_t st);

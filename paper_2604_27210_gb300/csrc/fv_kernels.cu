@@ -106,21 +106,23 @@ __device__ __forceinline__ void load_quote(const IvArgs& a, int64_t i, double& P
 // which the launcher zeroes on the stream before the launch.  Tiles cover
 // quotes [kHead, n); the head quotes [0, kHead), among them sigma[0..1], are
 // solved by the last block to finish, after every other block has stopped
-// using the counters, so the counters cost no memory of their own.  No block
-// ever waits for another.
+// using the counters, so the counters cost no memory of their own.  A caller
+// whose outputs are host memory read over the CPU-GPU link passes device
+// counters of its own instead (IvArgs::ctr); the tiles then cover [0, n).
+// No block ever waits for another.
 // ---------------------------------------------------------------------------
 constexpr int64_t kHead = 32;
 
 struct TileSched {
   unsigned long long* ctr;  // nullptr: static
   int64_t n_tiles;          // tiles after the head
-  int64_t head;             // kHead (dynamic) or 0 (static)
+  int64_t head;             // kHead (counters in sigma) or 0 (static, or own counters)
 };
 
 static TileSched make_sched(const IvArgs& a, int tile, bool dynamic) {
   TileSched t;
-  t.ctr = dynamic ? reinterpret_cast<unsigned long long*>(a.sigma) : nullptr;
-  t.head = dynamic ? kHead : 0;
+  t.ctr = !dynamic ? nullptr : a.ctr ? a.ctr : reinterpret_cast<unsigned long long*>(a.sigma);
+  t.head = dynamic && a.ctr == nullptr ? kHead : 0;
   t.n_tiles = (a.n - t.head + tile - 1) / tile;
   return t;
 }
@@ -146,6 +148,7 @@ __device__ __forceinline__ void for_each_tile(const TileSched& ts, int tile, int
     const int64_t base = ts.head + t * tile;
     body(base, (int)min((int64_t)tile, n - base));
   }
+  if (ts.head == 0) return;  // own counters: no head to solve (uniform over the block)
   if (threadIdx.x == 0) s_last = atomicAdd(ts.ctr + 1, 1ULL) == (unsigned long long)gridDim.x - 1;
   __syncthreads();
   if (s_last) body(0, (int)min(ts.head, n));

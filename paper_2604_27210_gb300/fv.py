@@ -17,6 +17,7 @@ FV_BLACK76, FV_BLACK_SCHOLES, FV_BSM = 0, 1, 2
 FV_LBR, FV_HALLEY = 0, 1
 FV_FP64, FV_MIXED, FV_FP32 = 0, 1, 2
 FV_DTYPE_F64, FV_DTYPE_F32 = 0, 1
+FV_TRANSFER_AUTO, FV_TRANSFER_STAGED, FV_TRANSFER_DIRECT = 0, 1, 2
 FV_Q_OK, FV_Q_BELOW_INTRINSIC, FV_Q_ABOVE_MAX, FV_Q_INVALID = 0, 1, 2, 3
 FV_SUCCESS, FV_ERR_ARG, FV_ERR_CUDA, FV_ERR_UNSUPPORTED, FV_ERR_NOMEM = 0, -1, -2, -3, -4
 
@@ -27,7 +28,8 @@ EXPORTS = ["fv_price", "fv_implied_vol", "fv_workspace_size", "fv_implied_vol_ws
            "fv_chains_plan_create", "fv_implied_vol_chains", "fv_implied_vol_chains_direct",
            "fv_chains_plan_info", "fv_chains_plan_tuning", "fv_autotune_cache_get",
            "fv_autotune_cache_put", "fv_chains_plan_destroy", "fv_stream_plan_create",
-           "fv_stream_plan_destroy", "fv_implied_vol_host", "fv_implied_vol_halley_noalloc",
+           "fv_stream_plan_destroy", "fv_stream_plan_set_transfer", "fv_stream_plan_last_transfer",
+           "fv_implied_vol_host", "fv_implied_vol_halley_noalloc",
            "fv_status_string", "fv_last_error"]
 
 
@@ -84,6 +86,8 @@ def _load():
     lib.fv_chains_plan_destroy.argtypes = [_P]
     lib.fv_stream_plan_create.argtypes = [_N, ctypes.POINTER(ctypes.c_void_p)]
     lib.fv_stream_plan_destroy.argtypes = [_P]
+    lib.fv_stream_plan_set_transfer.argtypes = [_P, _I]
+    lib.fv_stream_plan_last_transfer.argtypes = [_P, ctypes.POINTER(_I)]
     lib.fv_implied_vol_host.argtypes = [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P,
                                         _P]
     lib.fv_implied_vol_halley_noalloc.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _N, _P, _P, _P]
@@ -416,14 +420,27 @@ def _host_ptr(t, n, dtypes, name, allow_none=False):
 
 
 class fv_stream_plan:
-    """Device staging and two streams for host-resident batches (see
-    fv_implied_vol_host).  Host tensors should be pinned (tensor.pin_memory())
-    for the copies to overlap the solve."""
+    """Host-resident batches (see fv_implied_vol_host).  With pinned host
+    tensors (tensor.pin_memory()) the solver reads and writes them in place
+    over the CPU-GPU link (FV_TRANSFER_DIRECT); otherwise the plan's device
+    staging and two streams copy them in chunks overlapped with the solve
+    (FV_TRANSFER_STAGED).  set_transfer() forces one of the two."""
 
     def __init__(self, chunk_quotes=1 << 21):
         h = ctypes.c_void_p()
         _check(_lib.fv_stream_plan_create(int(chunk_quotes), ctypes.byref(h)), "fv_stream_plan_create")
         self._h = h
+
+    def set_transfer(self, mode):
+        _check(_lib.fv_stream_plan_set_transfer(self._h, int(mode)), "fv_stream_plan_set_transfer")
+
+    @property
+    def last_transfer(self):
+        """The mode the last call took (FV_TRANSFER_AUTO before the first)."""
+        m = _I()
+        _check(_lib.fv_stream_plan_last_transfer(self._h, ctypes.byref(m)),
+               "fv_stream_plan_last_transfer")
+        return m.value
 
     def implied_vol(self, model, solver, precision, price, S_or_F, K, T, r, q, flag, out_sigma=None,
                     status=None, stream=None):

@@ -29,6 +29,10 @@ int main(void) {
                      NULL) != FV_SUCCESS)
     return 4;
   if (fv_workspace_size(FV_LBR, 1000) != 0 || fv_workspace_size(FV_HALLEY, 1000) < 1000) return 5;
+  /* the stream plan's transfer mode: a plan is required */
+  int mode = -1;
+  if (fv_stream_plan_set_transfer(NULL, FV_TRANSFER_DIRECT) != FV_ERR_ARG) return 6;
+  if (fv_stream_plan_last_transfer(NULL, &mode) != FV_ERR_ARG || mode != -1) return 7;
   printf("%s\n", fv_status_string(FV_ERR_UNSUPPORTED));
   return 0;
 }

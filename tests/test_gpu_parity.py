@@ -685,22 +685,54 @@ def test_abi_argument_errors(fv, torch_dev):
 # ---------------------------------------------------------------------------
 # host-resident batches through the stream plan
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("solver,prec", [(0, 0), (0, 1), (1, 0)])
+@pytest.mark.parametrize("solver,prec", [(0, 0), (0, 1), (0, 2), (1, 0)])
 def test_host_streaming_matches_device(fv, torch_dev, solver, prec):
+    # pinned host arrays: the direct mode (the solver reads and writes them in
+    # place over the CPU-GPU link) runs the device call's kernel on the same
+    # quotes, bit for bit; the staged mode (chunks of up to 100,000 quotes,
+    # ramped at both ends, copied on two streams) solves its small chunks with
+    # the unbinned kernel, equal within rounding
     torch, dev = torch_dev
     w = wl.fill_prices(wl.bsm_grid(1000, 300, seed=41), orc.price_f64)
     keys = ("P", "S_or_F", "K", "T", "r", "q", "flag")
     host = {k: torch.tensor(w[k]).pin_memory() for k in keys}
-    plan = fv.fv_stream_plan_create(100000)  # chunks of up to 100,000 quotes, ramped at both ends
-    s_h, st_h = plan.implied_vol(fv.FV_BSM, solver, prec, *[host[k] for k in keys])
-    torch.cuda.synchronize()
     s_d, st_d = fv.fv_implied_vol_ex(fv.FV_BSM, solver, prec, *_args(torch_dev, w),
                                      _dev(torch_dev, w["flag"]))
-    s_h, s_d = s_h.numpy(), _np(s_d)
-    assert np.array_equal(st_h.numpy(), _np(st_d))
-    assert np.array_equal(np.isnan(s_h), np.isnan(s_d))
-    ok = ~np.isnan(s_d) & (s_d > 0)
-    assert np.all(np.abs(s_h[ok] - s_d[ok]) <= 1e-12 * s_d[ok])
+    s_d, st_d = _np(s_d), _np(st_d)
+    plan = fv.fv_stream_plan_create(100000)
+    assert plan.last_transfer == fv.FV_TRANSFER_AUTO
+    for mode, taken in ((fv.FV_TRANSFER_AUTO, fv.FV_TRANSFER_DIRECT),
+                        (fv.FV_TRANSFER_STAGED, fv.FV_TRANSFER_STAGED),
+                        (fv.FV_TRANSFER_DIRECT, fv.FV_TRANSFER_DIRECT)):
+        plan.set_transfer(mode)
+        s_h, st_h = plan.implied_vol(fv.FV_BSM, solver, prec, *[host[k] for k in keys])
+        torch.cuda.synchronize()
+        assert plan.last_transfer == taken
+        s_h, st_h = s_h.numpy(), st_h.numpy()
+        assert np.array_equal(st_h, st_d), mode
+        assert np.array_equal(np.isnan(s_h), np.isnan(s_d)), mode
+        ok = ~np.isnan(s_d) & (s_d > 0)
+        if taken == fv.FV_TRANSFER_DIRECT:
+            assert np.array_equal(s_h[ok], s_d[ok]), mode
+        elif prec != fv.FV_FP32:  # FP32: rounding differs by the conditioning
+            assert np.all(np.abs(s_h[ok] - s_d[ok]) <= 1e-12 * s_d[ok]), mode
+    # pageable arrays: AUTO stages them, DIRECT refuses them before any work
+    pageable = {k: torch.tensor(w[k]) for k in keys}
+    assert not pageable["P"].is_pinned()
+    plan.set_transfer(fv.FV_TRANSFER_DIRECT)
+    with pytest.raises(fv.FvError) as e:
+        plan.implied_vol(fv.FV_BSM, solver, prec, *[pageable[k] for k in keys])
+    assert e.value.code == fv.FV_ERR_ARG
+    plan.set_transfer(fv.FV_TRANSFER_AUTO)
+    s_p, st_p = plan.implied_vol(fv.FV_BSM, solver, prec, *[pageable[k] for k in keys],
+                                 out_sigma=torch.empty(s_d.size, dtype=torch.float64),
+                                 status=torch.empty(s_d.size, dtype=torch.uint8))
+    torch.cuda.synchronize()
+    assert plan.last_transfer == fv.FV_TRANSFER_STAGED
+    assert np.array_equal(st_p.numpy(), st_d)
+    with pytest.raises(fv.FvError) as e:
+        plan.set_transfer(7)
+    assert e.value.code == fv.FV_ERR_ARG
     plan.destroy()
 
 
