@@ -198,14 +198,15 @@ def run_path(fv, t, path, out, st):
 LAUNCHES_PER_STEP = {"lbr": 2, "mixed": 2, "fp32": 1, "halley": 1}
 
 
-def halley_fallback_fraction(fv, torch, t):
+def halley_fallback_fraction(fv, torch, t, model=None):
     """Share of the quotes whose eight Halley sweeps fail the convergence test:
     the workspace arrangement of the same solver leaves the length of its
     compacted fallback list in the first four bytes of the workspace."""
+    model = fv.FV_BSM if model is None else model
     n = t["P"].numel()
     ws = torch.zeros(fv.fv_workspace_size(fv.FV_HALLEY, n), dtype=torch.uint8, device=t["P"].device)
-    fv.fv_implied_vol_ws(fv.FV_BSM, fv.FV_HALLEY, t["P"], t["S_or_F"], t["K"], t["T"], t["r"],
-                         t["q"], t["flag"], ws)
+    fv.fv_implied_vol_ws(model, fv.FV_HALLEY, t["P"], t["S_or_F"], t["K"], t["T"], t["r"],
+                         t.get("q"), t["flag"], ws)
     torch.cuda.synchronize()
     return int(ws[:4].cpu().numpy().view(np.uint32)[0]) / n
 
@@ -238,43 +239,68 @@ def time_steps(torch, fn, steps, warmup, world_size):
     return total_ms, kernel_ms
 
 
-def small_batch_latency(fv, torch, dev, reps=200):
-    """Latency of the FP64 LBR on the 4,096 Black-76 quotes of the small
-    configuration (F = 100, K = F e^k, k ~ U[-1/2, 1/2], T ~ U[0.02, 2],
-    r = 0.03, alternating flags): microseconds per call, and per replay of the
-    call captured in a CUDA graph (launch overhead out).  Inputs priced by the
-    library's own pricing kernel."""
-    w = wl.black76_quotes(4096, seed=0)
+def _per_rep_us(torch, fn, reps):
+    for _ in range(20):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / reps
+
+
+def _black76_batch(fv, torch, dev, n, seed=0):
+    """n Black-76 quotes of the small configuration's distribution (F = 100,
+    K = F e^k, k ~ U[-1/2, 1/2], T ~ U[0.02, 2], r = 0.03, alternating flags),
+    priced by the library's own pricing kernel."""
+    w = wl.black76_quotes(n, seed=seed)
     t = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in ("S_or_F", "K", "T", "r", "flag")}
     sig = torch.from_numpy(w["sigma_true"]).to(dev)
-    P = fv.fv_price(fv.FV_BLACK76, t["flag"], t["S_or_F"], t["K"], t["T"], t["r"], None, sig)
+    t["P"] = fv.fv_price(fv.FV_BLACK76, t["flag"], t["S_or_F"], t["K"], t["T"], t["r"], None, sig)
+    return t
+
+
+def small_batch_latency(fv, torch, dev, reps=200):
+    """Latency of the FP64 LBR on the 4,096 Black-76 quotes of the small
+    configuration: microseconds per call, and per replay of the call captured
+    in a CUDA graph (launch overhead out)."""
+    t = _black76_batch(fv, torch, dev, 4096)
     out = torch.empty(4096, dtype=torch.float64, device=dev)
     st = torch.empty(4096, dtype=torch.uint8, device=dev)
-    call = lambda: fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR, P, t["S_or_F"], t["K"], t["T"], t["r"],
-                                     None, t["flag"], out, st)
-
-    def per_rep_us(fn):
-        for _ in range(20):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return 1e3 * e0.elapsed_time(e1) / reps
-
-    call_us = per_rep_us(call)
+    call = lambda: fv.fv_implied_vol(fv.FV_BLACK76, fv.FV_LBR, t["P"], t["S_or_F"], t["K"], t["T"],
+                                     t["r"], None, t["flag"], out, st)
+    call_us = _per_rep_us(torch, call, reps)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.graph(g, stream=side):
         call()
     torch.cuda.current_stream().wait_stream(side)
-    graph_us = per_rep_us(g.replay)
+    graph_us = _per_rep_us(torch, g.replay, reps)
     return {"quotes": 4096, "workload": "Black-76 4,096 quotes", "call_us": call_us, "graph_us": graph_us,
             "path": "lbr"}
+
+
+def paper_batch_latency(fv, torch, dev, n=100000, reps=100):
+    """The paper's benchmark batch size (Table 3: N = 10^5 quotes, CUDA events):
+    microseconds per call of every solver on n Black-76 quotes of the small
+    configuration's distribution (inputs 4.1 MB, L2-resident across the
+    back-to-back calls), and the Halley sweeps' hand-off share there."""
+    t = _black76_batch(fv, torch, dev, n, seed=5)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    res = {"quotes": n, "workload": "Black-76 %d quotes, the small configuration's distribution" % n}
+    for name, solver, prec in (("lbr", fv.FV_LBR, fv.FV_FP64), ("mixed", fv.FV_LBR, fv.FV_MIXED),
+                               ("fp32", fv.FV_LBR, fv.FV_FP32), ("halley", fv.FV_HALLEY, fv.FV_FP64),
+                               ("halley32", fv.FV_HALLEY, fv.FV_FP32)):
+        call = lambda: fv.fv_implied_vol_ex(fv.FV_BLACK76, solver, prec, t["P"], t["S_or_F"], t["K"],
+                                            t["T"], t["r"], None, t["flag"], out, st)
+        res[name + "_us"] = _per_rep_us(torch, call, reps)
+    res["halley_fallback_fraction"] = halley_fallback_fraction(fv, torch, t, fv.FV_BLACK76)
+    return res
 
 
 E2E_CHUNK = 1 << 20
@@ -556,6 +582,7 @@ def main():
                          "hbm_frac": BYTES_PER_QUOTE * n / (statistics.mean(km) * 1e-3) / 1e9 / hbm_peak}
         extras.setdefault("halley", {})["fallback_fraction"] = halley_fallback_fraction(fv, torch, t)
         extras["small_batch"] = small_batch_latency(fv, torch, dev)
+        extras["paper_batch"] = paper_batch_latency(fv, torch, dev)
         # pricing and Greeks on the same grid
         sig = t["P"].new_tensor(w["sigma_true"])
         for name, fn in (("price", lambda: fv.fv_price(fv.FV_BSM, t["flag"], t["S_or_F"], t["K"],

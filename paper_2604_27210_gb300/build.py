@@ -15,9 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfv.so")
-SOURCES = ["fv_kernels.cu", "fv_chains.cu", "fv_abi.cu", "fv_noalloc.cu"]
+SOURCES = ["fv_kernels.cu", "fv_kernels_mid.cu", "fv_chains.cu", "fv_abi.cu", "fv_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, f) for f in ("fv_device.cuh", "fv_binned.cuh", "fv_internal.h",
-                                          "fv_fp64_tables.h", "fv_df32.cuh", "fv_df32_tables.h")] + [
+                                          "fv_fp64_tables.h", "fv_df32.cuh", "fv_df32_tables.h", "fv_tiles.cuh")] + [
     os.path.join(ROOT, "include", "fv.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

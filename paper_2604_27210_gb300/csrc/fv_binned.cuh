@@ -26,10 +26,11 @@ using namespace fvd;
 // ---------------------------------------------------------------------------
 constexpr int kBinKeys = 8;  // 4 regions x {small t, not}
 
-template <int THREADS, int Q>
+template <int THREADS, int Q, bool INLINE = false>
 struct BinSmem {
   static constexpr int N = THREADS * Q;
   double beta[N], x[N], bmax[N], lnb[N], T[N];
+  double cbeta[INLINE ? N : 1];  // the refined c_beta (tiles that refine in place)
   float s32[N];
   unsigned char reg[N];
   unsigned short perm[N];  // the sorted order of the solving quotes
@@ -41,10 +42,14 @@ struct BinSmem {
 // quote's sigma / status.  LATE32: the mixed path's FP32 iterations run in
 // phase 2 (phase 1 only evaluates the FP32 guess that gives the sort key).
 // An ill-conditioned quote (needs_refine) is not solved here: its status is
-// written with kRefineMark and the refinement kernel solves it.
-template <int PREC, int THREADS, int Q, bool LATE32, typename Load>
-__device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int model, const Load& load,
-                                                double* sigma, uint8_t* status, int64_t out0) {
+// written with kRefineMark and the refinement kernel solves it.  INLINE
+// (medium batches, one launch): phase 1 refines its reduced price in place
+// and the quote is binned and solved with the others, the arithmetic of the
+// refinement kernel.
+template <int PREC, int THREADS, int Q, bool LATE32, bool INLINE = false, typename Load>
+__device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q, INLINE>& sm, int model,
+                                                const Load& load, double* sigma, uint8_t* status,
+                                                int64_t out0) {
   const int tid = threadIdx.x;
   if (tid < kBinKeys) sm.cnt[tid] = 0;
   __syncthreads();
@@ -58,11 +63,14 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     double P, SF, K, T, r, q;
     int flag;
     if (load(li, P, SF, K, T, r, q, flag)) {
-      const Norm nq = decide(model, P, SF, K, T, r, q, flag);
-      const bool refine = needs_refine(nq);
+      Norm nq = decide(model, P, SF, K, T, r, q, flag);
+      const bool refine = needs_refine(nq) && !INLINE;  // left to the refinement kernel
+      if (INLINE && needs_refine(nq))
+        refine_reduced(model, P, SF, K, T, r, q, flag, positive64(nq.iota), nq.beta_otm, nq.c_beta);
       status[out0 + li] = (uint8_t)nq.status | (refine ? kRefineMark : 0);
       if (nq.status == Q_OK && nq.solve && !refine) {
         const Reduced<double> q64 = reduced64(nq);
+        if constexpr (INLINE) sm.cbeta[li] = q64.c_beta;
         sm.beta[li] = q64.beta;
         sm.x[li] = q64.x;
         sm.bmax[li] = q64.bmax;
@@ -109,7 +117,10 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
     q.beta = sm.beta[li];
     q.x = sm.x[li];
     q.bmax = sm.bmax[li];
-    q.c_beta = q.bmax - q.beta;
+    if constexpr (INLINE)
+      q.c_beta = sm.cbeta[li];
+    else
+      q.c_beta = q.bmax - q.beta;  // as decide computes it
     q.ln_beta = sm.lnb[li];
     q.inv_ln_beta = 0.0;
     q.ln_c_beta = 0.0;
@@ -150,7 +161,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q>& sm, int mod
 // FP32 iterations, then (mixed) the double-float correction.  The FP32 path
 // marks nothing for the refinement pass (its 1e-5 does not need it).
 // ---------------------------------------------------------------------------
-template <int THREADS, int Q>
+template <int THREADS, int Q, bool INLINE = false>
 struct BinSmemMixed {
   static constexpr int N = THREADS * Q;
   fvdf::df beta[N], x[N], bmax[N], cbeta[N], lnb[N];
@@ -159,8 +170,9 @@ struct BinSmemMixed {
   unsigned char reg[N];
   unsigned char state[N];  // 0: no root to solve here, 1: solve, 2: solve from ln beta
   unsigned short perm[N], list[N];
+  unsigned short rlist[INLINE ? N : 1];  // ill-conditioned quotes refined in place
   int cnt[kBinKeys], off[kBinKeys + 1];
-  int nlist;
+  int nlist, nref;
 };
 
 __device__ __forceinline__ Reduced<float> reduced32_df(const fvdf::df& beta, const fvdf::df& cbeta,
@@ -185,14 +197,20 @@ static __device__ __noinline__ double mixed_solve_fp64(Reduced<double> q64, doub
   return lbr_solve_quote<P_MIXED>(q64) * rsqrt(T);
 }
 
-template <int PREC, int THREADS, int Q, typename Load>
-__device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q>& sm, int model,
+// INLINE (medium batches, one launch): the mixed path's ill-conditioned
+// quotes are not marked for the refinement kernel but listed, and phase 2
+// solves them first, with the refinement kernel's arithmetic.
+template <int PREC, int THREADS, int Q, bool INLINE = false, typename Load>
+__device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q, INLINE>& sm, int model,
                                                       const Load& load, double* sigma,
                                                       uint8_t* status, int64_t out0) {
   using fvdf::df;
   const int tid = threadIdx.x;
   if (tid < kBinKeys) sm.cnt[tid] = 0;
-  if (tid == 0) sm.nlist = 0;
+  if (tid == 0) {
+    sm.nlist = 0;
+    sm.nref = 0;
+  }
   __syncthreads();
   // pass A: the double-float status rule
 #pragma unroll 1
@@ -209,6 +227,10 @@ __device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q>& sm,
     }
     // ill-conditioned (mixed path) where b_max - beta < b_max/64
     const bool refine = PREC == P_MIXED && d.solve && d.c_beta.h < 0.015625f * d.bmax.h;
+    if (INLINE && refine) {
+      sm.rlist[atomicAdd(&sm.nref, 1)] = (unsigned short)li;
+      continue;
+    }
     status[out0 + li] = (uint8_t)d.status | (refine ? kRefineMark : 0);
     if (d.solve && !refine) {
       sm.beta[li] = d.beta;
@@ -232,6 +254,10 @@ __device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q>& sm,
     load(li, P, SF, K, T, r, q, flag);
     const Norm nq = decide(model, P, SF, K, T, r, q, flag);
     const bool refine = PREC == P_MIXED && needs_refine(nq);
+    if (INLINE && refine) {
+      sm.rlist[atomicAdd(&sm.nref, 1)] = (unsigned short)li;
+      continue;
+    }
     status[out0 + li] = (uint8_t)nq.status | (refine ? kRefineMark : 0);
     if (nq.status == Q_OK && nq.solve && !refine) {
       const Reduced<double> q64 = reduced64(nq);
@@ -301,10 +327,23 @@ __device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q>& sm,
   for (int k = 0; k < Q; k++)
     if (key[k] != 0xff) sm.perm[sm.off[key[k]] + rank[k]] = (unsigned short)(k * THREADS + tid);
   __syncthreads();
-  // phase 2: the FP32 iterations and (mixed) the double-float correction
-  const int ns = sm.off[kBinKeys];
+  // phase 2: the FP32 iterations and (mixed) the double-float correction;
+  // INLINE: the listed ill-conditioned quotes first, in FP64
+  const int nr = INLINE ? sm.nref : 0;
+  const int ns = sm.off[kBinKeys] + nr;
   for (int j = tid; j < ns; j += THREADS) {
-    const int li = sm.perm[j];
+    if (INLINE && j < nr) {
+      const int li = sm.rlist[j];
+      double P, SF, K, T, r, q;
+      int flag;
+      load(li, P, SF, K, T, r, q, flag);
+      Norm nq = decide(model, P, SF, K, T, r, q, flag);
+      refine_reduced(model, P, SF, K, T, r, q, flag, positive64(nq.iota), nq.beta_otm, nq.c_beta);
+      sigma[out0 + li] = mixed_solve_fp64(reduced64(nq), T);
+      status[out0 + li] = (uint8_t)nq.status;
+      continue;
+    }
+    const int li = sm.perm[j - nr];
     const bool tiny = sm.state[li] == 2;
     const df beta = sm.beta[li], x = sm.x[li], bmax = sm.bmax[li], cbeta = sm.cbeta[li],
              lnb = sm.lnb[li];

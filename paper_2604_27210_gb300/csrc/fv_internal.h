@@ -35,6 +35,11 @@ int grid_for(int64_t n, int block, int per_sm);
 // (zeroed on `st` before the launch), then the refinement kernel over the
 // quotes it marked; smaller ones one unbinned kernel
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
+// Medium batches, kMidBatch[prec] <= n < 2^17 quotes: one launch of 128-quote
+// region-binned tiles, one per block, that refine their ill-conditioned
+// quotes themselves (launch_iv_lbr dispatches here)
+constexpr int64_t kMidBatch[3] = {98304, 65536, 65536};  // FP64, mixed, FP32
+cudaError_t launch_iv_lbr_mid(const IvArgs& a, int prec, cudaStream_t st);
 
 // Halley x8 with the fallback and the double-double refinement of
 // ill-conditioned quotes inside the same kernel (tile-local compaction in

@@ -11,6 +11,7 @@
 #include "fv_binned.cuh"
 #include "fv_device.cuh"
 #include "fv_internal.h"
+#include "fv_tiles.cuh"
 
 namespace fvk {
 
@@ -58,12 +59,6 @@ int persistent_grid(int64_t units, int units_per_block, int block) {
   return grid_for(units, units_per_block, resident[dev]);
 }
 
-// Below kSmallBatch quotes a launch is latency-bound (each warp runs one long
-// chain of dependent FP64 instructions): 64-thread blocks spread the quotes
-// over as many SMs and sub-partitions as possible, and the LBR solvers skip
-// the binning.
-constexpr int64_t kSmallBatch = 1 << 17;
-
 // Launch of a one-quote-per-thread grid-stride kernel over n quotes: a small
 // batch takes 64-thread blocks, one per 64 quotes, so that it reaches as many
 // SMs as it can fill; a large one a single resident wave of 256-thread blocks.
@@ -73,91 +68,6 @@ void launch_shaped(int64_t n, cudaStream_t st, Args... args) {
     Kernel<<<grid_for(n, 64, 32), 64, 0, st>>>(args...);
   else
     Kernel<<<persistent_grid<Kernel>(n, 256, 256), 256, 0, st>>>(args...);
-}
-
-template <typename InT>
-__device__ __forceinline__ double ld(const void* p, int64_t i) {
-  return (double)__ldg(static_cast<const InT*>(p) + i);
-}
-
-// quote i of an IV call (strided / broadcast inputs)
-template <typename InT>
-__device__ __forceinline__ void load_quote(const IvArgs& a, int64_t i, double& P, double& SF,
-                                           double& K, double& T, double& r, double& q, int& flag) {
-  P = ld<InT>(a.P, i * a.st[0]);
-  SF = ld<InT>(a.SF, i * a.st[1]);
-  K = ld<InT>(a.K, i * a.st[2]);
-  T = ld<InT>(a.T, i * a.st[3]);
-  r = ld<InT>(a.r, i * a.st[4]);
-  q = (a.model == M_BSM) ? ld<InT>(a.q, i * a.st[5]) : 0.0;
-  flag = a.flag[i * a.st[6]];
-}
-
-// ---------------------------------------------------------------------------
-// Tile scheduling of the persistent tiled kernels
-//
-// Static (ctr == nullptr): block b solves tile b, one tile per block (small
-// batches, where the grid covers the batch).  Dynamic: one resident wave of
-// blocks claims tiles from an atomic counter, so that the blocks that drew
-// cheap tiles take more of them and every SM finishes at about the same time
-// (a static round-robin leaves the SMs' totals a few per cent apart).  The
-// two 64-bit counters -- the next tile, and the blocks that have finished --
-// live in the first two outputs sigma[0], sigma[1] (8-byte aligned doubles),
-// which the launcher zeroes on the stream before the launch.  Tiles cover
-// quotes [kHead, n); the head quotes [0, kHead), among them sigma[0..1], are
-// solved by the last block to finish, after every other block has stopped
-// using the counters, so the counters cost no memory of their own.  A caller
-// whose outputs are host memory read over the CPU-GPU link passes device
-// counters of its own instead (IvArgs::ctr); the tiles then cover [0, n).
-// No block ever waits for another.
-// ---------------------------------------------------------------------------
-constexpr int64_t kHead = 32;
-
-struct TileSched {
-  unsigned long long* ctr;  // nullptr: static
-  int64_t n_tiles;          // tiles after the head
-  int64_t head;             // kHead (counters in sigma) or 0 (static, or own counters)
-};
-
-static TileSched make_sched(const IvArgs& a, int tile, bool dynamic) {
-  TileSched t;
-  t.ctr = !dynamic ? nullptr : a.ctr ? a.ctr : reinterpret_cast<unsigned long long*>(a.sigma);
-  t.head = dynamic && a.ctr == nullptr ? kHead : 0;
-  t.n_tiles = (a.n - t.head + tile - 1) / tile;
-  return t;
-}
-
-// Runs body(first quote, quotes in the tile) for every tile this block takes.
-// Every thread of the block calls it; body may use __syncthreads().
-template <typename Body>
-__device__ __forceinline__ void for_each_tile(const TileSched& ts, int tile, int64_t n,
-                                              const Body& body) {
-  __shared__ unsigned long long s_tile;
-  __shared__ int s_last;
-  if (ts.ctr == nullptr) {
-    const int64_t base = (int64_t)blockIdx.x * tile;
-    if (base < n) body(base, (int)min((int64_t)tile, n - base));
-    return;
-  }
-  for (;;) {
-    __syncthreads();  // the previous tile's readers of s_tile are done
-    if (threadIdx.x == 0) s_tile = atomicAdd(ts.ctr, 1ULL);
-    __syncthreads();
-    const int64_t t = (int64_t)s_tile;
-    if (t >= ts.n_tiles) break;
-    const int64_t base = ts.head + t * tile;
-    body(base, (int)min((int64_t)tile, n - base));
-  }
-  if (ts.head == 0) return;  // own counters: no head to solve (uniform over the block)
-  if (threadIdx.x == 0) s_last = atomicAdd(ts.ctr + 1, 1ULL) == (unsigned long long)gridDim.x - 1;
-  __syncthreads();
-  if (s_last) body(0, (int)min(ts.head, n));
-}
-
-// zero the counters of a dynamic schedule on the launch stream
-static cudaError_t reset_sched(const TileSched& ts, cudaStream_t st) {
-  if (ts.ctr == nullptr) return cudaSuccess;
-  return cudaMemsetAsync(ts.ctr, 0, 2 * sizeof(unsigned long long), st);
 }
 
 // ---------------------------------------------------------------------------
@@ -208,7 +118,6 @@ __global__ void __launch_bounds__(256) k_iv_lbr(IvArgs a) {
   }
 }
 
-constexpr int kBinThreads = 256;
 
 // ---------------------------------------------------------------------------
 // The refinement kernel: the ill-conditioned quotes a large-batch LBR kernel
@@ -270,38 +179,21 @@ static cudaError_t launch_refine(const IvArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename InT, int PREC, int Q, int MINB, bool LATE32>
-__global__ void __launch_bounds__(kBinThreads, MINB) k_iv_lbr_binned(IvArgs a, TileSched ts) {
-  using Smem = typename std::conditional<PREC != P_FP64, BinSmemMixed<kBinThreads, Q>,
-                                         BinSmem<kBinThreads, Q>>::type;
-  __shared__ Smem sm;
-  for_each_tile(ts, kBinThreads * Q, a.n, [&](int64_t base, int count) {
-    auto load = [&](int li, double& P, double& SF, double& K, double& T, double& r, double& q,
-                    int& flag) {
-      if (li >= count) return false;
-      load_quote<InT>(a, base + li, P, SF, K, T, r, q, flag);
-      return true;
-    };
-    if constexpr (PREC != P_FP64)
-      lbr_binned_tile_df<PREC, kBinThreads, Q>(sm, a.model, load, a.sigma, a.status, base);
-    else
-      lbr_binned_tile<PREC, kBinThreads, Q, LATE32>(sm, a.model, load, a.sigma, a.status, base);
-  });
-}
-
-// binned batches are large (>= kSmallBatch quotes): dynamic tiles over one
-// resident wave
-template <typename InT, int PREC, int Q, int MINB, bool LATE32>
+// large batches (>= kSmallBatch quotes): dynamic tiles over one resident wave,
+// then the refinement kernel; medium ones (INLINE): one tile per block, every
+// tile resident at once, the ill-conditioned quotes refined in the tile
+template <typename InT, int PREC, int THREADS, int Q, int MINB, bool LATE32, bool INLINE = false>
 static cudaError_t launch_binned(const IvArgs& a, cudaStream_t st) {
-  constexpr auto kernel = k_iv_lbr_binned<InT, PREC, Q, MINB, LATE32>;
-  const TileSched ts = make_sched(a, kBinThreads * Q, true);
+  constexpr auto kernel = k_iv_lbr_binned<InT, PREC, THREADS, Q, MINB, LATE32, INLINE>;
+  const bool dynamic = a.n >= kSmallBatch;
+  const TileSched ts = make_sched(a, THREADS * Q, dynamic);
   const cudaError_t e = reset_sched(ts, st);
   if (e != cudaSuccess) return e;
-  const int grid = persistent_grid<kernel>(a.n, kBinThreads * Q, kBinThreads);
-  kernel<<<grid, kBinThreads, 0, st>>>(a, ts);
+  const int grid = dynamic ? persistent_grid<kernel>(a.n, THREADS * Q, THREADS) : (int)ts.n_tiles;
+  kernel<<<grid, THREADS, 0, st>>>(a, ts);
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess) return le;
-  if constexpr (PREC == P_FP32)
+  if constexpr (PREC == P_FP32 || INLINE)
     return cudaSuccess;  // nothing marked for refinement
   else
     return launch_refine<InT, PREC>(a, st);
@@ -332,6 +224,7 @@ static void launch_flat(const IvArgs& a, int prec, int block, cudaStream_t st) {
 }
 
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
+  if (a.n >= kMidBatch[prec] && a.n < kSmallBatch) return launch_iv_lbr_mid(a, prec, st);
   if (a.n < kSmallBatch) {
     const int block = a.n < kSmallBatch ? 64 : 256;
     if (a.f32_inputs)
@@ -341,12 +234,12 @@ cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st) {
     return cudaGetLastError();
   }
   if (a.f32_inputs)
-    return prec == P_FP64    ? launch_binned<float, P_FP64, 2, 4, false>(a, st)
-           : prec == P_MIXED ? launch_binned<float, P_MIXED, 2, 4, true>(a, st)
-                             : launch_binned<float, P_FP32, 2, 4, true>(a, st);
-  return prec == P_FP64    ? launch_binned<double, P_FP64, 2, 4, false>(a, st)
-         : prec == P_MIXED ? launch_binned<double, P_MIXED, 2, 4, true>(a, st)
-                           : launch_binned<double, P_FP32, 2, 4, true>(a, st);
+    return prec == P_FP64    ? launch_binned<float, P_FP64, kBinThreads, 2, 4, false>(a, st)
+           : prec == P_MIXED ? launch_binned<float, P_MIXED, kBinThreads, 2, 4, true>(a, st)
+                             : launch_binned<float, P_FP32, kBinThreads, 2, 4, true>(a, st);
+  return prec == P_FP64    ? launch_binned<double, P_FP64, kBinThreads, 2, 4, false>(a, st)
+         : prec == P_MIXED ? launch_binned<double, P_MIXED, kBinThreads, 2, 4, true>(a, st)
+                           : launch_binned<double, P_FP32, kBinThreads, 2, 4, true>(a, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -825,6 +825,55 @@ def test_binned_matches_unbinned_and_oracle(fv, torch_dev, prec):
     _sampled_parity(fv, torch_dev, w, s_big, st_big, fv.FV_BSM, n_sample=4096, seed=3)
 
 
+# medium batches (from 98,304 quotes in FP64, 65,536 in mixed and FP32, up to
+# 2^17): 128-quote binned tiles, one per block, refining their ill-conditioned
+# quotes in the tile instead of a second kernel
+MID_SIZES = {"fp64": (98304, 100000, 131071), "mixed": (65536, 100000, 131071),
+             "fp32": (65536, 100000, 131071)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("workload", ["black76", "grid"])
+def test_medium_batches_match_large_and_oracle(fv, torch_dev, prec, workload):
+    # the first m quotes of a 2^18-quote call, solved alone by the medium-batch
+    # kernel: the same per-quote arithmetic as the large-batch kernel and its
+    # refinement pass, so equal within rounding; then against the definition.
+    # The Black-76 quotes alternate flags: half are in the money, and a few
+    # per cent of those need the double-double reduced price
+    n = 1 << 18
+    if workload == "black76":
+        w = wl.fill_prices(wl.black76_quotes(n, seed=23), orc.price_f64)
+        model = fv.FV_BLACK76
+        _, x, beta, _ = orc.status(model, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None,
+                                   w["flag"])
+        iota = np.maximum(w["flag"] * (np.exp(x / 2) - np.exp(-x / 2)), 0.0)
+        assert ((iota > 0) & (beta - iota < beta / 64)).sum() > 100  # the in-tile refinement runs
+    else:
+        w = wl.fill_prices(wl.bsm_grid(4096, 64, seed=22), orc.price_f64)
+        model = fv.FV_BSM
+    args = _args(torch_dev, w)
+    flag = _dev(torch_dev, w["flag"])
+    p = {"fp64": fv.FV_FP64, "mixed": fv.FV_MIXED, "fp32": fv.FV_FP32}[prec]
+    s_big, st_big = fv.fv_implied_vol_ex(model, fv.FV_LBR, p, *args, flag)
+    s_big, st_big = _np(s_big), _np(st_big)
+    for m in MID_SIZES[prec]:
+        s_m, st_m = fv.fv_implied_vol_ex(model, fv.FV_LBR, p, *[None if a is None else a[:m]
+                                                                 for a in args], flag[:m])
+        s_m, st_m = _np(s_m), _np(st_m)
+        assert np.array_equal(st_big[:m], st_m), m
+        a, b = s_big[:m], s_m
+        assert np.array_equal(np.isnan(a), np.isnan(b)), m
+        ok = ~np.isnan(b) & (b > 0)
+        if prec == "fp32":  # the same double-float tile: rounding aside, equal
+            assert np.mean(a[ok] == b[ok]) > 0.999, m
+        else:
+            assert np.all(np.abs(a[ok] - b[ok]) <= 1e-12 * b[ok]), m
+    sub = {k: (None if w.get(k) is None else np.asarray(w[k])[:m]) for k in
+           ("P", "S_or_F", "K", "T", "r", "q", "flag")}
+    _sampled_parity(fv, torch_dev, sub, s_m, st_m, model, n_sample=8192, seed=4,
+                    tol_gate=1e-5 if prec == "fp32" else 1e-12)
+
+
 # ---------------------------------------------------------------------------
 # full reference sizes, in the launch configuration the benchmark times
 # ---------------------------------------------------------------------------
