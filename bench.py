@@ -199,9 +199,12 @@ LAUNCHES_PER_STEP = {"lbr": 2, "mixed": 2, "fp32": 1, "halley": 1}
 
 
 def halley_fallback_fraction(fv, torch, t, model=None):
-    """Share of the quotes whose eight Halley sweeps fail the convergence test:
-    the workspace arrangement of the same solver leaves the length of its
-    compacted fallback list in the first four bytes of the workspace."""
+    """Share of the quotes the Halley sweeps hand to the fallback: those that
+    fail the convergence test after the eighth sweep, and those the cubic-reach
+    test sends on earlier (too far from the root at sweep k to reach the
+    tolerance by the eighth).  The workspace arrangement of the same solver
+    leaves the length of its compacted fallback list in the first four bytes
+    of the workspace."""
     model = fv.FV_BSM if model is None else model
     n = t["P"].numel()
     ws = torch.zeros(fv.fv_workspace_size(fv.FV_HALLEY, n), dtype=torch.uint8, device=t["P"].device)

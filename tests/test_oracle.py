@@ -478,6 +478,25 @@ def test_halley_with_bisection_fallback(grid_truth):
     assert fb[atm].mean() < 0.05
 
 
+def test_halley_sweeps_failure_share():
+    # How often the method itself needs the fallback (Section 2.2: "typically
+    # < 0.5 %" on the paper's grid and tolerance): the oracle's eight plain
+    # sweeps from the Brenner-Subrahmanyam start, no early exit, tested at a
+    # relative Newton distance of 1e-10.  Near the money they converge; on
+    # Black-76 quotes of the small configuration's distribution (short
+    # maturities, |ln K/F| up to 1/2) about three in ten do not, and on a slice
+    # of the benchmark grid (log-moneyness to +-3) most do not.
+    w = wl.fill_prices(wl.black76_quotes(100000, seed=5), orc.price_f64)
+    _, st, fb = orc.iv_halley(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
+    share = fb[st == orc.OK].astype(bool).mean()
+    assert 0.2 < share < 0.4, share
+    near = (st == orc.OK) & (np.abs(np.log(w["K"] / w["S_or_F"])) < 0.05) & (w["T"] > 0.25)
+    assert fb[near].astype(bool).mean() < 0.01
+    g = wl.fill_prices(wl.bsm_grid(4096, 64, seed=1), orc.price_f64)
+    _, st, fb = orc.iv_halley(2, g["P"], g["S_or_F"], g["K"], g["T"], g["r"], g["q"], g["flag"])
+    assert 0.6 < fb[st == orc.OK].astype(bool).mean() < 0.85
+
+
 def test_solvers_on_in_the_money_quotes():
     w = wl.fill_prices(wl.black76_quotes(1024, seed=21), orc.price)
     sig, st = orc.iv(0, w["P"], w["S_or_F"], w["K"], w["T"], w["r"], None, w["flag"])
