@@ -24,7 +24,19 @@ using namespace fvd;
 // the same normalised-Black branch, and non-solving quotes do not occupy lanes.
 // The arithmetic of every quote is that of the unbinned solver.
 // ---------------------------------------------------------------------------
-constexpr int kBinKeys = 8;  // 4 regions x {small t, not}
+constexpr int kBinKeys = 8;  // room for 4 regions x {small t, not}; bin_key uses 6
+
+// The sort key of a solving quote: which code its FP64 work runs.  The two
+// middle regions share the objective (b - beta) and the normalised-Black
+// call, so they share keys; the small-t series and the erfcx form are
+// different code, and so are the two wing objectives.  Keys run lowest
+// (erfcx, series), middle (series, erfcx), highest (erfcx, series): the
+// neighbouring bins of a tile share the normalised-Black branch where they
+// can, so the warps that straddle two bins diverge less.
+__device__ __forceinline__ unsigned char bin_key(int reg, bool series) {
+  const int cls = reg == 0 ? 0 : (reg == 3 ? 2 : 1);
+  return (unsigned char)(cls * 2 + ((cls == 1) ? !series : series));
+}
 
 template <int THREADS, int Q, bool INLINE = false>
 struct BinSmem {
@@ -89,7 +101,7 @@ __device__ __forceinline__ void lbr_binned_tile(BinSmem<THREADS, Q, INLINE>& sm,
         // small-t class: the FP64 objective of this region takes the series
         const bool series = 0.5f * sg < (float)fvd::Prec<double>::t_small &&
                             (reg != 0 || series_in_log_space<float>(q32.x, sg));
-        key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
+        key[k] = bin_key(reg, series);
         rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
       } else if (!refine) {
         sigma[out0 + li] = nq.status == Q_OK ? 0.0 : qnan();
@@ -309,7 +321,7 @@ __device__ __forceinline__ void lbr_binned_tile_df(BinSmemMixed<THREADS, Q, INLI
       sm.reg[li] = (unsigned char)reg;
       const bool series = 0.5f * sg < (float)fvd::Prec<double>::t_small &&
                           (reg != 0 || series_in_log_space<float>(q32.x, sg));
-      key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
+      key[k] = bin_key(reg, series);
       rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
     }
   }

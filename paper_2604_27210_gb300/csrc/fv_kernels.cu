@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(THREADS, 2048 / THREADS / 2) k_iv_halley_tiled
         const float gf = f32_trunc(g);
         const bool series = 0.5f * gf < (float)fvd::Prec<double>::t_small &&
                             (reg != 0 || series_in_log_space<float>(f32_trunc(sm.x[li]), gf));
-        key[k] = (unsigned char)(reg * 2 + (series ? 1 : 0));
+        key[k] = bin_key(reg, series);
         rank[k] = (unsigned short)atomicAdd(&sm.cnt[key[k]], 1);
       }
     }
