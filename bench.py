@@ -48,15 +48,21 @@ ALG_FLOPS_PER_QUOTE = {"lbr": 370.4, "mixed": 237.4, "fp32": 85.7}
 # the solver, plus 4.2 per quote in the refinement pass over the quotes it
 # marked; profiles/iv_lbr_bsm_grid_4m.md, profiles/kernels_counters_4m.md),
 # shown beside the algorithmic figure.
-EXECUTED_FLOPS_PER_QUOTE = {"lbr": 307.2 + 4.2, "mixed": 228.2 + 4.2, "fp32": 121.0}
+EXECUTED_FLOPS_PER_QUOTE = {"lbr": 307.2 + 4.2}
+# The mixed and FP32 solvers run their status rule, reduction and correction in
+# double-float arithmetic on the FP32 pipe (1.6 FP64 flops per quote remain):
+# their roofline is the FP32 pipe, with the FP32 flops (FADD + FMUL + 2 x FFMA)
+# the same captures count per quote, against the measured FFMA rate.
+EXECUTED_FP32_FLOPS_PER_QUOTE = {"mixed": 1940.3, "fp32": 1298.0}
+FP32_PEAK_GFLOPS = 2 * 37459.7  # 37.46 T FFMA/s, bench_fp64_probe.py
 # DRAM bytes (read + write) per quote of the step's kernels from one ncu
 # capture each (dram__bytes_read.sum + dram__bytes_write.sum) on 4,194,304
 # quotes of the grid (profiles/iv_lbr_bsm_grid_4m.md): the solver, then the
 # refinement pass (13.70 MB: the status bytes and the marked quotes' inputs;
 # the same scan and the same marked quotes in both precisions).  Traffic grows
 # in proportion to the quotes, so a step's traffic is this x n.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205.79e6 + 24.73e6 + 13.70e6) / 4194304,
-                            "mixed": (206.29e6 + 24.51e6 + 13.70e6) / 4194304}
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205.85e6 + 24.64e6 + 13.70e6) / 4194304,
+                            "mixed": (206.30e6 + 26.67e6 + 13.70e6) / 4194304}
 # FP64 peaks: measured on this machine's GB300 by bench_fp64_probe.py (526 G
 # DFMA/s = 1,052 GFLOP/s; profiles/fp64_fp32_throughput_probe.md), and the
 # unit-count figure 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2070 MHz
@@ -555,7 +561,19 @@ def main():
     hbm_peak, hbm_kind = peaks()
     gbs = BYTES_PER_QUOTE * n / (k_ms * 1e-3) / 1e9
     flops_q = ALG_FLOPS_PER_QUOTE.get(args.path)
-    if flops_q is not None:
+    if args.path in EXECUTED_FP32_FLOPS_PER_QUOTE:
+        f32_q = EXECUTED_FP32_FLOPS_PER_QUOTE[args.path]
+        achieved = f32_q * n / (k_ms * 1e-3) / 1e9
+        dram_q = DRAM_BYTES_PER_QUOTE_NCU.get(args.path)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_GFLOPS,
+                    "unit": "GFLOP/s (FP32)", "frac": achieved / FP32_PEAK_GFLOPS,
+                    "traffic": dram_q * n if dram_q is not None else None,
+                    "flops_per_quote": f32_q,
+                    "flops_kind": "executed: FP32 flops per quote of the solver (ncu); the kernel is "
+                                  "bound by instruction issue, not by the FP32 pipe",
+                    "fp64_method_flops_per_quote": flops_q,
+                    "peak_kind": "measured FP32 FMA rate on this GPU (bench_fp64_probe.py)"}
+    elif flops_q is not None:
         achieved = flops_q * n / (k_ms * 1e-3) / 1e9
         dram_q = DRAM_BYTES_PER_QUOTE_NCU.get(args.path)
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
