@@ -376,9 +376,11 @@ def test_strided_broadcast_matches_arrays(fv, torch_dev):
     assert lib.fv_implied_vol_strided(2, 0, 0, 0, p, p, p, p, p, p, p, st, n, p, p, None) == fv.FV_ERR_ARG
 
 
-def test_iv_fp32_inputs(fv, torch_dev):
-    # FP32 inputs; the oracle inverts the same values widened to FP64
-    w = wl.black76_fp32(8192, seed=2)
+@pytest.mark.parametrize("n", [8192, 100000])
+def test_iv_fp32_inputs(fv, torch_dev, n):
+    # FP32 inputs; the oracle inverts the same values widened to FP64 (100,000
+    # quotes: the medium-batch tiles of every precision)
+    w = wl.black76_fp32(n, seed=2)
     wl.fill_prices(w, orc.price, price_dtype=np.float32)
     ref, st_ref, v, kap = _iv_ref(w)
     torch, dev = torch_dev
