@@ -26,6 +26,7 @@ namespace plain {
 #define R double
 #include "lbr_steps.h"
 #undef R
+#undef LBR_STEPS_PHASE  // the header's empty default hook
 }  // namespace plain
 
 namespace counted {
