@@ -721,6 +721,19 @@ __device__ __forceinline__ T small_t_series(T h, T t, T R) {
 // t, b_max of either type; the FP64 forms test the bits
 __device__ __forceinline__ bool small_t(double t) { return __double2hiint(t) < 0x3fb9999a; }  // 0.1
 __device__ __forceinline__ bool small_t(float t) { return t < Prec<float>::t_small; }
+// small_t with a preferred side near the threshold.  Over 0.09 <= t < 0.11
+// both forms are accurate (the series' truncation grows as t^12, 3x at 0.11;
+// the erfcx difference's cancellation as 1/t, 1.1x at 0.09), so there a quote
+// keeps the side its guess took (pref = 1: series, 0: erfcx; pref < 0: no
+// preference).  The binned solvers sort a tile's quotes by that side, and
+// the lanes of a warp then stay on one branch while their iterations cross
+// t_small instead of running both.
+__device__ __forceinline__ bool small_t_pref(double t, int pref) {
+  const int hi = __double2hiint(t);
+  if (pref >= 0 && hi >= 0x3fb70a3d && hi < 0x3fbc28f5) return pref != 0;  // [0.09, 0.11)
+  return hi < 0x3fb9999a;
+}
+__device__ __forceinline__ bool small_t_pref(float t, int) { return small_t(t); }
 __device__ __forceinline__ bool has_bound(double b) { return __double2hiint(b) >= 0; }
 __device__ __forceinline__ bool has_bound(float b) { return b >= 0.0f; }
 __device__ __forceinline__ bool positive(double v) { return positive64(v); }
@@ -746,13 +759,13 @@ __device__ __forceinline__ T halved(T v) {
 
 template <typename T, bool kIntHalf = true>
 __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e,
-                                        T bmax = T(-1), bool log_space = false) {
+                                        T bmax = T(-1), bool log_space = false, int pref = -1) {
   o.inv_s = recip(s);
   o.h = x * o.inv_s;
   o.t = halved<T, kIntHalf>(s);
   const T h = o.h, t = o.t;
   o.e = with_e ? f_exp(-halved<T, kIntHalf>(h * h + t * t)) : T(0);
-  const bool small = small_t(t) && !comp && (!log_space || series_in_log_space(x, s));
+  const bool small = small_t_pref(t, pref) && !comp && (!log_space || series_in_log_space(x, s));
   const bool via_comp = with_e && !comp && !small && has_bound(bmax) && positive(h + t);
   // erfcx of w/sqrt2 with w = -h, h + t or -(h + t)
   const T w1 = small ? -h : ((comp || via_comp) ? (h + t) : -(h + t));
@@ -931,9 +944,9 @@ __device__ __forceinline__ double guarded<double>(double s, double ds) {
 // it is not finite); the FP64 solver iterates it, the mixed solver applies it
 // once after its FP32 iterations.
 __device__ __forceinline__ double hh3_ds_mixed(const Reduced<double>& q, double s, int reg,
-                                               double* nu_out = nullptr) {
+                                               double* nu_out = nullptr, int pref = -1) {
   NB<double> v;
-  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax, reg == 0);
+  nb_eval<double>(q.x, s, reg == 3, v, reg == 1 || reg == 2, q.bmax, reg == 0, pref);
   const float hf = f32_trunc(v.h), sf = f32_trunc(s);
   const float hh = hf * hf, is = __frcp_rn(sf);
   const float u = hh * is - 0.25f * sf;
@@ -1075,16 +1088,16 @@ __device__ __forceinline__ T lbr_guess(Reduced<T>& q, int& reg) {
 
 // LBR iterations from the guess s of region reg: n_min Householder(3) steps,
 // then up to n_max while the last step still moved s by more than conv_tol
-// relative.
+// relative.  pref: the small-t side near the threshold (small_t_pref).
 template <typename T>
 __device__ __forceinline__ T lbr_iterate(Reduced<T> q, T s, int reg, int n_min, int n_max,
-                                         T conv_tol) {
+                                         T conv_tol, int pref = -1) {
   wing_logs<T>(q, reg);
   for (int k = 0; k < n_max; k++) {
     // FP64: residual and Newton step in FP64, second-order ratios in FP32
     T ds;
     if constexpr (std::is_same<T, double>::value)
-      ds = hh3_ds_mixed(q, s, reg);
+      ds = hh3_ds_mixed(q, s, reg, nullptr, pref);
     else
       ds = hh3_step<T>(objective<T>(q, s, reg));
     s = guarded<T>(s, ds);
@@ -1135,8 +1148,11 @@ __device__ __forceinline__ Reduced<float> reduced32(const Reduced<double>& q) {
 // hold the quote's scales (b_max below 1e-20, a guess outside 1e-30..1e30)
 // the FP64 guess is taken instead.
 __device__ __forceinline__ double lbr_solve64(const Reduced<double>& q, float g, int reg) {
+  // near t_small the iterations keep the guess's side (the side the binned
+  // tiles sort by)
   if (q.bmax > 1e-20 && g > 1e-30f && g < 1e30f)
-    return lbr_iterate<double>(q, f64_of(g), reg, 2, 3, 0x1p-17);
+    return lbr_iterate<double>(q, f64_of(g), reg, 2, 3, 0x1p-17,
+                               0.5f * g < (float)Prec<double>::t_small ? 1 : 0);
   int reg64 = 1;
   return lbr_solve<double>(q, 2, 3, 0x1p-17, reg64);
 }
