@@ -472,7 +472,7 @@ __device__ __forceinline__ Norm decide(int model, double P, double SF, double K,
   // subnormal rounding; its logarithm is taken from P directly
   // (beta < 1e-280 and P > 0 on the bit patterns: beta and P are finite here)
   o.ln_beta = (__double_as_longlong(beta) < __double_as_longlong(1e-280) && __double_as_longlong(P) > 0)
-                  ? log(P) + rate - 0.5 * log(__dmul_rn(SF, K))
+                  ? log64(P) + rate - 0.5 * log64(__dmul_rn(SF, K))
                   : 0.0;
   if (!bits_finite(x) || !bits_finite(beta)) return o;
   // Em = e^{-|x|/2} is the reduced call's bound; with E = Em - 1 (from expm1,
