@@ -1018,7 +1018,7 @@ def test_full_size_adjoint(fv, torch_dev):
     s, st = fv.fv_implied_vol(fv.FV_BSM, fv.FV_LBR, *ins, flag)
     adj = fv.fv_iv_adjoint(fv.FV_BSM, *ins, flag, s, st, _dev(torch_dev, w["grad_sigma"]))
     s_np, st_np = _np(s), _np(st)
-    idx = np.random.default_rng(5).choice(s_np.size, 2048, replace=False)
+    idx = np.random.default_rng(5).choice(s_np.size, 65536, replace=False)
     sub = lambda k: np.asarray(w[k])[idx]
     refs = orc.iv_grad(2, sub("S_or_F"), sub("K"), sub("T"), sub("r"), sub("q"), sub("flag"),
                        s_np[idx], st_np[idx], sub("grad_sigma"))
