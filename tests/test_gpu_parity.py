@@ -738,6 +738,39 @@ def test_host_streaming_matches_device(fv, torch_dev, solver, prec):
     plan.destroy()
 
 
+def test_host_batches_with_fp32_inputs(fv, torch_dev):
+    # FP32 host arrays through the stream plan: read in place (direct) they give
+    # the device call's results bit for bit; copied in chunks (staged) the same
+    # statuses and, in FP64 and mixed, sigma within rounding
+    torch, dev = torch_dev
+    w = wl.black76_fp32(200000, seed=12)
+    wl.fill_prices(w, orc.price, price_dtype=np.float32)
+    keys = ("P", "S_or_F", "K", "T", "r")
+    host = {k: torch.tensor(w[k]).pin_memory() for k in keys}
+    hflag = torch.tensor(w["flag"]).pin_memory()
+    devs = [torch.tensor(w[k], device=dev) for k in keys]
+    dflag = _dev(torch_dev, w["flag"])
+    plan = fv.fv_stream_plan_create(50000)
+    for prec in (fv.FV_FP64, fv.FV_MIXED, fv.FV_FP32):
+        s_d, st_d = fv.fv_implied_vol_ex(fv.FV_BLACK76, fv.FV_LBR, prec, *devs, None, dflag)
+        s_d, st_d = _np(s_d), _np(st_d)
+        for mode in (fv.FV_TRANSFER_DIRECT, fv.FV_TRANSFER_STAGED):
+            plan.set_transfer(mode)
+            s_h, st_h = plan.implied_vol(fv.FV_BLACK76, fv.FV_LBR, prec, *[host[k] for k in keys],
+                                         None, hflag)
+            torch.cuda.synchronize()
+            assert plan.last_transfer == mode
+            s_h, st_h = s_h.numpy(), st_h.numpy()
+            assert np.array_equal(st_h, st_d), (prec, mode)
+            assert np.array_equal(np.isnan(s_h), np.isnan(s_d)), (prec, mode)
+            ok = ~np.isnan(s_d) & (s_d > 0)
+            if mode == fv.FV_TRANSFER_DIRECT:
+                assert np.array_equal(s_h[ok], s_d[ok]), prec
+            elif prec != fv.FV_FP32:
+                assert np.all(np.abs(s_h[ok] - s_d[ok]) <= 1e-12 * s_d[ok]), prec
+    plan.destroy()
+
+
 # ---------------------------------------------------------------------------
 # the implied-volatility calls allocate nothing and never synchronise
 # ---------------------------------------------------------------------------
