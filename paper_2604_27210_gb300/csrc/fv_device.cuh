@@ -127,12 +127,24 @@ __device__ __forceinline__ double half64(double v) {
                                      : (sign | ((b & 0x7fffffffffffffffLL) >> 1)));
 }
 
+// Rare paths of the FP64 functions below, out of line: a warp whose lanes all
+// take the common path pays one untaken branch for them, where inlined code
+// of a short rare path can be predicated into every call and take FP64 issue
+// slots with no lane active.
+static __device__ __noinline__ double recip_rare(double s) { return 1.0 / s; }
+static __device__ __noinline__ double exp_rare(double v) { return v < -745.2 ? 0.0 : exp(v); }
+static __device__ __noinline__ double exp_expm1_rare(double v, double* em1) {
+  *em1 = v < 0.0 ? -1.0 : expm1(v);  // +inf, or NaN
+  return v < -745.2 ? 0.0 : exp(v);
+}
+static __device__ __noinline__ double log_rare(double y) { return log(y); }
+
 // 1/s for s in FP32's normal range (else the FP64 division): the FP32
 // reciprocal (relative error ~2^-23 after the truncation) and two Newton
 // steps r += r (1 - s r), the error squaring each time; within an ulp.
 __device__ __forceinline__ double recip64(double s) {
   const unsigned ah = (unsigned)__double2hiint(s) & 0x7fffffffu;
-  if (ah - 0x38200000u >= 0x0fb00000u) return 1.0 / s;  // |s| outside [2^-125, 2^126)
+  if (ah - 0x38200000u >= 0x0fb00000u) return recip_rare(s);  // |s| outside [2^-125, 2^126)
   double r = f64_of(__frcp_rn(f32_trunc(s)));
   r = fma(r, fma(-s, r, 1.0), r);
   return fma(r, fma(-s, r, 1.0), r);
@@ -164,7 +176,7 @@ __device__ __forceinline__ bool exp_table_range(double v) {
 }
 
 __device__ __forceinline__ double exp64(double v) {
-  if (!exp_table_range(v)) return v < -745.2 ? 0.0 : exp(v);
+  if (!exp_table_range(v)) return exp_rare(v);
   const double t = fma(v, FV_EXP_INV_LN2_N, 6755399441055744.0);  // 1.5 * 2^52: round to integer
   const int k = __double2loint(t);
   const double kd = t - 6755399441055744.0;
@@ -190,10 +202,7 @@ __device__ __forceinline__ double exp64(double v) {
 // there), so that the two terms never cancel by more than a factor ~1.3.
 // Within ~1 ulp for both.
 __device__ __forceinline__ double exp_expm1_64(double v, double& em1) {
-  if (!exp_table_range(v)) {
-    em1 = v < 0.0 ? -1.0 : expm1(v);  // +inf, or NaN
-    return v < -745.2 ? 0.0 : exp(v);
-  }
+  if (!exp_table_range(v)) return exp_expm1_rare(v, &em1);
   const double t = fma(v, FV_EXP_INV_LN2_N, 6755399441055744.0);
   const bool tiny = (__double2hiint(v) & 0x7fffffff) < 0x3f747ae1;  // |v| < 0.005
   const int k = tiny ? 0 : __double2loint(t);
@@ -242,8 +251,8 @@ __device__ __forceinline__ double erfcx_piece(int k, const MakeV& make_v) {
   return fma(p, v, c0.y);
 }
 
-// z >= 128, +inf (gives 0) or NaN (gives NaN)
-__device__ __forceinline__ double erfcx_asymptotic(double z) {
+// z >= 128, +inf (gives 0) or NaN (gives NaN); out of line (rare)
+static __device__ __noinline__ double erfcx_asymptotic(double z) {
   const double r = 1.0 / z, w = r * r;
   const double sum = fma(w, fma(w, fma(w, fma(w, 6.5625, -1.875), 0.75), -0.5), 1.0);
   return kInvSqrtPi * r * sum;
@@ -301,12 +310,15 @@ __device__ __forceinline__ double erfcx64(double z) {
 
 // erfcx(w/sqrt2) for any w, by the same reflection; z^2 = w^2/2 is split
 // exactly from w (the halving is exact)
-__device__ __forceinline__ double erfcx64_w(double w) {
-  const double p = erfcx_nonneg_w(fabs(w));
-  if (__double2hiint(w) >= 0) return p;
+static __device__ __noinline__ double erfcx_w_reflected(double w, double p) {
   const double ww = w * w, wl = fma(w, w, -ww);
   const double e2 = 2.0 * exp64(0.5 * ww);
   return isinf(e2) ? e2 : fma(e2, 0.5 * wl, e2) - p;
+}
+__device__ __forceinline__ double erfcx64_w(double w) {
+  const double p = erfcx_nonneg_w(fabs(w));
+  if (__double2hiint(w) >= 0) return p;
+  return erfcx_w_reflected(w, p);  // below zero: rare on the solvers' paths
 }
 
 // FP64 natural logarithm, the table-driven method of P. T. P. Tang (ACM TOMS
@@ -323,7 +335,7 @@ template <bool kWithC>
 __device__ __forceinline__ double log64_core(double y, double c) {
   const int hi = __double2hiint(y), lo = __double2loint(y);
   // positive, normal and finite: exponent field 1..2046 with the sign clear
-  if ((unsigned)hi - 0x00100000u >= 0x7fe00000u) return log(y);
+  if ((unsigned)hi - 0x00100000u >= 0x7fe00000u) return log_rare(y);
   const int mant = hi & 0xfffff;
   int m = (hi >> 20) - 1023, j, ehi;
   if (mant >= 0x6a09e) {  // f >= sqrt2: take f/2 in [1/sqrt2, 1), j in -75..0
@@ -757,6 +769,21 @@ __device__ __forceinline__ T halved(T v) {
   return T(0.5) * v;
 }
 
+// R(z) ~ 1/|z| - 1/|z|^3 for z -> -inf: with a = |h|, D = a^2 - t^2,
+// [R(h+t) - R(h-t)]/2 = (t/D) (1 - (3a^2 + t^2)/D^2) + O(t/a^6), times
+// sqrt(2/pi); the FP64 form out of line (|h| > 1e6: rare)
+template <typename T>
+__device__ __forceinline__ T series_asymptote_inline(T h, T t) {
+  const T D = h * h - t * t;
+  return T(kSqrt2OverPi) * (t / D) * (T(1) - (T(3) * h * h + t * t) / (D * D));
+}
+static __device__ __noinline__ double series_asymptote(double h, double t) {
+  return series_asymptote_inline<double>(h, t);
+}
+__device__ __forceinline__ float series_asymptote(float h, float t) {
+  return series_asymptote_inline<float>(h, t);
+}
+
 template <typename T, bool kIntHalf = true>
 __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with_e,
                                         T bmax = T(-1), bool log_space = false, int pref = -1) {
@@ -774,10 +801,7 @@ __device__ __forceinline__ void nb_eval(T x, T s, bool comp, NB<T>& o, bool with
     if (f_abs(h) < Prec<T>::h_asym) {
       o.B = T(kSqrt2OverPi) * small_t_series<T>(h, t, T(kSqrtPiOver2) * Y1);
     } else {
-      // R(z) ~ 1/|z| - 1/|z|^3 for z -> -inf: with a = |h|, D = a^2 - t^2,
-      // [R(h+t) - R(h-t)]/2 = (t/D) (1 - (3a^2 + t^2)/D^2) + O(t/a^6)
-      const T D = h * h - t * t;
-      o.B = T(kSqrt2OverPi) * (t / D) * (T(1) - (T(3) * h * h + t * t) / (D * D));
+      o.B = series_asymptote(h, t);
     }
   } else {
     const T Y2 = f_erfcx_w(t - h);
