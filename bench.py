@@ -61,7 +61,7 @@ FP32_PEAK_GFLOPS = 2 * 37459.7  # 37.46 T FFMA/s, bench_fp64_probe.py
 # refinement pass (13.70 MB: the status bytes and the marked quotes' inputs;
 # the same scan and the same marked quotes in both precisions).  Traffic grows
 # in proportion to the quotes, so a step's traffic is this x n.
-DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (205.78e6 + 24.57e6 + 13.70e6) / 4194304,
+DRAM_BYTES_PER_QUOTE_NCU = {"lbr": (206.03e6 + 25.57e6 + 13.70e6) / 4194304,
                             "mixed": (206.31e6 + 26.39e6 + 13.70e6) / 4194304}
 # FP64 peaks: measured on this machine's GB300 by bench_fp64_probe.py (526 G
 # DFMA/s = 1,052 GFLOP/s; profiles/fp64_fp32_throughput_probe.md), and the
