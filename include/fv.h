@@ -298,7 +298,9 @@ fv_err fv_autotune_cache_put(const char* path, const char* key, int block, int q
 fv_err fv_chains_plan_destroy(fv_chains_plan* plan);
 
 /* ---- host-resident batches ------------------------------------------- */
-/* A stream plan holds device staging for two chunks of up to chunk_quotes
+/* Section 2.1: the paper's entry points take host arrays (NumPy arrays,
+ * lists, pandas columns); these calls are their form for host memory on this
+ * GPU.  A stream plan holds device staging for two chunks of up to chunk_quotes
  * quotes (inputs and outputs), two CUDA streams and a 16-byte device tile
  * counter.  Created once (allocates device memory); used by
  * fv_implied_vol_host.  One call at a time per plan. */
