@@ -357,6 +357,20 @@ def test_status_margin_counts_ulps_to_the_nearest_threshold():
         margin = orc.status(orc.BLACK76, P, F, K, 1.0, 0.0, None, fl)[3][0]
         want = float(abs(k) * scale)
         assert abs(margin - want) <= 2.0, (K, fl, which, k, margin, want)
+        # and the decision on each side of the threshold, from the rule's
+        # definition: below intrinsic under iota (1 - e_s); sigma = 0 up to
+        # iota (1 + e_s); above the bound from b_max (1 - e_s) of the reduced quote
+        sig, st = orc.iv(orc.BLACK76, P, F, K, 1.0, 0.0, None, fl)
+        if which == "below":
+            assert st[0] == (orc.BELOW_INTRINSIC if k < 0 else orc.OK), (K, fl, which, k)
+            if k > 0:
+                assert sig[0] == 0.0
+        elif which == "at":
+            assert st[0] == orc.OK and ((sig[0] == 0.0) if k < 0 else (sig[0] > 0.0)), (K, fl, which, k)
+        else:
+            assert st[0] == (orc.ABOVE_MAX if k > 0 else orc.OK), (K, fl, which, k)
+            if k < 0:
+                assert sig[0] > 0.0
     # far from every threshold the margin is large; an invalid quote has none
     assert orc.status(orc.BLACK76, 12.0, F, 90.0, 1.0, 0.0, None, 1)[3][0] > 1e10
     assert orc.status(orc.BLACK76, 5.0, F, 90.0, 1.0, 0.0, None, 0)[3][0] == np.inf
