@@ -54,6 +54,13 @@ MUTANTS = [
      "const R iota = itm ? (-E * (1.0 - Em)) / Em : 0.0;\n  o->x = x;"),
     ("status: upper band on the wrong side",
      "if (beta_otm >= bmax_otm * (1.0 - EPS_S)) {", "if (beta_otm >= bmax_otm * (1.0 + EPS_S)) {"),
+    ("status: band of 4 units of 2^-52 instead of 64",
+     "#define EPS_S (64.0 * 2.220446049250313080847263336181640625e-16)",
+     "#define EPS_S (4.0 * 2.220446049250313080847263336181640625e-16)"),
+    ("status: below-intrinsic test without its band",
+     "if (beta < iota * (1.0 - EPS_S)) {", "if (beta < iota) {"),
+    ("status: at-intrinsic test without its band",
+     "o->solve = beta_otm > iota * EPS_S;", "o->solve = beta_otm > 0.0;"),
     ("status: in-the-money test with the wrong sign",
      "const int itm = th * x > 0;\n  const R iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x",
      "const int itm = th * x < 0;\n  const R iota = itm ? (-E * (1.0 + Em)) / Em : 0.0;\n  o->x"),
