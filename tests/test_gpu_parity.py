@@ -661,6 +661,74 @@ def test_invalid_and_boundary_quotes(fv, torch_dev):
     assert list(st_ref[:12]) == [0, 1, 1, 0, 2, 2, 3, 3, 3, 3, 3, 3]
 
 
+def _status_edge_quotes():
+    """Black-76 quotes (F = 100, T = 1, r = 0, so beta = P / sqrt(F K)) built
+    in 50 digits at k units of 2^-52 from each threshold of the status rule
+    (below intrinsic at iota (1 - e_s), at intrinsic at iota (1 + e_s), above
+    the bound at b_max (1 - e_s) of the reduced quote, e_s = 64 * 2^-52), and
+    the status and sigma class the rule's definition gives each side."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    F, u = Decimal(100), Decimal(2) ** -52
+    es = 64 * u
+    P, K, flag, want, zero = [], [], [], [], []
+    for k in (-48, -20, -6, 6, 20, 48):
+        for Kv, fl, which in ((90, 1, "below"), (110, -1, "below"), (90, 1, "at"),
+                              (110, 1, "above"), (90, -1, "above"), (90, 1, "above")):
+            x = (F / Decimal(Kv)).ln()
+            itm = fl * x > 0
+            if which != "above" and not itm:
+                continue
+            a = abs(x) / 2
+            iota = (a.exp() - (-a).exp()) if itm else Decimal(0)
+            bmax = (-a).exp()
+            if which == "below":
+                beta = iota * (1 - es) * (1 + k * u)
+                st, z = (orc.BELOW_INTRINSIC, False) if k < 0 else (orc.OK, True)
+            elif which == "at":
+                beta = iota * (1 + es) * (1 + k * u)
+                st, z = orc.OK, k < 0
+            else:
+                beta = iota + bmax * (1 - es) * (1 + k * u)
+                st, z = (orc.ABOVE_MAX, False) if k > 0 else (orc.OK, False)
+            P.append(float(beta * (F * Decimal(Kv)).sqrt()))
+            K.append(float(Kv))
+            flag.append(fl)
+            want.append(st)
+            zero.append(z)
+    return (np.array(P), np.array(K), np.array(flag, np.int8), np.array(want, np.uint8),
+            np.array(zero))
+
+
+def test_status_edges_on_every_path(fv, torch_dev):
+    # Every solver decides the quotes 6 to 48 units of 2^-52 from a threshold
+    # as the rule's definition (and the oracle's FP64 rule) does, in the small,
+    # medium and large launch shapes: the double-float rule of the mixed and
+    # FP32 tiles hands such quotes to the FP64 rule
+    torch, dev = torch_dev
+    P, K, flag, want, zero = _status_edge_quotes()
+    st_o = orc.status(orc.BLACK76, P, np.full(P.size, 100.0), K, np.ones(P.size), np.zeros(P.size),
+                      None, flag)[0]
+    assert np.array_equal(st_o, want)
+    for n in (P.size, 100000, 1 << 17):
+        reps = -(-n // P.size)
+        t = lambda a: torch.tensor(np.tile(a, reps)[:n], device=dev)
+        args = [t(P), torch.full((n,), 100.0, dtype=torch.float64, device=dev), t(K),
+                torch.ones(n, dtype=torch.float64, device=dev),
+                torch.zeros(n, dtype=torch.float64, device=dev)]
+        fl = t(flag)
+        w, z = np.tile(want, reps)[:n], np.tile(zero, reps)[:n]
+        for solver, prec in ((0, 0), (0, 1), (0, 2), (1, 0), (1, 2)):
+            s, st = fv.fv_implied_vol_ex(fv.FV_BLACK76, solver, prec, *args, None, fl)
+            s, st = _np(s), _np(st)
+            assert np.array_equal(st, w), (n, solver, prec, int((st != w).sum()))
+            ok = w == orc.OK
+            assert np.all(s[ok & z] == 0.0), (n, solver, prec)
+            if prec != 2:  # FP32 paths: only what the rule decides (beside the bound sigma may overflow)
+                assert np.all(s[ok & ~z] > 0.0), (n, solver, prec)
+            assert np.all(np.isnan(s[~ok])), (n, solver, prec)
+
+
 def test_zero_length_is_a_noop(fv, torch_dev):
     torch, dev = torch_dev
     e = torch.empty(0, dtype=torch.float64, device=dev)
