@@ -40,6 +40,32 @@ def test_binding_lists_every_declared_symbol():
     assert sorted(fv.EXPORTS) == declared_symbols()
 
 
+def declared_constants():
+    """Every enumerator and #define FV_* value of the header, by name."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, value in re.findall(r"\b(FV_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(value)
+    for name, value in re.findall(r"#define\s+(FV_[A-Z0-9_]+)\s+(-?\d+)", src):
+        consts[name] = int(value)
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    # the Python names of the enumerators carry the header's values (an enum
+    # the binding does not name is fine; a wrong value is not)
+    from paper_2604_27210_gb300 import fv
+    consts = declared_constants()
+    for must in ("FV_BSM", "FV_HALLEY", "FV_FP32", "FV_DTYPE_F32", "FV_TRANSFER_DIRECT",
+                 "FV_NOALLOC_MAX_QUOTES", "FV_ERR_ARG"):
+        assert must in consts, must
+    named = {k: v for k, v in consts.items() if hasattr(fv, k)}
+    assert len(named) >= 20, sorted(named)
+    for k, v in named.items():
+        assert getattr(fv, k) == v, (k, getattr(fv, k), v)
+
+
 def _p(v=0x1000):
     return ctypes.c_void_p(v)
 
