@@ -33,7 +33,8 @@ int grid_for(int64_t n, int block, int per_sm);
 // LBR: batches of kSmallBatch quotes or more run the region-binned kernel with
 // dynamic tiles, whose counters are a.ctr or else the first two sigma outputs
 // (zeroed on `st` before the launch), then the refinement kernel over the
-// quotes it marked; smaller ones one unbinned kernel
+// quotes it marked; medium ones (from kMidBatch[prec]) the medium-batch tiles
+// below; smaller ones one unbinned kernel
 cudaError_t launch_iv_lbr(const IvArgs& a, int prec, cudaStream_t st);
 // Medium batches, kMidBatch[prec] <= n < 2^17 quotes: one launch of 128-quote
 // region-binned tiles, one per block, that refine their ill-conditioned

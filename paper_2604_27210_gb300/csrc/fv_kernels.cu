@@ -205,7 +205,9 @@ static cudaError_t launch_binned(const IvArgs& a, cudaStream_t st) {
 // 5 blocks per SM would cap the registers at 48 and spill).  The mixed and
 // FP32 paths run the tile whose status rule is in double-float (2 quotes per
 // thread, 4 blocks per SM; their FP32 iterations in phase 2).  Batches below
-// kSmallBatch take the unbinned kernel with 64-thread blocks.
+// kSmallBatch take the medium-batch tiles (fv_kernels_mid.cu) from
+// kMidBatch[precision] quotes, and the unbinned kernel with 64-thread blocks
+// below that.
 
 template <typename InT, int PREC>
 static void launch_flat_prec(const IvArgs& a, int block, cudaStream_t st) {
